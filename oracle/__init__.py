@@ -1,0 +1,195 @@
+"""CPU FP64 oracle for inverse iteration with MGS / Householder / compact-WY reorthogonalization
+(Ishigami, Kimura, Nakamura, arXiv:1209.1910).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``.  The product path (the CUDA
+library and its binding) never imports it, and it shares no code with that path.
+
+The arithmetic lives in ``tinv_oracle.c`` (plain C, built with ``-ffp-contract=off``); this
+module only compiles it and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tinv_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MGS, CWY, HOUSE = 0, 1, 2
+METHODS = {"mgs": MGS, "cwy": CWY, "house": HOUSE}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, -O2, no FP contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "tinv_oracle.h"))
+    ):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("breakdowns", ctypes.c_int64),
+                ("orth_flops", ctypes.c_double)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            D = ctypes.c_double
+            lib.orc_sm64_mix.restype = ctypes.c_uint64
+            lib.orc_sm64_mix.argtypes = [ctypes.c_uint64]
+            lib.orc_start_value.restype = D
+            lib.orc_start_value.argtypes = [ctypes.c_uint64, I64, ctypes.c_int, I64]
+            lib.orc_onenorm.restype = D
+            lib.orc_onenorm.argtypes = [I64, P, P]
+            lib.orc_sturm_count.restype = I64
+            lib.orc_sturm_count.argtypes = [I64, P, P, D, D]
+            lib.orc_bisect.restype = None
+            lib.orc_bisect.argtypes = [I64, P, P, P]
+            lib.orc_plan.restype = None
+            lib.orc_plan.argtypes = [I64, P, P, I64, P, P, P, P, P, P]
+            lib.orc_lagtf.restype = None
+            lib.orc_lagtf.argtypes = [I64, P, P, D, P, P, P, P, P]
+            lib.orc_lagts.restype = D
+            lib.orc_lagts.argtypes = [I64, P, P, P, P, P, P]
+            for name in ("orc_orth_mgs",):
+                getattr(lib, name).restype = D
+                getattr(lib, name).argtypes = [I64, I64, P, I64, P, I64]
+            for name in ("orc_orth_house", "orc_orth_cwy_ordinary", "orc_orth_cwy_new"):
+                getattr(lib, name).restype = D
+                getattr(lib, name).argtypes = [I64, I64, P, I64, P, I64, P, P]
+            lib.orc_tinv.restype = I64
+            lib.orc_tinv.argtypes = [I64, P, P, I64, P, I64, P, I64, ctypes.c_int,
+                                     ctypes.c_uint64, P, P, ctypes.POINTER(_Stats)]
+            lib.orc_jacobi.restype = None
+            lib.orc_jacobi.argtypes = [I64, P, P, P]
+            _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None and a.size else None
+
+
+# ----------------------------------------------------------------------------------------
+def sm64_mix(z: int) -> int:
+    return int(_load().orc_sm64_mix(ctypes.c_uint64(z & 0xFFFFFFFFFFFFFFFF)))
+
+
+def start_vector(seed: int, j: int, n: int, attempt: int = 0) -> np.ndarray:
+    lib = _load()
+    return np.array([lib.orc_start_value(seed, j, attempt, i) for i in range(n)])
+
+
+def onenorm(d, e) -> float:
+    d, e = _f64(d), _f64(e)
+    return float(_load().orc_onenorm(len(d), _p(d), _p(e)))
+
+
+def sturm_count(d, e, x: float, pivmin: float) -> int:
+    d, e = _f64(d), _f64(e)
+    return int(_load().orc_sturm_count(len(d), _p(d), _p(e), x, pivmin))
+
+
+def bisect(d, e) -> np.ndarray:
+    d, e = _f64(d), _f64(e)
+    w = np.empty(len(d))
+    _load().orc_bisect(len(d), _p(d), _p(e), _p(w))
+    return w
+
+
+def plan(d, e, w):
+    """Returns (wp, head, onenrm, ortol, dtpcrt)."""
+    d, e, w = _f64(d), _f64(e), _f64(w)
+    m = len(w)
+    wp = np.empty(m)
+    head = np.empty(m, dtype=np.int64)
+    o = (ctypes.c_double * 3)()
+    _load().orc_plan(len(d), _p(d), _p(e), m, _p(w), _p(wp), _p(head),
+                     ctypes.byref(o, 0), ctypes.byref(o, 8), ctypes.byref(o, 16))
+    return wp, head, o[0], o[1], o[2]
+
+
+def lagtf(d, e, lam: float):
+    """Returns (u0, u1, u2, l, piv) of T - lam*I = P L U."""
+    d, e = _f64(d), _f64(e)
+    n = len(d)
+    u0, u1, u2, l = (np.zeros(n) for _ in range(4))
+    piv = np.zeros(n, dtype=np.uint8)
+    _load().orc_lagtf(n, _p(d), _p(e), lam, _p(u0), _p(u1), _p(u2), _p(l), _p(piv))
+    return u0, u1, u2, l, piv
+
+
+def lagts(factors, y):
+    u0, u1, u2, l, piv = factors
+    x = _f64(y).copy()
+    tol = _load().orc_lagts(len(u0), _p(u0), _p(u1), _p(u2), _p(l), _p(piv), _p(x))
+    return x, tol
+
+
+def orth(V, method: str):
+    """Stand-alone orthogonalization of the columns of V (n x m).  Returns (Q, Y, T, flops);
+    Y/T are None for MGS, T is the vector of t_j for Householder."""
+    V = np.asfortranarray(V, dtype=np.float64)
+    n, m = V.shape
+    Q = np.zeros((n, m), order="F")
+    lib = _load()
+    if method == "mgs":
+        fl = lib.orc_orth_mgs(n, m, _p(V), n, _p(Q), n)
+        return Q, None, None, fl
+    Y = np.zeros((n, m), order="F")
+    if method == "house":
+        tv = np.zeros(m)
+        fl = lib.orc_orth_house(n, m, _p(V), n, _p(Q), n, _p(Y), _p(tv))
+        return Q, Y, tv, fl
+    T = np.zeros((m, m), order="F")
+    fn = {"cwy_ordinary": lib.orc_orth_cwy_ordinary, "cwy_new": lib.orc_orth_cwy_new}[method]
+    fl = fn(n, m, _p(V), n, _p(Q), n, _p(Y), _p(T))
+    return Q, Y, T, fl
+
+
+def tinv(d, e, w, method: str = "cwy", seed: int = 0, j0: int = 0):
+    """Inverse iteration for the eigenvectors of w.  Returns (Z, info, ifail, iters, stats)."""
+    d, e, w = _f64(d), _f64(e), _f64(w)
+    n, m = len(d), len(w)
+    Z = np.zeros((n, m), order="F")
+    ifail = np.zeros(max(m, 1), dtype=np.int64)
+    iters = np.zeros(max(m, 1), dtype=np.int32)
+    st = _Stats()
+    info = _load().orc_tinv(n, _p(d), _p(e), m, _p(w), j0, _p(Z), n, METHODS[method],
+                            ctypes.c_uint64(seed), _p(ifail), _p(iters), ctypes.byref(st))
+    return Z, int(info), ifail[:info], iters[:m], {
+        "sweeps": st.sweeps, "breakdowns": st.breakdowns, "orth_flops": st.orth_flops}
+
+
+def jacobi(A):
+    """Cyclic Jacobi: returns (ascending eigenvalues, eigenvectors as columns)."""
+    A = np.asfortranarray(A, dtype=np.float64).copy(order="F")
+    n = A.shape[0]
+    lam = np.zeros(n)
+    V = np.zeros((n, n), order="F")
+    _load().orc_jacobi(n, _p(A), _p(lam), _p(V))
+    return lam, V

@@ -1,0 +1,132 @@
+"""Pins of the oracle's inverse iteration (Alg. 1 with MGS, Alg. 4 with compact WY, Alg. 2
+applied incrementally): closed-form Toeplitz eigenvectors, the residual and orthogonality
+invariants, dense Jacobi brute force, LAPACK's DSTEIN run as a black box, and agreement of
+the three orthogonalizations on each cluster's invariant subspace."""
+import numpy as np
+import pytest
+import scipy.linalg.lapack as lapack
+
+from helpers import EPS, clusters_from_heads, dense, orth_ratio, residual_ratio, sign_fix, sin_angle
+from paper_1209_1910_gb300 import inputs
+
+METHODS = ["cwy", "mgs", "house"]
+
+
+def _cases():
+    d1, e1 = inputs.uniform(300, seed=1)
+    d2, e2 = inputs.glued_wilkinson(20, 1e-10)
+    d3, e3 = inputs.toeplitz(301, 0.0, 1.0)
+    d4, e4 = inputs.uniform(200, seed=2, lo=0.0, hi=1.0)   # Type 1 of Sec. 5.1
+    d5, e5 = inputs.glued_wilkinson(10, 1e-4)             # Type 3 of Sec. 5.1
+    return {"uniform300": (d1, e1), "glued420": (d2, e2), "zero301": (d3, e3),
+            "type1_200": (d4, e4), "type3_210": (d5, e5)}
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("case", list(CASES))
+def test_invariants(orc, case, method):
+    d, e = CASES[case]
+    w = orc.bisect(d, e)
+    Z, info, ifail, iters, st = orc.tinv(d, e, w, method)
+    assert info == 0
+    assert residual_ratio(d, e, w, Z) <= 10.0
+    assert orth_ratio(Z) <= 10.0
+    assert np.all((iters >= 3) & (iters <= 5))
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_toeplitz_closed_form_vectors(orc, method):
+    n = 200
+    d, e = inputs.toeplitz(n, 2.0, 1.0)
+    lam, V = inputs.toeplitz_eigenpairs(n, 2.0, 1.0)
+    Z, info, *_ = orc.tinv(d, e, lam, method)
+    assert info == 0
+    R = dense(d, e) @ Z - Z * lam
+    gaps = np.minimum(np.r_[np.inf, np.diff(lam)], np.r_[np.diff(lam), np.inf])
+    # Davis-Kahan: sin(angle) <= ||r|| / gap for a simple eigenvalue
+    bound = 4 * np.linalg.norm(R, axis=0) / gaps + 1e-14
+    ang = np.linalg.norm(Z - V * np.sign(np.sum(Z * V, axis=0)), axis=0)
+    assert np.all(ang <= bound)
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_jacobi_brute_force(orc, method):
+    d, e = inputs.uniform(48, seed=9)
+    lam, V = orc.jacobi(dense(d, e))
+    w = orc.bisect(d, e)
+    Z, info, *_ = orc.tinv(d, e, w, method)
+    assert info == 0 and np.abs(w - lam).max() < 1e-13
+    _, head, *_ = orc.plan(d, e, w)
+    for idx in clusters_from_heads(head):
+        assert sin_angle(V[:, idx], Z[:, idx]) < 1e-10
+        if len(idx) == 1:
+            assert np.abs(sign_fix(Z[:, idx]) - sign_fix(V[:, idx])).max() < 1e-12
+
+
+def test_orthogonalizations_agree_per_cluster(orc):
+    d, e = inputs.glued_wilkinson(20, 1e-10)
+    w = orc.bisect(d, e)
+    Zc = orc.tinv(d, e, w, "cwy")[0]
+    Zh = orc.tinv(d, e, w, "house")[0]
+    Zm = orc.tinv(d, e, w, "mgs")[0]
+    _, head, *_ = orc.plan(d, e, w)
+    cl = clusters_from_heads(head)
+    assert len(cl) == 14
+    for idx in cl:
+        assert sin_angle(Zc[:, idx], Zh[:, idx]) < 1e-10
+        assert sin_angle(Zc[:, idx], Zm[:, idx]) < 1e-10
+
+
+@pytest.mark.parametrize("case", ["uniform300", "glued420", "type3_210"])
+def test_lapack_dstein_black_box(orc, case):
+    # LAPACK's DSTEIN (the paper's baseline, run as a black box through SciPy) finds the same
+    # invariant subspace for every cluster; its bases inside clusters differ (other starts).
+    d, e = CASES[case]
+    n = len(d)
+    w = orc.bisect(d, e)
+    Zl, info = lapack.dstein(d, e, w, np.ones(n, dtype=np.int32), np.full(n, n, dtype=np.int32))
+    assert info == 0
+    Z = orc.tinv(d, e, w, "cwy")[0]
+    _, head, *_ = orc.plan(d, e, w)
+    for idx in clusters_from_heads(head):
+        assert sin_angle(Zl[:, idx], Z[:, idx]) < 1e-10
+        if len(idx) == 1:
+            assert np.abs(sign_fix(Z[:, idx]) - sign_fix(Zl[:, idx])).max() < 1e-10
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_subrange_reproduces_full_problem(orc, method):
+    d, e = inputs.glued_wilkinson(12, 1e-10)
+    w = orc.bisect(d, e)
+    Z = orc.tinv(d, e, w, method)[0]
+    _, head, *_ = orc.plan(d, e, w)
+    for idx in clusters_from_heads(head)[:4]:
+        s, t = idx[0], idx[-1] + 1
+        Zs = orc.tinv(d, e, w[s:t], method, j0=s)[0]
+        assert np.array_equal(Zs, Z[:, s:t])
+
+
+def test_edge_cases(orc):
+    Z, info, *_ = orc.tinv([3.0], [], [3.0], "cwy")
+    assert info == 0 and Z.tolist() == [[1.0]]
+    d, e = np.array([1.0, 1.0]), np.array([1.0])
+    Z, info, *_ = orc.tinv(d, e, np.array([0.0, 2.0]), "cwy")
+    s = 1 / np.sqrt(2)
+    assert info == 0 and np.allclose(Z, [[s, s], [-s, s]], atol=1e-15)
+    # exact zero off-diagonal entries: decoupled blocks with coinciding eigenvalues
+    d = np.array([0.5, 0.5, 0.5, -0.2])
+    e = np.array([0.0, 0.0, 0.3])
+    w = np.sort(np.linalg.eigvalsh(dense(d, e)))
+    for method in METHODS:
+        Z, info, *_ = orc.tinv(d, e, w, method)
+        assert info == 0
+        assert residual_ratio(d, e, w, Z) <= 10 and orth_ratio(Z) <= 10
+    # subset of the spectrum (m < n)
+    d, e = inputs.uniform(50, seed=4)
+    w = orc.bisect(d, e)
+    Z, info, *_ = orc.tinv(d, e, w[10:30], "cwy", j0=10)
+    assert Z.shape == (50, 20) and info == 0
+    assert residual_ratio(d, e, w[10:30], Z) <= 10
