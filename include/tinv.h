@@ -1,0 +1,153 @@
+/*
+ * tinv.h -- C ABI of the GB300 (sm_103a) library for all eigenvectors of a real symmetric
+ * tridiagonal matrix by inverse iteration with compact-WY (or MGS) reorthogonalization.
+ *
+ * Method: Ishigami, Kimura, Nakamura, "On Implementation and Evaluation of Inverse Iteration
+ * Algorithm with compact WY Orthogonalization", arXiv:1209.1910.  Problem statement Sec. 2.1
+ * (Eq. 1); classical inverse iteration Alg. 1; DSTEIN-cWY Alg. 4 with the compact-WY update
+ * of Sec. 3.3.2 (Eqs. yt, cwy1, cwy2).
+ *
+ * Conventions shared by every entry point:
+ *   - T is given by its diagonal d[0..n) and off-diagonal e[0..n-1) (e may be NULL if n == 1).
+ *   - Eigenvalue approximations w[0..m) must be finite and ascending (non-decreasing).
+ *   - Matrices are column-major with a leading dimension (ldz >= n, ldv >= n).
+ *   - All arithmetic is IEEE binary64.
+ *   - Unless tinv_opts.device_ptrs is set, every pointer is HOST memory owned by the caller;
+ *     the call copies inputs to the GPU, runs, copies results back and synchronizes.
+ *     With device_ptrs set, every array pointer is DEVICE memory of the current device, the
+ *     work is enqueued on tinv_opts.stream and the call returns without synchronizing.
+ *   - Return codes: 0 = success; -k = argument k is invalid (1-based position in the call);
+ *     > 0 = number of eigenvectors that did not converge within MAXITS = 5 sweeps (their
+ *     columns are still written, as LAPACK DSTEIN does); values <= -100 are runtime errors
+ *     listed below.  tinv_strerror() gives a message for any code.
+ *   - Thread safety: calls on different streams may run concurrently from different host
+ *     threads; the library keeps no global mutable state besides a per-device cache of the
+ *     number of SMs.
+ */
+#ifndef TINV_H
+#define TINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TINV_OK 0
+#define TINV_ENOMEM (-101)    /* device or pinned-host allocation failed                   */
+#define TINV_ECUDA (-102)     /* a CUDA runtime call failed (launch, copy, sync)           */
+#define TINV_ETIMEDOUT (-103) /* a bounded device-side wait expired (see each kernel)      */
+#define TINV_EAGAIN (-104)    /* server: no slot / memory free right now, retry            */
+#define TINV_ECANCELED (-105) /* server: request was cancelled                            */
+#define TINV_ENOTSUP (-106)   /* size beyond what this build supports                      */
+#define TINV_ENODEV (-107)    /* no CUDA device, or not an sm_103 device                   */
+#define TINV_EWORKSPACE (-108) /* caller-provided workspace is too small                   */
+
+/* Reorthogonalization of eigenvectors inside a cluster. */
+#define TINV_CWY 0 /* compact-WY Householder orthogonalization (Sec. 3.3.2, Alg. 4)   */
+#define TINV_MGS 1 /* modified Gram-Schmidt as in LAPACK DSTEIN (Alg. 1)               */
+
+typedef struct tinv_opts {
+    int32_t method;      /* TINV_CWY (default) or TINV_MGS                                   */
+    int32_t device_ptrs; /* 0: host pointers, synchronous; 1: device pointers, async         */
+    void* stream;        /* cudaStream_t used when device_ptrs = 1 (NULL = legacy stream)    */
+    uint64_t seed;       /* start vectors: counter-based SplitMix64 keyed by (seed, j0 + j)  */
+    int64_t j0;          /* index offset of w[0] inside a larger problem (for start keys)    */
+    void* workspace;     /* optional device workspace (device_ptrs = 1); NULL = the library  */
+    size_t workspace_bytes; /*   allocates stream-ordered memory itself                       */
+    int32_t* iters;      /* optional [m]: sweeps taken by vector j, negated if not converged;  */
+                         /*   host or device memory following device_ptrs                     */
+    int64_t* info;       /* optional (device_ptrs = 1): device scalar that receives the count */
+                         /*   of non-converged vectors                                         */
+    int32_t max_team;    /* 0 = automatic; otherwise the most CTAs one cluster may use        */
+    int32_t grid_ctas;   /* 0 = all co-resident CTAs; otherwise cap on the persistent grid    */
+    float* phase_ms;     /* optional HOST [4]: device milliseconds of the plan, LU, first-sweep */
+                         /*   and cluster kernels, from CUDA events on the call's stream; the  */
+                         /*   call then synchronizes that stream before returning             */
+    int32_t reserved[8];
+} tinv_opts;
+
+/* Fill *o with the defaults: CWY, host pointers, seed 0, j0 0, automatic scheduling. */
+void tinv_opts_default(tinv_opts* o);
+
+/* Human-readable message for a return code. */
+const char* tinv_strerror(int code);
+
+/* Library version string and the CUDA architecture it was built for. */
+const char* tinv_version(void);
+
+/*
+ * tinv -- all n eigenvectors of T (Sec. 2.1: compute v_j for every lambda_j).
+ *   n   : matrix order, n >= 0 (n = 0 is a no-op; n = 1 gives Z = [1]).
+ *   d,e : host arrays [n], [n-1].
+ *   w   : host array [n], ascending eigenvalue approximations (e.g. from bisection).
+ *   Z   : host array n x n, column-major, ldz = n, caller-allocated; column j receives the
+ *         unit eigenvector of w[j], sign chosen so its first entry of largest magnitude is
+ *         positive.
+ * Defaults of tinv_opts_default() apply (CWY, seed 0).  Returns as described above.
+ */
+int tinv(int64_t n, const double* d, const double* e, const double* w, double* Z);
+
+/*
+ * tinv_ex -- eigenvectors of m eigenvalues w[0..m) (m <= n), with options.
+ *   Arguments as tinv; Z is n x m with leading dimension ldz >= n.
+ *   ifail : optional host array [m]; on return its first r entries are the (0-based) indices
+ *           of the r vectors that did not converge (host-pointer mode only).
+ *   o     : options (NULL = defaults).  With o->device_ptrs the call is asynchronous on
+ *           o->stream and returns 0 when the work is enqueued; the non-converged count goes
+ *           to o->info and per-vector sweep counts to o->iters.
+ * Clusters are found by the Peters-Wilkinson test |w'_j - w'_{j-1}| <= 1e-3 ||T||_1 over the
+ * perturbed shifts w' (Sec. 2.1; Alg. 1 / Alg. 4).
+ */
+int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double* w, double* Z,
+            int64_t ldz, const tinv_opts* o, int64_t* ifail);
+
+/* Bytes of device workspace tinv_ex needs for (n, m) with the given options. */
+size_t tinv_workspace_size(int64_t n, int64_t m, const tinv_opts* o);
+
+/*
+ * tinv_plan -- step a1/a2 alone (Sec. 2.1; Alg. 4 lines 8-9 and 17-18): ||T||_1, the cluster
+ * tolerance, the convergence threshold and the cluster head of every eigenvalue.
+ *   wp    : [m] perturbed shifts w' (coincident approximations are separated by 10 eps |w|).
+ *   head  : [m] index of the first member of the cluster of j (j itself for a cluster head).
+ *   scal  : [3] = { ||T||_1, 1e-3 ||T||_1, sqrt(0.1/n) }.
+ * Pointers follow o->device_ptrs.  Deterministic and bit-identical to a sequential scan.
+ */
+int tinv_plan(int64_t n, const double* d, const double* e, int64_t m, const double* w,
+              double* wp, int32_t* head, double* scal, const tinv_opts* o);
+
+/*
+ * tinv_lu -- step a3 alone: LU with scaled partial pivoting of T - s_j I (the matrix of Eq. 1)
+ * for every shift s[0..m).  Outputs are m x n arrays, row j (stride n) for shift j:
+ *   l     : multipliers of the unit lower bidiagonal L;  u0 : diagonal of U;
+ *   u1,u2 : first and second superdiagonals of U;  piv : 1 where rows k, k+1 were swapped.
+ * Entries past the end of each factor (l, u1, u2 at k = n-1, u2 at n-2) are written as 0.
+ * Bit-identical to a sequential evaluation with the same operation order (no contraction).
+ */
+int tinv_lu(int64_t n, const double* d, const double* e, int64_t m, const double* s, double* l,
+            double* u0, double* u1, double* u2, uint8_t* piv, const tinv_opts* o);
+
+/*
+ * tinv_solve -- step a5 alone: x_j <- (T - s_j I)^{-1} x_j for m right-hand sides X (n x m,
+ * ldx), each scaled first as in DSTEIN when scale != 0 (x <- x n ||T||_1 max(eps,|u_nn|)/||x||_1).
+ * Diagonal entries of U below tol = eps max|U| in magnitude are replaced by sign(u) tol.
+ */
+int tinv_solve(int64_t n, const double* d, const double* e, int64_t m, const double* s,
+               double* X, int64_t ldx, int32_t scale, const tinv_opts* o);
+
+/*
+ * tinv_orth -- incremental orthogonalization of the columns of V (n x m, ldv) by the GPU
+ * reorthogonalization kernels, without inverse iteration (Sec. 3):
+ *   method TINV_CWY: Alg. 3 in the form of Sec. 3.3.2; Q[:,j] = (Y_j T_j Y_j^T - I) e_j (the
+ *                    sign-flipped q_j of that section); optional Y (n x m, ld n) and T
+ *                    (m x m, ld m, upper triangular) receive the compact-WY factors.
+ *   method TINV_MGS: modified Gram-Schmidt; Q[:,j] unit vectors; Y and T are not written.
+ */
+int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int64_t ldq,
+              double* Y, double* T, const tinv_opts* o);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TINV_H */

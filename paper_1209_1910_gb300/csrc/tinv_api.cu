@@ -1,0 +1,672 @@
+// tinv_api.cu -- host side of libtinv: argument checks, workspace layout, transfers and the
+// launch sequence of the C ABI declared in include/tinv.h.
+//
+// Launch sequence of tinv_ex (one stream, no host synchronization in between):
+//   k_plan (1 CTA)        a1-a2: ||T||_1, tolerances, perturbed shifts, clusters, team schedule
+//   k_lu   (thread/shift) a3   : LU with scaled partial pivoting of T - w'_j I, all j
+//   k_first(warp/shift)   a4-a5, a7-a8 for cluster heads and singletons; first sweep of members
+//   k_chain(cooperative)  a5-a8 with a6 (compact WY or MGS) for cluster members, in order
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/tinv.h"
+#include "tinv_internal.h"
+
+namespace tinvx {
+
+cudaError_t launch_norm(const Problem& p, const Ws& w, cudaStream_t st);
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+Layout make_layout(int64_t n, int64_t m, int32_t P, bool need_chain)
+{
+    Layout L;
+    memset(&L, 0, sizeof(L));
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + (bytes ? bytes : 1), 256);
+        return o;
+    };
+    const size_t nn = (size_t)n, mm = (size_t)m, pp = (size_t)P;
+    L.scal = take(4 * sizeof(double));
+    L.wp = take(mm * sizeof(double));
+    L.head = take(mm * sizeof(int32_t));
+    L.clstart = take(mm * sizeof(int32_t));
+    L.clsize = take(mm * sizeof(int32_t));
+    L.cltoff = take(mm * sizeof(int64_t));
+    L.sched = take(pp * 4 * sizeof(int32_t));
+    L.queue = take(mm * sizeof(int32_t));
+    L.ctr = take(kCtrCount * sizeof(int64_t));
+    L.bar = take(pp * sizeof(uint32_t));
+    L.fl = take(mm * nn * sizeof(double));
+    L.fu1 = take(mm * nn * sizeof(double));
+    L.fu2 = take(mm * nn * sizeof(double));
+    L.fr = take(mm * nn * sizeof(double));
+    L.fpiv = take(mm * nn);
+    L.u0n = take(mm * sizeof(double));
+    if (need_chain) {
+        L.Y = take(nn * mm * sizeof(double));
+        L.T = take(mm * mm * sizeof(double));
+        L.partS = take(pp * nn * sizeof(double));
+        L.partG = take(pp * nn * sizeof(double));
+        L.partScal = take(pp * kScalTeam * sizeof(double));
+        L.vecS = take(pp * nn * sizeof(double));
+        L.vecX = take(pp * nn * sizeof(double));
+        L.vecR = take(pp * nn * sizeof(double));
+        L.qbuf = take(pp * nn * sizeof(double));
+        if (!chain_use_smem(n)) L.gvec = take(pp * 2 * nn * sizeof(double));
+    }
+    L.total = off;
+    return L;
+}
+
+Ws bind_layout(void* base, const Layout& L, int64_t n, int64_t m, int32_t P)
+{
+    char* b = (char*)base;
+    Ws w;
+    memset(&w, 0, sizeof(w));
+    w.scal = (double*)(b + L.scal);
+    w.wp = (double*)(b + L.wp);
+    w.head = (int32_t*)(b + L.head);
+    w.clstart = (int32_t*)(b + L.clstart);
+    w.clsize = (int32_t*)(b + L.clsize);
+    w.cltoff = (int64_t*)(b + L.cltoff);
+    w.sched = (int32_t*)(b + L.sched);
+    w.queue = (int32_t*)(b + L.queue);
+    w.ctr = (int64_t*)(b + L.ctr);
+    w.bar = (uint32_t*)(b + L.bar);
+    w.fl = (double*)(b + L.fl);
+    w.fu1 = (double*)(b + L.fu1);
+    w.fu2 = (double*)(b + L.fu2);
+    w.fr = (double*)(b + L.fr);
+    w.fpiv = (uint8_t*)(b + L.fpiv);
+    w.u0n = (double*)(b + L.u0n);
+    if (L.Y) {
+        w.Y = (double*)(b + L.Y);
+        w.T = (double*)(b + L.T);
+        w.partS = (double*)(b + L.partS);
+        w.partG = (double*)(b + L.partG);
+        w.partScal = (double*)(b + L.partScal);
+        w.vecS = (double*)(b + L.vecS);
+        w.vecX = (double*)(b + L.vecX);
+        w.vecR = (double*)(b + L.vecR);
+        w.qbuf = (double*)(b + L.qbuf);
+        w.gvec = L.gvec ? (double*)(b + L.gvec) : nullptr;
+    }
+    w.P = P;
+    w.use_smem = chain_use_smem(n) ? 1 : 0;
+    return w;
+}
+
+}  // namespace tinvx
+
+using namespace tinvx;
+
+namespace {
+
+
+int cuda_code(cudaError_t e)
+{
+    if (e == cudaSuccess) return TINV_OK;
+    if (e == cudaErrorMemoryAllocation) return TINV_ENOMEM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
+        e == cudaErrorNoKernelImageForDevice || e == cudaErrorInvalidDevice)
+        return TINV_ENODEV;
+    return TINV_ECUDA;
+}
+
+bool all_finite(const double* a, int64_t k)
+{
+    for (int64_t i = 0; i < k; ++i)
+        if (!isfinite(a[i])) return false;
+    return true;
+}
+
+bool ascending(const double* a, int64_t k)
+{
+    for (int64_t i = 1; i < k; ++i)
+        if (!(a[i] >= a[i - 1])) return false;
+    return true;
+}
+
+// Device allocation that is freed on scope exit (stream-ordered when a stream is given).
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    bool async = false;
+    cudaError_t alloc(size_t bytes, cudaStream_t s, bool use_async)
+    {
+        st = s;
+        async = use_async;
+        if (bytes == 0) bytes = 256;
+        return async ? cudaMallocAsync(&p, bytes, st) : cudaMalloc(&p, bytes);
+    }
+    ~DevBuf()
+    {
+        if (!p) return;
+        if (async)
+            cudaFreeAsync(p, st);
+        else
+            cudaFree(p);
+    }
+};
+
+__global__ void k_finish(const int64_t* ctr, int64_t* info)
+{
+    const int64_t err = ctr[kCtrErr];
+    *info = err ? (int64_t)TINV_ETIMEDOUT : ctr[kCtrInfo];
+}
+
+struct Opts {
+    tinv_opts o;
+    explicit Opts(const tinv_opts* src)
+    {
+        if (src)
+            o = *src;
+        else
+            tinv_opts_default(&o);
+    }
+};
+
+// Enqueue the full inverse-iteration path on `st` for a problem whose arrays are all on the
+// device.  `ws` must hold make_layout(n, m, P, true).total bytes.
+// When phase_ms is given, CUDA events bracket each launch and the elapsed device times are
+// stored after synchronizing on the last event.
+int enqueue_tinv(const Problem& p, void* ws, int32_t P, int32_t max_team, cudaStream_t st,
+                 float* phase_ms)
+{
+    const Layout L = make_layout(p.n, p.m, P, true);
+    const Ws w = bind_layout(ws, L, p.n, p.m, P);
+    cudaEvent_t ev[5] = {};
+    cudaError_t e = cudaSuccess;
+    if (phase_ms) {
+        for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    }
+    if (e == cudaSuccess) e = launch_plan(p, w, max_team, st);
+    if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess)
+        e = launch_lu(p.n, p.d, p.e, p.m, w.wp, w.fl, w.fr, w.fu1, w.fu2, w.fpiv, w.u0n, 1, st);
+    if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[2], st);
+    if (e == cudaSuccess) e = launch_first(p, w, st);
+    if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[3], st);
+    if (e == cudaSuccess) e = launch_chain(p, w, kModeInvit, nullptr, 0, st);
+    if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[4], st);
+    if (e == cudaSuccess && phase_ms) {
+        e = cudaEventSynchronize(ev[4]);
+        for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&phase_ms[i], ev[i], ev[i + 1]);
+    }
+    for (int i = 0; i < 5; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    return cuda_code(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+void tinv_opts_default(tinv_opts* o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->method = TINV_CWY;
+}
+
+const char* tinv_strerror(int code)
+{
+    switch (code) {
+    case TINV_OK: return "success";
+    case TINV_ENOMEM: return "device memory allocation failed";
+    case TINV_ECUDA: return "CUDA runtime error";
+    case TINV_ETIMEDOUT: return "a bounded device-side wait expired";
+    case TINV_EAGAIN: return "no capacity right now; retry";
+    case TINV_ECANCELED: return "request cancelled";
+    case TINV_ENOTSUP: return "size not supported by this build";
+    case TINV_ENODEV: return "no usable sm_103 CUDA device";
+    case TINV_EWORKSPACE: return "workspace too small";
+    default: break;
+    }
+    if (code < 0) return "invalid argument";
+    return "some eigenvectors did not converge";
+}
+
+const char* tinv_version(void) { return "tinv 0.1 (sm_103a, FP64)"; }
+
+size_t tinv_workspace_size(int64_t n, int64_t m, const tinv_opts* o)
+{
+    if (n < 0 || m < 0) return 0;
+    const Opts op(o);
+    const int32_t P = chain_grid(op.o.grid_ctas);
+    return make_layout(n, m, P, true).total;
+}
+
+int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double* w, double* Z,
+            int64_t ldz, const tinv_opts* o, int64_t* ifail)
+{
+    const Opts op(o);
+    if (n < 0) return -1;
+    if (n > 0 && !d) return -2;
+    if (n > 1 && !e) return -3;
+    if (m < 0 || m > n) return -4;
+    if (m > 0 && !w) return -5;
+    if (m > 0 && !Z) return -6;
+    if (ldz < (n > 0 ? n : 1)) return -7;
+    if (op.o.method != TINV_CWY && op.o.method != TINV_MGS) return -8;
+    if (n == 0 || m == 0) return 0;
+    if (n > (int64_t)INT32_MAX / 2 || m > (int64_t)INT32_MAX / 2) return TINV_ENOTSUP;
+
+    Problem p;
+    memset(&p, 0, sizeof(p));
+    p.n = n;
+    p.m = m;
+    p.ldz = ldz;
+    p.method = op.o.method;
+    p.seed = op.o.seed;
+    p.j0 = op.o.j0;
+    const int32_t P = chain_grid(op.o.grid_ctas);
+
+    if (op.o.device_ptrs) {
+        cudaStream_t st = (cudaStream_t)op.o.stream;
+        if (n == 1) {
+            std::vector<double> ones(m, 0.0);
+            for (int64_t j = 0; j < m; ++j) {
+                const double one = 1.0;
+                cudaError_t ce = cudaMemcpyAsync(Z + j * ldz, &one, sizeof(double),
+                                                 cudaMemcpyHostToDevice, st);
+                if (ce != cudaSuccess) return cuda_code(ce);
+            }
+            cudaStreamSynchronize(st);
+            return 0;
+        }
+        p.d = d;
+        p.e = e;
+        p.w = w;
+        p.Z = Z;
+        p.iters = op.o.iters;
+        const size_t need = make_layout(n, m, P, true).total;
+        DevBuf own;
+        void* ws = op.o.workspace;
+        if (ws) {
+            if (op.o.workspace_bytes < need) return TINV_EWORKSPACE;
+        } else {
+            cudaError_t ce = own.alloc(need, st, true);
+            if (ce != cudaSuccess) return TINV_ENOMEM;
+            ws = own.p;
+        }
+        int rc = enqueue_tinv(p, ws, P, op.o.max_team, st, op.o.phase_ms);
+        if (rc != 0) return rc;
+        if (op.o.info) {
+            const Ws wsb = bind_layout(ws, make_layout(n, m, P, true), n, m, P);
+            k_finish<<<1, 1, 0, st>>>(wsb.ctr, op.o.info);
+            if (cudaGetLastError() != cudaSuccess) return TINV_ECUDA;
+        }
+        return 0;
+    }
+
+    // ---- host pointers: validate values, copy in, run, copy out ----
+    if (!all_finite(d, n) || (n > 1 && !all_finite(e, n - 1))) return -2;
+    if (!all_finite(w, m)) return -5;
+    if (!ascending(w, m)) return -5;
+    if (n == 1) {
+        for (int64_t j = 0; j < m; ++j) Z[j * ldz] = 1.0;
+        return 0;
+    }
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return TINV_ENODEV;
+    int rc = 0;
+    {
+        const Layout L = make_layout(n, m, P, true);
+        DevBuf dd, de, dw, dz, dit, ws;
+        cudaError_t ce = dd.alloc(n * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = de.alloc((n - 1) * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = dw.alloc(m * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = dz.alloc((size_t)n * m * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = dit.alloc(m * sizeof(int32_t), st, true);
+        if (ce == cudaSuccess) ce = ws.alloc(L.total, st, true);
+        if (ce != cudaSuccess) rc = TINV_ENOMEM;
+        if (!rc) {
+            ce = cudaMemcpyAsync(dd.p, d, n * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(de.p, e, (n - 1) * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(dw.p, w, m * sizeof(double), cudaMemcpyHostToDevice, st);
+            rc = cuda_code(ce);
+        }
+        if (!rc) {
+            p.d = (const double*)dd.p;
+            p.e = (const double*)de.p;
+            p.w = (const double*)dw.p;
+            p.Z = (double*)dz.p;
+            p.ldz = n;
+            p.iters = (int32_t*)dit.p;
+            rc = enqueue_tinv(p, ws.p, P, op.o.max_team, st, op.o.phase_ms);
+        }
+        int64_t ctr[kCtrCount];
+        std::vector<int32_t> its(m);
+        if (!rc) {
+            const Ws wsb = bind_layout(ws.p, L, n, m, P);
+            ce = cudaMemcpy2DAsync(Z, ldz * sizeof(double), dz.p, n * sizeof(double),
+                                   n * sizeof(double), m, cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(ctr, wsb.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(its.data(), dit.p, m * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+            rc = cuda_code(ce);
+        }
+        if (!rc) {
+            if (ctr[kCtrErr]) {
+                rc = TINV_ETIMEDOUT;
+            } else {
+                int64_t cnt = 0;
+                for (int64_t j = 0; j < m; ++j) {
+                    if (its[j] < 0) {
+                        if (ifail) ifail[cnt] = j;
+                        ++cnt;
+                    }
+                }
+                if (op.o.iters)
+                    for (int64_t j = 0; j < m; ++j) op.o.iters[j] = its[j];
+                rc = (int)cnt;
+            }
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return rc;
+}
+
+int tinv(int64_t n, const double* d, const double* e, const double* w, double* Z)
+{
+    return tinv_ex(n, d, e, n, w, Z, n > 0 ? n : 1, nullptr, nullptr);
+}
+
+int tinv_plan(int64_t n, const double* d, const double* e, int64_t m, const double* w,
+              double* wp, int32_t* head, double* scal, const tinv_opts* o)
+{
+    const Opts op(o);
+    if (n < 1) return -1;
+    if (!d) return -2;
+    if (n > 1 && !e) return -3;
+    if (m < 0 || m > n) return -4;
+    if (m > 0 && !w) return -5;
+    if (m > 0 && !wp) return -6;
+    if (m > 0 && !head) return -7;
+    if (!scal) return -8;
+    const int32_t P = chain_grid(op.o.grid_ctas);
+    const Layout L = make_layout(n, m, P, false);
+    Problem p;
+    memset(&p, 0, sizeof(p));
+    p.n = n;
+    p.m = m;
+    p.method = op.o.method;
+    cudaStream_t st = op.o.device_ptrs ? (cudaStream_t)op.o.stream : nullptr;
+    bool own_stream = false;
+    if (!op.o.device_ptrs) {
+        if (!all_finite(d, n) || (n > 1 && !all_finite(e, n - 1))) return -2;
+        if (!all_finite(w, m) || !ascending(w, m)) return -5;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return TINV_ENODEV;
+        own_stream = true;
+    }
+    int rc = 0;
+    {
+        DevBuf ws, dd, de, dw;
+        cudaError_t ce = ws.alloc(L.total, st, true);
+        if (ce == cudaSuccess && !op.o.device_ptrs) {
+            ce = dd.alloc(n * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = de.alloc((n > 1 ? n - 1 : 1) * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = dw.alloc((m > 0 ? m : 1) * sizeof(double), st, true);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(dd.p, d, n * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess && n > 1)
+                ce = cudaMemcpyAsync(de.p, e, (n - 1) * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess && m > 0)
+                ce = cudaMemcpyAsync(dw.p, w, m * sizeof(double), cudaMemcpyHostToDevice, st);
+            p.d = (const double*)dd.p;
+            p.e = (const double*)de.p;
+            p.w = (const double*)dw.p;
+        } else {
+            p.d = d;
+            p.e = e;
+            p.w = w;
+        }
+        rc = cuda_code(ce);
+        const Ws wsb = bind_layout(ws.p, L, n, m, P);
+        if (!rc) rc = cuda_code(launch_plan(p, wsb, 0, st));
+        if (!rc) {
+            const cudaMemcpyKind k = op.o.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            ce = cudaMemcpyAsync(scal, wsb.scal, 3 * sizeof(double), k, st);
+            if (ce == cudaSuccess && m > 0) ce = cudaMemcpyAsync(wp, wsb.wp, m * sizeof(double), k, st);
+            if (ce == cudaSuccess && m > 0)
+                ce = cudaMemcpyAsync(head, wsb.head, m * sizeof(int32_t), k, st);
+            if (ce == cudaSuccess && !op.o.device_ptrs) ce = cudaStreamSynchronize(st);
+            rc = cuda_code(ce);
+        }
+    }
+    if (own_stream) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    return rc;
+}
+
+int tinv_lu(int64_t n, const double* d, const double* e, int64_t m, const double* s, double* l,
+            double* u0, double* u1, double* u2, uint8_t* piv, const tinv_opts* o)
+{
+    const Opts op(o);
+    if (n < 1) return -1;
+    if (!d) return -2;
+    if (n > 1 && !e) return -3;
+    if (m < 0) return -4;
+    if (m > 0 && !s) return -5;
+    if (m > 0 && (!l || !u0 || !u1 || !u2 || !piv)) return -6;
+    if (m == 0) return 0;
+    if (op.o.device_ptrs) {
+        cudaStream_t st = (cudaStream_t)op.o.stream;
+        return cuda_code(launch_lu(n, d, e, m, s, l, u0, u1, u2, piv, nullptr, 0, st));
+    }
+    if (!all_finite(d, n) || (n > 1 && !all_finite(e, n - 1))) return -2;
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return TINV_ENODEV;
+    int rc = 0;
+    {
+        const size_t mn = (size_t)m * (size_t)n;
+        DevBuf dd, de, ds, dl, d0, d1, d2, dp;
+        cudaError_t ce = dd.alloc(n * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = de.alloc((n > 1 ? n - 1 : 1) * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = ds.alloc(m * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = dl.alloc(mn * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = d0.alloc(mn * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = d1.alloc(mn * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = d2.alloc(mn * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = dp.alloc(mn, st, true);
+        if (ce != cudaSuccess) rc = TINV_ENOMEM;
+        if (!rc) {
+            ce = cudaMemcpyAsync(dd.p, d, n * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess && n > 1)
+                ce = cudaMemcpyAsync(de.p, e, (n - 1) * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(ds.p, s, m * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess)
+                ce = launch_lu(n, (double*)dd.p, (double*)de.p, m, (double*)ds.p, (double*)dl.p,
+                               (double*)d0.p, (double*)d1.p, (double*)d2.p, (uint8_t*)dp.p, nullptr,
+                               0, st);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(l, dl.p, mn * sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(u0, d0.p, mn * sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(u1, d1.p, mn * sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(u2, d2.p, mn * sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(piv, dp.p, mn, cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+            rc = cuda_code(ce);
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return rc;
+}
+
+int tinv_solve(int64_t n, const double* d, const double* e, int64_t m, const double* s,
+               double* X, int64_t ldx, int32_t scale, const tinv_opts* o)
+{
+    const Opts op(o);
+    if (n < 1) return -1;
+    if (!d) return -2;
+    if (n > 1 && !e) return -3;
+    if (m < 0) return -4;
+    if (m > 0 && !s) return -5;
+    if (m > 0 && !X) return -6;
+    if (ldx < n) return -7;
+    if (m == 0) return 0;
+    const int32_t P = chain_grid(op.o.grid_ctas);
+    const Layout L = make_layout(n, m, P, false);
+    Problem p;
+    memset(&p, 0, sizeof(p));
+    p.n = n;
+    p.m = m;
+    cudaStream_t st = op.o.device_ptrs ? (cudaStream_t)op.o.stream : nullptr;
+    bool own_stream = false;
+    if (!op.o.device_ptrs) {
+        if (!all_finite(d, n) || (n > 1 && !all_finite(e, n - 1))) return -2;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return TINV_ENODEV;
+        own_stream = true;
+    }
+    int rc = 0;
+    {
+        DevBuf ws, dd, de, ds, dx;
+        cudaError_t ce = ws.alloc(L.total, st, true);
+        double* X_dev = X;
+        int64_t ldx_dev = ldx;
+        if (ce == cudaSuccess && !op.o.device_ptrs) {
+            ce = dd.alloc(n * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = de.alloc((n > 1 ? n - 1 : 1) * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = ds.alloc(m * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = dx.alloc((size_t)n * m * sizeof(double), st, true);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(dd.p, d, n * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess && n > 1)
+                ce = cudaMemcpyAsync(de.p, e, (n - 1) * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(ds.p, s, m * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpy2DAsync(dx.p, n * sizeof(double), X, ldx * sizeof(double),
+                                       n * sizeof(double), m, cudaMemcpyHostToDevice, st);
+            p.d = (const double*)dd.p;
+            p.e = (const double*)de.p;
+            X_dev = (double*)dx.p;
+            ldx_dev = n;
+            p.w = (const double*)ds.p;
+        } else {
+            p.d = d;
+            p.e = e;
+            p.w = s;
+        }
+        rc = cuda_code(ce);
+        const Ws wsb = bind_layout(ws.p, L, n, m, P);
+        if (!rc) rc = cuda_code(launch_norm(p, wsb, st));
+        if (!rc)
+            rc = cuda_code(launch_lu(n, p.d, p.e, m, p.w, wsb.fl, wsb.fr, wsb.fu1, wsb.fu2, wsb.fpiv,
+                                     wsb.u0n, 1, st));
+        if (!rc) rc = cuda_code(launch_solve_rhs(n, m, wsb, X_dev, ldx_dev, scale, st));
+        if (!rc && !op.o.device_ptrs) {
+            ce = cudaMemcpy2DAsync(X, ldx * sizeof(double), X_dev, n * sizeof(double),
+                                   n * sizeof(double), m, cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+            rc = cuda_code(ce);
+        }
+    }
+    if (own_stream) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    return rc;
+}
+
+int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int64_t ldq,
+              double* Y, double* T, const tinv_opts* o)
+{
+    const Opts op(o);
+    if (n < 1) return -1;
+    if (m < 0 || m > n) return -2;
+    if (m > 0 && !V) return -3;
+    if (ldv < n) return -4;
+    if (m > 0 && !Q) return -5;
+    if (ldq < n) return -6;
+    if (op.o.method != TINV_CWY && op.o.method != TINV_MGS) return -9;
+    if (m == 0) return 0;
+    int32_t P = chain_grid(op.o.grid_ctas);
+    const Layout L = make_layout(n, m, P, true);
+    Problem p;
+    memset(&p, 0, sizeof(p));
+    p.n = n;
+    p.m = m;
+    p.method = op.o.method;
+    cudaStream_t st = op.o.device_ptrs ? (cudaStream_t)op.o.stream : nullptr;
+    bool own_stream = false;
+    if (!op.o.device_ptrs) {
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return TINV_ENODEV;
+        own_stream = true;
+    }
+    int rc = 0;
+    {
+        DevBuf ws, dv, dq;
+        cudaError_t ce = ws.alloc(L.total, st, true);
+        const double* V_dev = V;
+        int64_t ldv_dev = ldv;
+        if (ce == cudaSuccess && !op.o.device_ptrs) {
+            ce = dv.alloc((size_t)n * m * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = dq.alloc((size_t)n * m * sizeof(double), st, true);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpy2DAsync(dv.p, n * sizeof(double), V, ldv * sizeof(double),
+                                       n * sizeof(double), m, cudaMemcpyHostToDevice, st);
+            V_dev = (const double*)dv.p;
+            ldv_dev = n;
+            p.Z = (double*)dq.p;
+            p.ldz = n;
+        } else {
+            p.Z = Q;
+            p.ldz = ldq;
+        }
+        rc = cuda_code(ce);
+        Ws wsb = bind_layout(ws.p, L, n, m, P);
+        // team size for one cluster of m columns: at most n/16 CTAs
+        const int32_t g = (int32_t)((n / 16 < (int64_t)P) ? (n / 16) : P);
+        if (g >= 2 && op.o.method == TINV_CWY) {
+            wsb.P = g;
+        } else {
+            wsb.P = 1;
+        }
+        if (op.o.max_team > 0 && wsb.P > op.o.max_team) wsb.P = op.o.max_team;
+        if (wsb.P < 1) wsb.P = 1;
+        if (!rc) rc = cuda_code(launch_orth_plan(m, wsb, p.method, st));
+        if (!rc) rc = cuda_code(launch_chain(p, wsb, kModeOrth, V_dev, ldv_dev, st));
+        const cudaMemcpyKind k = op.o.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (!rc && !op.o.device_ptrs) {
+            ce = cudaMemcpy2DAsync(Q, ldq * sizeof(double), p.Z, n * sizeof(double),
+                                   n * sizeof(double), m, cudaMemcpyDeviceToHost, st);
+            rc = cuda_code(ce);
+        }
+        if (!rc && Y && op.o.method == TINV_CWY)
+            rc = cuda_code(cudaMemcpyAsync(Y, wsb.Y, (size_t)n * m * sizeof(double), k, st));
+        if (!rc && T && op.o.method == TINV_CWY)
+            rc = cuda_code(cudaMemcpyAsync(T, wsb.T, (size_t)m * m * sizeof(double), k, st));
+        if (!rc && !op.o.device_ptrs) {
+            int64_t ctr[kCtrCount];
+            ce = cudaMemcpyAsync(ctr, wsb.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+            rc = cuda_code(ce);
+            if (!rc && ctr[kCtrErr]) rc = TINV_ETIMEDOUT;
+        }
+    }
+    if (own_stream) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,1005 @@
+// tinv_kernels.cu -- sm_103a kernels of libtinv.
+//
+//   k_plan   : ||T||_1, cluster tolerance, DSTEIN shift perturbation, Peters-Wilkinson cluster
+//              heads (Sec. 2.1; Alg. 4 lines 8-9, 17-18), cluster list, T offsets and the
+//              assignment of clusters to CTA teams of the persistent kernel.
+//   k_lu     : one thread per shift: LU with scaled partial pivoting of T - s_j I (Eq. 1).
+//   k_first  : one warp per eigenvalue: random start, DSTEIN scaling and the chunked solve; full
+//              sweep loop + normalization for cluster heads and singletons (Alg. 1 / Alg. 4
+//              without reorthogonalization), first sweep only for the other cluster members.
+//   k_chain  : persistent cooperative kernel: each cluster's members in order (Alg. 4 j-loop),
+//              with the compact-WY update of Sec. 3.3.2 spread over a team of CTAs (or MGS,
+//              Alg. 1, on one CTA per cluster).
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include "tinv_device.cuh"
+
+namespace tinvx {
+
+// ==========================================================================================
+// Plan
+// ==========================================================================================
+
+// Inclusive block scans over blockDim (multiple of 32) values; sred >= 33 entries.
+template <typename TV, class Op>
+__device__ TV block_scan_incl(TV v, TV* sred, Op op, TV ident, TV* total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        TV u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v = op(u, v);
+    }
+    __syncthreads();
+    if (lane == 31) sred[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        TV s = lane < nw ? sred[lane] : ident;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            TV u = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s = op(u, s);
+        }
+        sred[lane] = s;  // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    if (wid > 0) v = op(sred[wid - 1], v);
+    *total = sred[nw - 1];
+    __syncthreads();
+    return v;
+}
+
+struct OpMax {
+    template <typename T>
+    __device__ T operator()(T a, T b) const { return a > b ? a : b; }
+};
+struct OpAdd {
+    template <typename T>
+    __device__ T operator()(T a, T b) const { return a + b; }
+};
+
+__device__ __forceinline__ bool new_cluster(const double* wp, int64_t j, double ortol)
+{
+    return j == 0 || fabs(__dsub_rn(wp[j], wp[j - 1])) > ortol;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan(Problem p, Ws w, int32_t max_team,
+                                                       int32_t norm_only)
+{
+    __shared__ double sredd[33];
+    __shared__ int32_t sredi[33];
+    __shared__ int64_t sredl[33];
+    __shared__ int s_tight;
+    const int t = threadIdx.x, B = blockDim.x;
+    const int64_t n = p.n, m = p.m;
+
+    // ||T||_1 = max_i (|d_i| + |e_{i-1}|) + |e_i|   (added in this order, as the oracle)
+    double loc = 0.0;
+    for (int64_t i = t; i < n; i += B) {
+        double s = fabs(p.d[i]);
+        if (i > 0) s = __dadd_rn(s, fabs(p.e[i - 1]));
+        if (i < n - 1) s = __dadd_rn(s, fabs(p.e[i]));
+        loc = fmax(loc, s);
+    }
+    const double onenrm = block_max(loc, sredd);
+    const double ortol = __dmul_rn(1e-3, onenrm);
+    const double dtpcrt = __dsqrt_rn(__ddiv_rn(0.1, (double)n));
+    if (t == 0) {
+        w.scal[0] = onenrm;
+        w.scal[1] = ortol;
+        w.scal[2] = dtpcrt;
+        w.scal[3] = 0.0;
+        for (int c = 0; c < kCtrCount; ++c) w.ctr[c] = 0;
+        s_tight = 0;
+    }
+    for (int b = t; b < w.P; b += B) w.bar[b] = 0u;
+    if (norm_only) return;
+    __syncthreads();
+
+    // Shift perturbation (DSTEIN): if w_j - w'_{j-1} < 10 eps |w_j| then
+    // w'_j = w'_{j-1} + 10 eps |w_j|.  Without any such pair w' = w; otherwise one thread scans.
+    for (int64_t j = 1 + t; j < m; j += B) {
+        const double xj = p.w[j];
+        const double pertol = __dmul_rn(10.0, fabs(__dmul_rn(kEps, xj)));
+        if (__dsub_rn(xj, p.w[j - 1]) < pertol) s_tight = 1;
+    }
+    __syncthreads();
+    if (s_tight == 0) {
+        for (int64_t j = t; j < m; j += B) w.wp[j] = p.w[j];
+    } else if (t == 0) {
+        double xjm = 0.0;
+        for (int64_t j = 0; j < m; ++j) {
+            double xj = p.w[j];
+            if (j > 0) {
+                const double pertol = __dmul_rn(10.0, fabs(__dmul_rn(kEps, xj)));
+                if (__dsub_rn(xj, xjm) < pertol) xj = __dadd_rn(xjm, pertol);
+            }
+            w.wp[j] = xj;
+            xjm = xj;
+        }
+    }
+    __syncthreads();
+
+    // Cluster heads (max-scan of head positions) and the list of clusters with >= 2 members:
+    // a start is a head whose successor continues its cluster, an end is a member whose
+    // successor is a head (or the last index); starts and ends pair up in order.
+    int32_t carry_head = 0, carry_cnt = 0, carry_end = 0;
+    for (int64_t base = 0; base < m; base += B) {
+        const int64_t j = base + t;
+        const bool in = j < m;
+        const bool fj = in && new_cluster(w.wp, j, ortol);
+        const bool fj1 = in && (j + 1 < m) && new_cluster(w.wp, j + 1, ortol);
+        const bool is_start = fj && (j + 1 < m) && !fj1;
+        const bool is_end = in && !fj && (j + 1 == m || fj1);
+        int32_t tot, tot2, tot3;
+        int32_t hd = block_scan_incl<int32_t>(fj ? (int32_t)j : 0, sredi, OpMax(), 0, &tot);
+        hd = max(hd, carry_head);
+        const int32_t cs = block_scan_incl<int32_t>(is_start ? 1 : 0, sredi, OpAdd(), 0, &tot2);
+        const int32_t ce = block_scan_incl<int32_t>(is_end ? 1 : 0, sredi, OpAdd(), 0, &tot3);
+        if (in) w.head[j] = hd;
+        if (is_start) w.clstart[carry_cnt + cs - 1] = (int32_t)j;
+        if (is_end) w.clsize[carry_end + ce - 1] = (int32_t)(j - hd + 1);
+        carry_head = max(carry_head, tot);
+        carry_cnt += tot2;
+        carry_end += tot3;
+        __syncthreads();
+    }
+    const int32_t K = carry_cnt;
+    __syncthreads();
+    // T offsets: exclusive prefix sum of size^2
+    int64_t carry_off = 0;
+    for (int64_t base = 0; base < K; base += B) {
+        const int64_t c = base + t;
+        const int64_t sz = (c < K) ? (int64_t)w.clsize[c] : 0;
+        int64_t tot;
+        int64_t inc = block_scan_incl<int64_t>(sz * sz, sredl, OpAdd(), (int64_t)0, &tot);
+        if (c < K) w.cltoff[c] = carry_off + inc - sz * sz;
+        carry_off += tot;
+        __syncthreads();
+    }
+    if (t == 0) {
+        w.ctr[kCtrNClust] = K;
+        w.ctr[kCtrTSize] = carry_off;
+    }
+
+    // Team schedule (one thread): clusters whose share of the work (~ m_c^2) is worth >= 2 CTAs
+    // get a contiguous team of CTAs; the rest form a queue served by single CTAs.  CTAs that
+    // finish their team's cluster join the queue.
+    if (t == 0) {
+        const int32_t P = w.P;
+        for (int32_t b = 0; b < P; ++b) {
+            w.sched[4 * b + 0] = b;
+            w.sched[4 * b + 1] = 1;
+            w.sched[4 * b + 2] = 0;
+            w.sched[4 * b + 3] = -1;
+        }
+        int32_t nq = 0;
+        if (p.method != 0 || K == 0) {
+            for (int32_t c = 0; c < K; ++c) w.queue[nq++] = c;
+        } else {
+            double wtot = 0.0;
+            for (int32_t c = 0; c < K; ++c) wtot += (double)w.clsize[c] * (double)w.clsize[c];
+            int32_t gmax = (int32_t)min((int64_t)P, max((int64_t)1, n / 16));
+            if (max_team > 0) gmax = min(gmax, max_team);
+            double wq = 0.0, wteam = 0.0;
+            for (int32_t c = 0; c < K; ++c) {
+                const double wc = (double)w.clsize[c] * (double)w.clsize[c];
+                if (floor(P * wc / wtot) >= 2.0 && gmax >= 2)
+                    wteam += wc;
+                else
+                    wq += wc;
+            }
+            int32_t Q = 0;
+            if (wq > 0.0) Q = max(1, (int32_t)llrint(P * wq / wtot));
+            const int32_t Pteam = max(0, P - Q);
+            int32_t next = 0;
+            for (int32_t c = 0; c < K; ++c) {
+                const double wc = (double)w.clsize[c] * (double)w.clsize[c];
+                int32_t g = 0;
+                if (floor(P * wc / wtot) >= 2.0 && gmax >= 2 && wteam > 0.0)
+                    g = min(gmax, (int32_t)floor(Pteam * wc / wteam));
+                if (g >= 2 && next + g <= Pteam) {
+                    for (int32_t r = 0; r < g; ++r) {
+                        const int32_t b = next + r;
+                        w.sched[4 * b + 0] = next;
+                        w.sched[4 * b + 1] = g;
+                        w.sched[4 * b + 2] = r;
+                        w.sched[4 * b + 3] = c;
+                    }
+                    next += g;
+                } else {
+                    w.queue[nq++] = c;
+                }
+            }
+        }
+        w.ctr[kCtrNQueue] = nq;
+        w.ctr[kCtrQHead] = 0;
+    }
+}
+
+// Plan for stand-alone orthogonalization: one cluster made of all m columns.
+__global__ void k_orth_plan(int64_t m, Ws w, int32_t method)
+{
+    const int t = threadIdx.x;
+    for (int b = t; b < w.P; b += blockDim.x) {
+        w.bar[b] = 0u;
+        w.sched[4 * b + 0] = b;
+        w.sched[4 * b + 1] = 1;
+        w.sched[4 * b + 2] = 0;
+        w.sched[4 * b + 3] = -1;
+    }
+    if (t == 0) {
+        for (int c = 0; c < kCtrCount; ++c) w.ctr[c] = 0;
+        w.clstart[0] = 0;
+        w.clsize[0] = (int32_t)m;
+        w.cltoff[0] = 0;
+        w.ctr[kCtrNClust] = 1;
+        w.ctr[kCtrTSize] = m * m;
+        w.scal[0] = w.scal[1] = w.scal[2] = w.scal[3] = 0.0;
+    }
+    __syncthreads();
+    if (t == 0) {
+        if (method == 0 && w.P >= 2) {
+            const int32_t g = w.P;
+            for (int32_t r = 0; r < g; ++r) {
+                w.sched[4 * r + 0] = 0;
+                w.sched[4 * r + 1] = g;
+                w.sched[4 * r + 2] = r;
+                w.sched[4 * r + 3] = 0;
+            }
+            w.ctr[kCtrNQueue] = 0;
+        } else {
+            w.queue[0] = 0;
+            w.ctr[kCtrNQueue] = 1;
+        }
+    }
+}
+
+// ==========================================================================================
+// LU of T - s I with scaled partial pivoting, one thread per shift (bit-exact: explicit
+// round-to-nearest operations, no contraction).  Row j of each output holds shift j.
+// ==========================================================================================
+__global__ void k_lu(int64_t n, const double* __restrict__ d, const double* __restrict__ e,
+                     int64_t m, const double* __restrict__ shift, double* __restrict__ L,
+                     double* __restrict__ U0, double* __restrict__ U1, double* __restrict__ U2,
+                     uint8_t* __restrict__ PV, double* __restrict__ u0n, int store_reciprocal)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const double lam = shift[j];
+    const size_t base = (size_t)j * (size_t)n;
+    double* l = L + base;
+    double* u0 = U0 + base;
+    double* u1 = U1 + base;
+    double* u2 = U2 + base;
+    uint8_t* pv = PV + base;
+    double ak = __dsub_rn(d[0], lam);
+    double bk = (n > 1) ? e[0] : 0.0;
+    double umax = 0.0;
+    for (int64_t k = 0; k + 1 < n; ++k) {
+        const double ck = e[k];
+        const double a1 = __dsub_rn(d[k + 1], lam);
+        const double b1 = (k + 2 < n) ? e[k + 1] : 0.0;
+        const double scale1 = __dadd_rn(fabs(ak), fabs(bk));
+        const double scale2 = __dadd_rn(__dadd_rn(fabs(ck), fabs(a1)), fabs(b1));
+        const double piv1 = (ak == 0.0) ? 0.0 : __ddiv_rn(fabs(ak), scale1);
+        const double piv2 = (ck == 0.0) ? 0.0 : __ddiv_rn(fabs(ck), scale2);
+        double lk, w0, w1, w2;
+        uint8_t sw;
+        if (piv2 <= piv1) {
+            lk = (ck == 0.0) ? 0.0 : __ddiv_rn(ck, ak);
+            w0 = ak;
+            w1 = bk;
+            w2 = 0.0;
+            sw = 0;
+            ak = __dsub_rn(a1, __dmul_rn(lk, bk));
+            bk = b1;
+        } else {
+            lk = __ddiv_rn(ak, ck);
+            w0 = ck;
+            w1 = a1;
+            w2 = b1;
+            sw = 1;
+            ak = __dsub_rn(bk, __dmul_rn(lk, a1));
+            bk = -__dmul_rn(lk, b1);
+        }
+        l[k] = lk;
+        u0[k] = w0;
+        u1[k] = w1;
+        u2[k] = w2;
+        pv[k] = sw;
+        umax = fmax(umax, fmax(fabs(w0), fmax(fabs(w1), fabs(w2))));
+    }
+    u0[n - 1] = ak;
+    l[n - 1] = 0.0;
+    u1[n - 1] = 0.0;
+    u2[n - 1] = 0.0;
+    pv[n - 1] = 0;
+    umax = fmax(umax, fabs(ak));
+    if (u0n) u0n[j] = fabs(ak);
+    if (store_reciprocal) {
+        // tiny pivots: |u0_k| < tol = eps * max|U| -> sign(u0_k) * tol (sign(0) = +)
+        double tol = __dmul_rn(kEps, umax);
+        if (tol == 0.0) tol = kEps;
+        for (int64_t k = 0; k < n; ++k) {
+            double a = u0[k];
+            if (fabs(a) < tol) a = (a >= 0.0) ? tol : -tol;
+            u0[k] = __drcp_rn(a);
+        }
+    }
+}
+
+// ==========================================================================================
+// One warp per eigenvalue: start vector, DSTEIN scaling, chunked solve, convergence test and
+// normalization (cluster heads and singletons); cluster members get their first solve only.
+// ==========================================================================================
+__device__ __forceinline__ Fac fac_of(const Ws& w, int64_t j, int64_t n)
+{
+    const size_t base = (size_t)j * (size_t)n;
+    Fac f;
+    f.l = w.fl + base;
+    f.u1 = w.fu1 + base;
+    f.u2 = w.fu2 + base;
+    f.r = w.fr + base;
+    f.piv = w.fpiv + base;
+    return f;
+}
+
+__device__ void warp_scale(int64_t n, double* x, double onenrm, double u0n, int lane)
+{
+    double as = 0.0;
+    for (int64_t i = lane; i < n; i += 32) as += fabs(x[i]);
+    as = warp_sum(as);
+    const double scl = ((double)n * onenrm) * fmax(kEps, u0n) / as;
+    __syncwarp();
+    for (int64_t i = lane; i < n; i += 32) x[i] *= scl;
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kFirstWarps * 32) k_first(Problem p, Ws w)
+{
+    __shared__ double sh_all[kFirstWarps][8 * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * kFirstWarps + warp;
+    if (j >= p.m) return;
+    double* sh = sh_all[warp];
+    const int64_t n = p.n;
+    double* x = p.Z + j * p.ldz;
+    const Fac f = fac_of(w, j, n);
+    const double onenrm = w.scal[0], dtpcrt = w.scal[2], u0n = w.u0n[j];
+    const bool is_head = (w.head[j] == (int32_t)j);
+    const uint64_t key = start_key(p.seed, p.j0 + j, 0);
+    for (int64_t i = lane; i < n; i += 32) x[i] = start_value(key, i);
+    __syncwarp();
+    const int maxits = is_head ? kMaxIts : 1;
+    int nrmchk = 0, its = 0;
+    bool conv = false;
+    while (its < maxits) {
+        ++its;
+        warp_scale(n, x, onenrm, u0n, lane);
+        chunk_solve(n, f, x, sh, lane, 32, WarpSync());
+        if (!is_head) break;
+        double mx = 0.0;
+        for (int64_t i = lane; i < n; i += 32) mx = fmax(mx, fabs(x[i]));
+        mx = warp_max(mx);
+        if (mx >= dtpcrt && ++nrmchk >= kExtra + 1) {
+            conv = true;
+            break;
+        }
+    }
+    if (!is_head) return;
+    // normalize; the first entry of largest magnitude becomes positive
+    double ss = 0.0, am = -1.0;
+    int64_t ai = 0;
+    for (int64_t i = lane; i < n; i += 32) {
+        const double v = x[i];
+        ss = fma(v, v, ss);
+        if (fabs(v) > am) {
+            am = fabs(v);
+            ai = i;
+        }
+    }
+    ss = warp_sum(ss);
+    warp_argmax(am, ai);
+    double s = 1.0 / sqrt(ss);
+    if (x[ai] < 0.0) s = -s;
+    __syncwarp();
+    for (int64_t i = lane; i < n; i += 32) x[i] *= s;
+    if (lane == 0) {
+        if (p.iters) p.iters[j] = conv ? its : -its;
+        if (!conv) atomicAdd((unsigned long long*)&w.ctr[kCtrInfo], 1ull);
+    }
+}
+
+// Solve for given right-hand sides (tinv_solve): one warp per column.
+__global__ void __launch_bounds__(kFirstWarps * 32) k_solve_rhs(int64_t n, int64_t m, Ws w,
+                                                                double* X, int64_t ldx, int scale)
+{
+    __shared__ double sh_all[kFirstWarps][8 * 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * kFirstWarps + warp;
+    if (j >= m) return;
+    double* x = X + j * ldx;
+    if (scale) warp_scale(n, x, w.scal[0], w.u0n[j], lane);
+    chunk_solve(n, fac_of(w, j, n), x, sh_all[warp], lane, 32, WarpSync());
+}
+
+// ==========================================================================================
+// Persistent cluster kernel
+// ==========================================================================================
+struct Team {
+    int32_t leader, G, rank;
+    uint32_t* bar;
+    uint32_t target;
+};
+
+struct ChainCtx {
+    Problem p;
+    Ws w;
+    int32_t mode;
+    const double* V;
+    int64_t ldv;
+    double* vsm;   // [n] working vector (shared or global)
+    double* s1;    // [n] staging vector (shared or global)
+    double* red;   // [2048] reduction / solve scratch (shared)
+    int* err;
+};
+
+__device__ __forceinline__ int64_t part_lo(int64_t a, int64_t b, int r, int G)
+{
+    return a + ((b - a) * r) / G;
+}
+
+// Split [0, k) so that column i of an upper-triangular matrix (work i+1) is balanced.
+__device__ __forceinline__ int64_t tri_col_lo(int64_t k, int r, int G)
+{
+    if (r <= 0) return 0;
+    if (r >= G) return k;
+    return min(k, (int64_t)llrint((double)k * sqrt((double)r / (double)G)));
+}
+// Split [0, k) so that row i of an upper-triangular matrix (work k-i) is balanced.
+__device__ __forceinline__ int64_t tri_row_lo(int64_t k, int r, int G)
+{
+    if (r <= 0) return 0;
+    if (r >= G) return k;
+    return max((int64_t)0, k - (int64_t)llrint((double)k * sqrt(1.0 - (double)r / (double)G)));
+}
+
+__device__ __forceinline__ int solve_group_size(int64_t n)
+{
+    int P = (int)ceil(sqrt(2.0 * (double)n));
+    P = ((P + 31) / 32) * 32;
+    return max(32, min(256, P));
+}
+
+// Team-wide order statistics of pass C (per CTA: sum|q|, max|q|, argmax, sum q^2).
+struct QStats {
+    double asum, amax, sumsq;
+    int64_t arg;
+};
+
+// ---- compact-WY processing of one cluster by a team (Alg. 4, Sec. 3.3.2) -----------------
+__device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
+{
+    const Problem& p = cx.p;
+    const Ws& w = cx.w;
+    const int64_t n = p.n;
+    const int t = threadIdx.x;
+    const int B = blockDim.x;
+    const int G = tm.G, rank = tm.rank, leader = tm.leader;
+    const int64_t s0 = w.clstart[c];
+    const int64_t mc = w.clsize[c];
+    double* Tc = w.T + w.cltoff[c];
+    const int64_t ldt = mc;
+    double* Yc = w.Y + (size_t)s0 * (size_t)n;
+    double* vecS = w.vecS + (size_t)leader * n;
+    double* vecX = w.vecX + (size_t)leader * n;
+    double* vecR = w.vecR + (size_t)leader * n;
+    double* qbuf = w.qbuf + (size_t)leader * n;
+    double* myS = w.partS + (size_t)(leader + rank) * n;
+    double* myG = w.partG + (size_t)(leader + rank) * n;
+    double* scal_t = w.partScal + (size_t)leader * kScalTeam;  // rank r at + r*kScalTeam
+    double* vsm = cx.vsm;
+    double* s1 = cx.s1;
+    double* red = cx.red;
+    const double onenrm = w.scal[0], dtpcrt = w.scal[2];
+    const bool orth = (cx.mode == kModeOrth);
+    __shared__ double s_b[8];
+    __shared__ int64_t s_arg;
+
+    // rows of passes A and C and of the head step
+    const int64_t ra0 = part_lo(0, n, rank, G), ra1 = part_lo(0, n, rank + 1, G);
+
+    int64_t kstart = 0;
+    if (!orth) {
+        // Alg. 4 lines 10-12: Y_1 = [y_1], T_1 = [t_1] from the final head vector z.
+        const double* z = p.Z + s0 * p.ldz;
+        double ss = 0.0;
+        for (int64_t r = ra0 + t; r < ra1; r += B) ss = fma(z[r], z[r], ss);
+        ss = block_sum(ss, red);
+        if (t == 0) scal_t[rank * kScalTeam + 6] = ss;
+        if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+        if (t == 0) {
+            double tot = 0.0;
+            for (int r = 0; r < G; ++r) tot += __ldcg(&scal_t[r * kScalTeam + 6]);
+            const double nrm = sqrt(tot);
+            const double z0 = z[0];
+            const bool broke = !(nrm > 0.0) || !isfinite(nrm);
+            const double cc = broke ? -1.0 : -sgn(z0) * nrm;
+            const double u11 = broke ? 1.0 : z0;
+            s_b[0] = cc;
+            s_b[1] = 1.0 / (cc * cc - u11 * cc);
+            s_b[2] = broke ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        const double cc = s_b[0];
+        const bool broke = s_b[2] != 0.0;
+        for (int64_t r = ra0 + t; r < ra1; r += B) {
+            double y = broke ? 0.0 : z[r];
+            if (r == 0) y = broke ? 2.0 : z[0] - cc;
+            Yc[r] = y;
+        }
+        if (rank == 0 && t == 0) Tc[0] = s_b[1];
+        kstart = 1;
+        // Y[:,0] and T[0,0] must be complete before members stage rows of Y
+        if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+    }
+
+    for (int64_t kk = kstart; kk < mc; ++kk) {
+        const int64_t j = s0 + kk;
+        const int64_t k = kk;  // previous reflectors: columns 0..k-1 of Yc
+        // stage r = row k of Y_k into vecR (spread over the team)
+        for (int64_t l = (int64_t)rank * B + t; l < k; l += (int64_t)G * B) vecR[l] = Yc[k + l * n];
+        const Fac f = orth ? Fac{} : fac_of(w, j, n);
+        const double u0n = orth ? 0.0 : w.u0n[j];
+        int nrmchk = 0, its = 0;
+        bool conv = false;
+        double fac_next = 0.0;
+        const int maxits = orth ? 1 : kMaxIts;
+        while (its < maxits) {
+            ++its;
+            // ---- the iterate v (full vector in every CTA of the team) ----
+            if (orth) {
+                for (int64_t r = t; r < n; r += B) vsm[r] = cx.V[r + kk * cx.ldv];
+                __syncthreads();
+            } else if (its == 1) {
+                for (int64_t r = t; r < n; r += B) vsm[r] = p.Z[r + j * p.ldz];
+                __syncthreads();
+            } else {
+                for (int64_t r = t; r < n; r += B) vsm[r] = __ldcg(&qbuf[r]) * fac_next;
+                __syncthreads();
+                chunk_solve(n, f, vsm, red, t, solve_group_size(n), CtaSync());
+            }
+            if (k > 0) {
+                // ---- pass A: s = Y_k^T v = L_k^T v_check + Yhat_k^T v_hat (team partials) ----
+                cta_coldots<kLower>(Yc, n, 0, k, ra0, ra1, vsm, red,
+                                    [&](int64_t i, double s) { myS[i] = s; });
+                if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+                // ---- s' = T_k^T s, columns split over the team ----
+                const int64_t c0 = tri_col_lo(k, rank, G), c1 = tri_col_lo(k, rank + 1, G);
+                for (int64_t l = t; l < c1; l += B) {
+                    double a = 0.0;
+                    for (int r = 0; r < G; ++r) a += __ldcg(&w.partS[(size_t)(leader + r) * n + l]);
+                    s1[l] = a;
+                }
+                __syncthreads();
+                cta_coldots<kUpper>(Tc, ldt, c0, c1, 0, k, s1, red,
+                                    [&](int64_t i, double s) { vecS[i] = s; });
+                if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+                for (int64_t l = t; l < k; l += B) s1[l] = __ldcg(&vecS[l]);
+                __syncthreads();
+            }
+            // ---- pass B: u_hat = v_hat - Yhat_k s' (rows [k, n) split over the team) ----
+            const int64_t rb0 = part_lo(k, n, rank, G), rb1 = part_lo(k, n, rank + 1, G);
+            if (k > 0) {
+                cta_rowdots<kAllCols, 1>(Yc, n, rb0, rb1, k, s1, nullptr, red,
+                                         [&](int64_t rho, double a, double) { vsm[rho] -= a; });
+            }
+            double uu = 0.0;
+            for (int64_t r = rb0 + t; r < rb1; r += B) uu = fma(vsm[r], vsm[r], uu);
+            uu = block_sum(uu, red);
+            if (k > 0) {
+                // g_u = Yhat_k^T u_hat (partial over this CTA's rows)
+                cta_coldots<kLower>(Yc, n, 0, k, rb0, rb1, vsm, red,
+                                    [&](int64_t i, double s) { myG[i] = s; });
+            }
+            if (t == 0) {
+                scal_t[rank * kScalTeam + 0] = uu;
+                scal_t[rank * kScalTeam + 1] = (rb0 <= k && k < rb1) ? vsm[k] : 0.0;
+            }
+            if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+            // ---- reflector (Eq. yt with t = 1/(c^2 - u_kk c), Sec. 3.3.2) ----
+            if (t == 0) {
+                double tot = 0.0, ukk = 0.0;
+                for (int r = 0; r < G; ++r) {
+                    tot += __ldcg(&scal_t[r * kScalTeam + 0]);
+                    ukk += __ldcg(&scal_t[r * kScalTeam + 1]);
+                }
+                const double nrm = sqrt(tot);
+                const bool broke = !(nrm > 0.0) || !isfinite(nrm);
+                const double cc = broke ? -1.0 : -sgn(ukk) * nrm;
+                const double ue = broke ? 1.0 : ukk;
+                s_b[0] = cc;
+                s_b[1] = 1.0 / (cc * cc - ue * cc);  // t_k
+                s_b[2] = ue - cc;                    // y_kk
+                s_b[3] = broke ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            const double cc = s_b[0], tk = s_b[1], ykk = s_b[2];
+            const bool broke = s_b[3] != 0.0;
+            // ---- T column: t_hat = -t_k T_k (Yhat_k^T y_hat) with Yhat^T y_hat = g_u - c r;
+            //      and x_T = T_{k+1} (row k of Y_{k+1}) = [T_k r + t_hat y_kk ; t_k y_kk] ----
+            const int64_t i0 = tri_row_lo(k, rank, G), i1 = tri_row_lo(k, rank + 1, G);
+            for (int64_t l = i0 + t; l < k; l += B) {
+                double g = 0.0;
+                if (broke) {
+                    g = __ldcg(&vecR[l]);
+                } else {
+                    for (int r = 0; r < G; ++r) g += __ldcg(&w.partG[(size_t)(leader + r) * n + l]);
+                }
+                s1[l] = g;
+            }
+            __syncthreads();
+            // second vector (r) read through a shared copy of vecR
+            double* rsm = (double*)vecR;  // read-only from here on
+            cta_rowdots<kUpperCol, 2>(Tc, ldt, i0, i1, k, s1, rsm, red + 1024,
+                                      [&](int64_t i, double a, double b) {
+                                          const double th = -tk * fma(-cc, b, a);
+                                          Tc[i + kk * ldt] = th;
+                                          vecX[i] = fma(th, ykk, b);
+                                      });
+            if (rank == 0 && t == 0) {
+                Tc[kk + kk * ldt] = tk;
+                vecX[kk] = tk * ykk;
+            }
+            // Y column k: rows of pass B (u_hat, with the diagonal entry u_kk - c)
+            for (int64_t r = rb0 + t; r < rb1; r += B) {
+                double y = broke ? 0.0 : vsm[r];
+                if (r == k) y = ykk;
+                Yc[r + kk * n] = y;
+            }
+            if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+            // ---- pass C: q = (Y_{k+1} T_{k+1} Y_{k+1}^T - I) e_k = Y_{k+1} x_T - e_k ----
+            for (int64_t l = t; l <= k; l += B) s1[l] = __ldcg(&vecX[l]);
+            __syncthreads();
+            double as = 0.0, am = -1.0, sq = 0.0;
+            int64_t ai = n;
+            cta_rowdots<kLowerCol, 1>(Yc, n, ra0, ra1, k + 1, s1, nullptr, red,
+                                      [&](int64_t rho, double a, double) {
+                                          const double q = (rho == k) ? a - 1.0 : a;
+                                          qbuf[rho] = q;
+                                          as += fabs(q);
+                                          sq = fma(q, q, sq);
+                                          if (fabs(q) > am || (fabs(q) == am && rho < ai)) {
+                                              am = fabs(q);
+                                              ai = rho;
+                                          }
+                                      });
+            as = block_sum(as, red);
+            sq = block_sum(sq, red);
+            // arg max over the CTA
+            {
+                double a2 = am;
+                int64_t i2 = ai;
+                warp_argmax(a2, i2);
+                __shared__ double s_am[32];
+                __shared__ int64_t s_ai[32];
+                const int lane = t & 31, wid = t >> 5;
+                if (lane == 0) {
+                    s_am[wid] = a2;
+                    s_ai[wid] = i2;
+                }
+                __syncthreads();
+                if (wid == 0) {
+                    double a3 = lane < (B >> 5) ? s_am[lane] : -1.0;
+                    int64_t i3 = lane < (B >> 5) ? s_ai[lane] : n;
+                    warp_argmax(a3, i3);
+                    if (lane == 0) {
+                        scal_t[rank * kScalTeam + 2] = as;
+                        scal_t[rank * kScalTeam + 3] = a3;
+                        scal_t[rank * kScalTeam + 4] = (double)i3;
+                        scal_t[rank * kScalTeam + 5] = sq;
+                    }
+                }
+            }
+            if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+            if (orth) {
+                for (int64_t r = ra0 + t; r < ra1; r += B)
+                    p.Z[r + kk * p.ldz] = qbuf[r];
+                break;
+            }
+            // ---- team statistics, convergence test on x = -c q (||x||_inf = |c| max|q|) ----
+            if (t == 0) {
+                double A1 = 0.0, S2 = 0.0, M = -1.0;
+                int64_t I = n;
+                for (int r = 0; r < G; ++r) {
+                    A1 += __ldcg(&scal_t[r * kScalTeam + 2]);
+                    S2 += __ldcg(&scal_t[r * kScalTeam + 5]);
+                    const double mr = __ldcg(&scal_t[r * kScalTeam + 3]);
+                    const int64_t ir = (int64_t)__ldcg(&scal_t[r * kScalTeam + 4]);
+                    if (mr > M || (mr == M && ir < I)) {
+                        M = mr;
+                        I = ir;
+                    }
+                }
+                s_b[4] = A1;
+                s_b[5] = M;
+                s_b[6] = S2;
+                s_arg = (I >= 0 && I < n) ? I : 0;  // all-NaN guard
+            }
+            __syncthreads();
+            const double A1 = s_b[4], M = s_b[5], S2 = s_b[6];
+            const bool success = !broke && fabs(cc) * M >= dtpcrt;
+            if (success && ++nrmchk >= kExtra + 1) conv = true;
+            if (conv || its == maxits) {
+                // Alg. 4 line 21: normalize; first entry of largest magnitude positive
+                const double qa = __ldcg(&qbuf[s_arg]);
+                double sc = 1.0 / sqrt(S2);
+                if (qa < 0.0) sc = -sc;
+                for (int64_t r = ra0 + t; r < ra1; r += B) p.Z[r + j * p.ldz] = qbuf[r] * sc;
+                if (rank == 0 && t == 0) {
+                    if (p.iters) p.iters[j] = conv ? its : -its;
+                    if (!conv) atomicAdd((unsigned long long*)&w.ctr[kCtrInfo], 1ull);
+                }
+                break;
+            }
+            // next sweep's scaled input: scl * x = q * (-sgn(c) n ||T||_1 max(eps,|u_nn|) / sum|q|)
+            fac_next = -sgn(cc) * (((double)n * onenrm) * fmax(kEps, u0n)) / A1;
+        }
+    }
+    return true;
+}
+
+// ---- MGS processing of one cluster by one CTA (Alg. 1) -----------------------------------
+__device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
+{
+    const Problem& p = cx.p;
+    const Ws& w = cx.w;
+    const int64_t n = p.n;
+    const int t = threadIdx.x, B = blockDim.x;
+    const int64_t s0 = w.clstart[c];
+    const int64_t mc = w.clsize[c];
+    double* v = cx.vsm;
+    double* red = cx.red;
+    const bool orth = (cx.mode == kModeOrth);
+    const double onenrm = w.scal[0], dtpcrt = w.scal[2];
+    const int64_t kstart = orth ? 0 : 1;
+    for (int64_t kk = kstart; kk < mc; ++kk) {
+        const int64_t j = s0 + kk;
+        const Fac f = orth ? Fac{} : fac_of(w, j, n);
+        const double u0n = orth ? 0.0 : w.u0n[j];
+        int nrmchk = 0, its = 0, attempt = 0;
+        bool conv = false;
+        const int maxits = orth ? 1 : kMaxIts;
+        while (its < maxits) {
+            ++its;
+            if (orth) {
+                for (int64_t r = t; r < n; r += B) v[r] = cx.V[r + kk * cx.ldv];
+                __syncthreads();
+            } else if (its == 1) {
+                for (int64_t r = t; r < n; r += B) v[r] = p.Z[r + j * p.ldz];
+                __syncthreads();
+            } else {
+                double as = 0.0;
+                for (int64_t r = t; r < n; r += B) as += fabs(v[r]);
+                as = block_sum(as, red);
+                const double scl = ((double)n * onenrm) * fmax(kEps, u0n) / as;
+                for (int64_t r = t; r < n; r += B) v[r] *= scl;
+                __syncthreads();
+                chunk_solve(n, f, v, red, t, solve_group_size(n), CtaSync());
+            }
+            // Alg. 1 lines 9-11: v <- v - <v, z_i> z_i for the previous members, in order
+            for (int64_t i = s0; i < j; ++i) {
+                const double* zi = p.Z + i * p.ldz;
+                double h = 0.0;
+                for (int64_t r = t; r < n; r += B) h = fma(v[r], zi[r], h);
+                h = block_sum(h, red);
+                for (int64_t r = t; r < n; r += B) v[r] = fma(-h, zi[r], v[r]);
+                __syncthreads();
+            }
+            double as = 0.0, mx = 0.0;
+            for (int64_t r = t; r < n; r += B) {
+                as += fabs(v[r]);
+                mx = fmax(mx, fabs(v[r]));
+            }
+            as = block_sum(as, red);
+            mx = block_max(mx, red);
+            bool ok = true;
+            if (!(as > 0.0) && !orth) {
+                // breakdown: restart from a fresh random vector
+                ++attempt;
+                const uint64_t key = start_key(p.seed, p.j0 + j, attempt);
+                for (int64_t r = t; r < n; r += B) v[r] = start_value(key, r);
+                __syncthreads();
+                ok = false;
+            }
+            if (orth) break;
+            if (ok && mx >= dtpcrt && ++nrmchk >= kExtra + 1) {
+                conv = true;
+                break;
+            }
+        }
+        // normalize; first entry of largest magnitude positive (orth: unit vector only)
+        double ss = 0.0, am = -1.0;
+        int64_t ai = n;
+        for (int64_t r = t; r < n; r += B) {
+            ss = fma(v[r], v[r], ss);
+            if (fabs(v[r]) > am) {
+                am = fabs(v[r]);
+                ai = r;
+            }
+        }
+        ss = block_sum(ss, red);
+        {
+            warp_argmax(am, ai);
+            __shared__ double s_am[32];
+            __shared__ int64_t s_ai[32];
+            const int lane = t & 31, wid = t >> 5;
+            if (lane == 0) {
+                s_am[wid] = am;
+                s_ai[wid] = ai;
+            }
+            __syncthreads();
+            if (wid == 0) {
+                double a3 = lane < (B >> 5) ? s_am[lane] : -1.0;
+                int64_t i3 = lane < (B >> 5) ? s_ai[lane] : n;
+                warp_argmax(a3, i3);
+                if (lane == 0) s_ai[0] = i3;
+            }
+            __syncthreads();
+            ai = (s_ai[0] >= 0 && s_ai[0] < n) ? s_ai[0] : 0;
+        }
+        double sc = 1.0 / sqrt(ss);
+        if (!orth && v[ai] < 0.0) sc = -sc;
+        double* dst = p.Z + (orth ? kk : j) * p.ldz;
+        for (int64_t r = t; r < n; r += B) dst[r] = v[r] * sc;
+        __syncthreads();
+        if (!orth && t == 0) {
+            if (p.iters) p.iters[j] = conv ? its : -its;
+            if (!conv) atomicAdd((unsigned long long*)&w.ctr[kCtrInfo], 1ull);
+        }
+        if (ld_volatile_i32(cx.err) != 0) return false;
+    }
+    return true;
+}
+
+template <int METHOD>
+__global__ void __launch_bounds__(kChainThreads, 1) k_chain(Problem p, Ws w, int32_t mode,
+                                                           const double* V, int64_t ldv)
+{
+    extern __shared__ double smem[];
+    const int b = blockIdx.x, t = threadIdx.x;
+    const int64_t n = p.n;
+    ChainCtx cx;
+    cx.p = p;
+    cx.w = w;
+    cx.mode = mode;
+    cx.V = V;
+    cx.ldv = ldv;
+    cx.red = smem;  // 2048 doubles
+    if (w.use_smem) {
+        cx.vsm = smem + 2048;
+        cx.s1 = smem + 2048 + n;
+    } else {
+        cx.vsm = w.gvec + (size_t)b * 2 * (size_t)n;
+        cx.s1 = cx.vsm + n;
+    }
+    cx.err = (int*)&w.ctr[kCtrErr];
+    __shared__ int s_c;
+
+    const int32_t tf = w.sched[4 * b + 0], tg = w.sched[4 * b + 1], tr = w.sched[4 * b + 2],
+                  tc = w.sched[4 * b + 3];
+    if (tc >= 0) {
+        Team tm{tf, tg, tr, w.bar + tf, 0u};
+        const bool ok = (METHOD == 0) ? cwy_cluster(cx, tc, tm) : mgs_cluster(cx, tc);
+        if (!ok) return;
+    }
+    const int64_t nq = w.ctr[kCtrNQueue];
+    for (;;) {
+        if (t == 0) {
+            const unsigned long long q =
+                atomicAdd((unsigned long long*)&w.ctr[kCtrQHead], 1ull);
+            s_c = ((int64_t)q < nq && ld_volatile_i32(cx.err) == 0) ? w.queue[q] : -1;
+        }
+        __syncthreads();
+        const int32_t c = s_c;
+        __syncthreads();
+        if (c < 0) break;
+        Team tm{b, 1, 0, w.bar + b, 0u};
+        const bool ok = (METHOD == 0) ? cwy_cluster(cx, c, tm) : mgs_cluster(cx, c);
+        if (!ok) return;
+    }
+}
+
+// ==========================================================================================
+// Launchers
+// ==========================================================================================
+bool chain_use_smem(int64_t n)
+{
+    return (size_t)(2048 + 2 * n) * sizeof(double) + 4096 <= 220u * 1024u;
+}
+
+size_t chain_smem_bytes(int64_t n, bool use_smem)
+{
+    return (size_t)(2048 + (use_smem ? 2 * n : 0)) * sizeof(double);
+}
+
+int32_t chain_grid(int32_t cap)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int32_t P = sms > 0 ? sms : 1;  // one CTA per SM (kChainThreads threads, large smem)
+    if (cap > 0 && cap < P) P = cap;
+    return P;
+}
+
+cudaError_t launch_plan(const Problem& p, const Ws& w, int32_t max_team, cudaStream_t st)
+{
+    k_plan<<<1, kPlanThreads, 0, st>>>(p, w, max_team, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm(const Problem& p, const Ws& w, cudaStream_t st)
+{
+    k_plan<<<1, kPlanThreads, 0, st>>>(p, w, 0, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orth_plan(int64_t m, const Ws& w, int32_t method, cudaStream_t st)
+{
+    k_orth_plan<<<1, 256, 0, st>>>(m, w, method);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lu(int64_t n, const double* d, const double* e, int64_t m, const double* shift,
+                      double* l, double* u0_or_r, double* u1, double* u2, uint8_t* piv,
+                      double* u0n, int store_reciprocal, cudaStream_t st)
+{
+    if (m <= 0) return cudaSuccess;
+    const int th = 128;
+    const unsigned blocks = (unsigned)((m + th - 1) / th);
+    k_lu<<<blocks, th, 0, st>>>(n, d, e, m, shift, l, u0_or_r, u1, u2, piv, u0n, store_reciprocal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_first(const Problem& p, const Ws& w, cudaStream_t st)
+{
+    if (p.m <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((p.m + kFirstWarps - 1) / kFirstWarps);
+    k_first<<<blocks, kFirstWarps * 32, 0, st>>>(p, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_rhs(int64_t n, int64_t m, const Ws& w, double* X, int64_t ldx,
+                             int32_t scale, cudaStream_t st)
+{
+    if (m <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((m + kFirstWarps - 1) / kFirstWarps);
+    k_solve_rhs<<<blocks, kFirstWarps * 32, 0, st>>>(n, m, w, X, ldx, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chain(const Problem& p, const Ws& w, int32_t mode, const double* V, int64_t ldv,
+                         cudaStream_t st)
+{
+    const size_t smem = chain_smem_bytes(p.n, w.use_smem != 0);
+    void* fn = (p.method == 0) ? (void*)k_chain<0> : (void*)k_chain<1>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, occ = 0;
+    cudaGetDevice(&dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kChainThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorLaunchOutOfResources;
+    Problem pp = p;
+    Ws ww = w;
+    int32_t mm = mode;
+    const double* VV = V;
+    int64_t ll = ldv;
+    void* args[] = {&pp, &ww, &mm, &VV, &ll};
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)w.P), dim3(kChainThreads), args, smem, st);
+}
+
+}  // namespace tinvx
