@@ -31,20 +31,27 @@ def _deps():
     return files
 
 
-def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
-    if not force and os.path.exists(LIB):
-        if os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in _deps()):
-            return LIB
-    os.makedirs(OBJDIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False,
+          profile: bool = False) -> str:
+    """Compile libtinv.so (or, with profile=True, the phase-timing diagnostic variant
+    libtinv_prof.so, which prints per-CTA phase cycle counts of the cluster kernel)."""
+    lib = LIB.replace("libtinv.so", "libtinv_prof.so") if profile else LIB
+    objdir = OBJDIR + ("_prof" if profile else "")
+    if not force and os.path.exists(lib):
+        if os.path.getmtime(lib) >= max(os.path.getmtime(f) for f in _deps()):
+            return lib
+    os.makedirs(objdir, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                     "--expt-relaxed-constexpr", "-I", INCLUDE]
     if verbose:
         flags += ["-Xptxas", "-v"]
     if debug:
         flags += ["-DTINV_DEBUG=1"]
+    if profile:
+        flags += ["-DTINV_PHASE_PROFILE=1"]
 
     def compile_one(src):
-        obj = os.path.join(OBJDIR, src.replace(".cu", ".o"))
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
         cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj] + flags
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -55,13 +62,13 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

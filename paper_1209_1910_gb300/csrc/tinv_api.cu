@@ -59,6 +59,8 @@ Layout make_layout(int64_t n, int64_t m, int32_t P, bool need_chain)
         L.vecX = take(pp * nn * sizeof(double));
         L.vecR = take(pp * nn * sizeof(double));
         L.qbuf = take(pp * nn * sizeof(double));
+        L.vbuf = take(pp * nn * sizeof(double));
+        L.tpub = take(pp * 8 * sizeof(double));
         if (!chain_use_smem(n)) L.gvec = take(pp * 2 * nn * sizeof(double));
     }
     L.total = off;
@@ -96,6 +98,8 @@ Ws bind_layout(void* base, const Layout& L, int64_t n, int64_t m, int32_t P)
         w.vecX = (double*)(b + L.vecX);
         w.vecR = (double*)(b + L.vecR);
         w.qbuf = (double*)(b + L.qbuf);
+        w.vbuf = (double*)(b + L.vbuf);
+        w.tpub = (double*)(b + L.tpub);
         w.gvec = L.gvec ? (double*)(b + L.gvec) : nullptr;
     }
     w.P = P;

@@ -311,6 +311,269 @@ __device__ void chunk_solve(int64_t n, const Fac& f, double* x, double* sh, int 
 }
 
 // ------------------------------------------------------------------------------------------
+// Team-distributed solve of (T - s I) x = fac * b.
+//
+// The team's G CTAs each own rows [r0, r1) (>= 2 rows each).  Inside a CTA the first 128
+// threads own contiguous chunks; every chunk computes the affine map of both substitutions
+// over its rows (as in chunk_solve).  Maps are combined by an inclusive Kogge-Stone scan inside
+// each warp (at most 32 chunks, so composed maps stay small), then by one thread over the 4
+// warps into the CTA's map, which is published to the team.  After one team barrier per
+// direction every CTA folds the published maps of the CTAs before it (forward) or after it
+// (back) as actual values, then re-runs its rows from the true boundary values.
+//   bsrc  : right-hand side (global, or shared when G == 1); the solve reads bsrc[k] * fac for
+//           its rows and the first row of the next CTA.
+//   vsm   : row-indexed scratch of the CTA (n slots); on return vsm[r0..r1) = x.
+//   vout  : if not null, also receives x[r0..r1) (global, for other CTAs of the team).
+//   pubf, pubb : team buffers of 2 and 6 doubles per rank for the published maps.
+//   sh    : >= 128 doubles of shared scratch.
+// ------------------------------------------------------------------------------------------
+struct TeamRef {
+    uint32_t* bar;
+    uint32_t* target;
+    int G, rank;
+    int* err;
+};
+
+__device__ __forceinline__ void compose2(double& m00, double& m01, double& m10, double& m11,
+                                         double& f0, double& f1, double n00, double n01,
+                                         double n10, double n11, double g0, double g1)
+{
+    // (M, f) <- (M, f) o (N, g) = (M N, M g + f): apply (N, g) first
+    const double a00 = fma(m00, n00, m01 * n10), a01 = fma(m00, n01, m01 * n11);
+    const double a10 = fma(m10, n00, m11 * n10), a11 = fma(m10, n01, m11 * n11);
+    const double b0 = fma(m00, g0, fma(m01, g1, f0)), b1 = fma(m10, g0, fma(m11, g1, f1));
+    m00 = a00;
+    m01 = a01;
+    m10 = a10;
+    m11 = a11;
+    f0 = b0;
+    f1 = b1;
+}
+
+__device__ bool team_solve(int64_t n, const Fac& f, const double* bsrc, double fac, double* vsm,
+                           double* vout, int64_t r0, int64_t r1, double* pubf, double* pubb,
+                           TeamRef tr, double* sh)
+{
+    constexpr int NW = 4, PT = 32 * NW;
+    const int t = threadIdx.x, B = blockDim.x, lane = t & 31, wid = t >> 5;
+    const int64_t R = r1 - r0;
+    const int Pn = (int)min((int64_t)PT, max((int64_t)1, R / 2));
+    const int64_t L = (R + Pn - 1) / Pn;
+    const bool part = t < PT;
+    const int64_t lo = r0 + (int64_t)t * L;
+    const int64_t hi = (t < Pn) ? min(r1, lo + L) : lo;
+    const bool act = (t < Pn) && (lo < hi);
+
+    // stage b (scaled) for the own rows and the first row of the next CTA
+    const int64_t send = min(r1 + 1, n);
+    for (int64_t k = r0 + t; k < send; k += B) vsm[k] = bsrc[k] * fac;
+    __syncthreads();
+
+    // ---------------- forward (P, L) ----------------
+    double A = 1.0, Bf = 0.0, bnext = 0.0;
+    if (act) {
+        for (int64_t k = lo; k < hi; ++k) {
+            if (k + 1 < n) {
+                const double b1 = vsm[k + 1];
+                const double lk = f.l[k];
+                if (f.piv[k]) {
+                    Bf = fma(-lk, b1, Bf);
+                } else {
+                    A = -lk * A;
+                    Bf = fma(-lk, Bf, b1);
+                }
+            }
+        }
+        if (hi < n) bnext = vsm[hi];
+    }
+    double ea = 1.0, eb = 0.0;  // exclusive prefix map within the warp
+    if (part) {
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const double pa = __shfl_up_sync(0xffffffffu, A, d);
+            const double pb = __shfl_up_sync(0xffffffffu, Bf, d);
+            if (lane >= d) {
+                Bf = fma(A, pb, Bf);
+                A = A * pa;
+            }
+        }
+        ea = __shfl_up_sync(0xffffffffu, A, 1);
+        eb = __shfl_up_sync(0xffffffffu, Bf, 1);
+        if (lane == 0) {
+            ea = 1.0;
+            eb = 0.0;
+        }
+        if (lane == 31) {
+            sh[2 * wid] = A;
+            sh[2 * wid + 1] = Bf;
+        }
+    }
+    __syncthreads();
+    if (t == 0 && tr.G > 1) {
+        double CA = 1.0, CB = 0.0;
+        for (int w2 = 0; w2 < NW; ++w2) {
+            CB = fma(sh[2 * w2], CB, sh[2 * w2 + 1]);
+            CA = sh[2 * w2] * CA;
+        }
+        pubf[2 * tr.rank] = CA;
+        pubf[2 * tr.rank + 1] = CB;
+    }
+    if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+    if (t == 0) {
+        double c;
+        if (tr.rank == 0) {
+            c = vsm[r0];
+        } else {
+            c = bsrc[0] * fac;
+            for (int q = 0; q < tr.rank; ++q) c = fma(__ldcg(&pubf[2 * q]), c, __ldcg(&pubf[2 * q + 1]));
+        }
+        for (int w2 = 0; w2 < NW; ++w2) {
+            sh[16 + w2] = c;
+            c = fma(sh[2 * w2], c, sh[2 * w2 + 1]);
+        }
+    }
+    __syncthreads();
+    if (act) {
+        double c = fma(ea, sh[16 + wid], eb);
+        for (int64_t k = lo; k < hi; ++k) {
+            if (k + 1 < n) {
+                const double b1 = (k + 1 < hi) ? vsm[k + 1] : bnext;
+                const double lk = f.l[k];
+                if (f.piv[k]) {
+                    vsm[k] = b1;
+                    c = fma(-lk, b1, c);
+                } else {
+                    vsm[k] = c;
+                    c = fma(-lk, c, b1);
+                }
+            } else {
+                vsm[k] = c;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---------------- back substitution (U) ----------------
+    // chunk map: (x_lo, x_lo+1) = M (x_hi, x_hi+1) + f
+    double m00 = 1.0, m01 = 0.0, m10 = 0.0, m11 = 1.0, f0 = 0.0, f1 = 0.0;
+    if (act) {
+        double p0 = 0.0, p1 = 0.0, h10 = 1.0, h11 = 0.0, h20 = 0.0, h21 = 1.0;
+        for (int64_t k = hi - 1; k >= lo; --k) {
+            const double rk = f.r[k], a = f.u1[k], b = f.u2[k], y = vsm[k];
+            const double vp = fma(-b, p1, fma(-a, p0, y)) * rk;
+            const double v1 = fma(-b, h11, -a * h10) * rk;
+            const double v2 = fma(-b, h21, -a * h20) * rk;
+            p1 = p0;
+            p0 = vp;
+            h11 = h10;
+            h10 = v1;
+            h21 = h20;
+            h20 = v2;
+        }
+        m00 = h10;
+        m01 = h20;
+        m10 = h11;
+        m11 = h21;
+        f0 = p0;
+        f1 = p1;
+    }
+    // inclusive suffix scan within the warp: S_p = m_p o m_{p+1} o ... o m_31
+    double e00 = 1.0, e01 = 0.0, e10 = 0.0, e11 = 1.0, g0 = 0.0, g1 = 0.0;  // exclusive
+    if (part) {
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const double n00 = __shfl_down_sync(0xffffffffu, m00, d);
+            const double n01 = __shfl_down_sync(0xffffffffu, m01, d);
+            const double n10 = __shfl_down_sync(0xffffffffu, m10, d);
+            const double n11 = __shfl_down_sync(0xffffffffu, m11, d);
+            const double q0 = __shfl_down_sync(0xffffffffu, f0, d);
+            const double q1 = __shfl_down_sync(0xffffffffu, f1, d);
+            if (lane + d < 32) compose2(m00, m01, m10, m11, f0, f1, n00, n01, n10, n11, q0, q1);
+        }
+        e00 = __shfl_down_sync(0xffffffffu, m00, 1);
+        e01 = __shfl_down_sync(0xffffffffu, m01, 1);
+        e10 = __shfl_down_sync(0xffffffffu, m10, 1);
+        e11 = __shfl_down_sync(0xffffffffu, m11, 1);
+        g0 = __shfl_down_sync(0xffffffffu, f0, 1);
+        g1 = __shfl_down_sync(0xffffffffu, f1, 1);
+        if (lane == 31) {
+            e00 = 1.0;
+            e01 = 0.0;
+            e10 = 0.0;
+            e11 = 1.0;
+            g0 = 0.0;
+            g1 = 0.0;
+        }
+        if (lane == 0) {
+            double* o = sh + 32 + 6 * wid;
+            o[0] = m00;
+            o[1] = m01;
+            o[2] = m10;
+            o[3] = m11;
+            o[4] = f0;
+            o[5] = f1;
+        }
+    }
+    __syncthreads();
+    if (t == 0 && tr.G > 1) {
+        double c00 = 1.0, c01 = 0.0, c10 = 0.0, c11 = 1.0, c0 = 0.0, c1 = 0.0;
+        for (int w2 = NW - 1; w2 >= 0; --w2) {  // CTA map = W_0 o W_1 o W_2 o W_3
+            const double* o = sh + 32 + 6 * w2;
+            double t00 = o[0], t01 = o[1], t10 = o[2], t11 = o[3], t0 = o[4], t1 = o[5];
+            compose2(t00, t01, t10, t11, t0, t1, c00, c01, c10, c11, c0, c1);
+            c00 = t00;
+            c01 = t01;
+            c10 = t10;
+            c11 = t11;
+            c0 = t0;
+            c1 = t1;
+        }
+        double* o = pubb + 6 * tr.rank;
+        o[0] = c00;
+        o[1] = c01;
+        o[2] = c10;
+        o[3] = c11;
+        o[4] = c0;
+        o[5] = c1;
+    }
+    if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+    if (t == 0) {
+        double s0 = 0.0, s1 = 0.0;  // x_n = x_{n+1} = 0 below the last CTA
+        for (int q = tr.G - 1; q > tr.rank; --q) {
+            const double* o = pubb + 6 * q;
+            const double n0 = fma(__ldcg(&o[0]), s0, fma(__ldcg(&o[1]), s1, __ldcg(&o[4])));
+            const double n1 = fma(__ldcg(&o[2]), s0, fma(__ldcg(&o[3]), s1, __ldcg(&o[5])));
+            s0 = n0;
+            s1 = n1;
+        }
+        for (int w2 = NW - 1; w2 >= 0; --w2) {
+            sh[64 + 2 * w2] = s0;
+            sh[64 + 2 * w2 + 1] = s1;
+            const double* o = sh + 32 + 6 * w2;
+            const double n0 = fma(o[0], s0, fma(o[1], s1, o[4]));
+            const double n1 = fma(o[2], s0, fma(o[3], s1, o[5]));
+            s0 = n0;
+            s1 = n1;
+        }
+    }
+    __syncthreads();
+    if (act) {
+        const double w0 = sh[64 + 2 * wid], w1 = sh[64 + 2 * wid + 1];
+        double cur = fma(e00, w0, fma(e01, w1, g0));
+        double nxt = fma(e10, w0, fma(e11, w1, g1));
+        for (int64_t k = hi - 1; k >= lo; --k) {
+            const double v = fma(-f.u2[k], nxt, fma(-f.u1[k], cur, vsm[k])) * f.r[k];
+            vsm[k] = v;
+            if (vout) vout[k] = v;
+            nxt = cur;
+            cur = v;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// ------------------------------------------------------------------------------------------
 // CTA-wide products used by the reorthogonalization.
 //
 // coldots: out(i, sum_{rho in R(i)} A[rho + i lda] x[rho]) for columns i in [c0, c1), with
@@ -324,6 +587,109 @@ __device__ void chunk_solve(int64_t n, const Fac& f, double* x, double* sh, int 
 enum ColKind { kLower = 0, kUpper = 1 };
 enum RowKind { kLowerCol = 0, kUpperCol = 1, kAllCols = 2 };
 
+// Warp-uniform part of per-lane ranges [a, b): lanes that take part pass their range, the
+// others (act = false) must not constrain it.
+__device__ __forceinline__ void warp_core(int64_t a, int64_t b, bool act, int64_t& lo, int64_t& hi)
+{
+    int64_t la = act ? a : INT64_MIN, lb = act ? b : INT64_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        la = max(la, __shfl_xor_sync(0xffffffffu, la, o));
+        lb = min(lb, __shfl_xor_sync(0xffffffffu, lb, o));
+    }
+    lo = la;
+    hi = lb;
+}
+
+// sum over r in [a, b) of p[r * stride] * x[r]  (core part [lo, hi) is warp-uniform, unrolled by
+// 8 with all loads issued before the FMAs; the rest is per-lane)
+template <int STRIDE1>
+__device__ __forceinline__ double dot_range(const double* __restrict__ p, int64_t stride,
+                                            const double* x, int64_t a, int64_t b, int64_t lo,
+                                            int64_t hi, bool act)
+{
+    double acc0 = 0.0, acc1 = 0.0;
+    if (!act) return 0.0;
+    const int64_t st = STRIDE1 ? 1 : stride;
+    if (lo < hi && lo >= a && hi <= b) {
+        for (int64_t r = a; r < lo; ++r) acc0 = fma(p[r * st], x[r], acc0);
+        int64_t r = lo;
+        for (; r + 8 <= hi; r += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = p[(r + u) * st];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                acc0 = fma(v[u], x[r + u], acc0);
+                acc1 = fma(v[u + 1], x[r + u + 1], acc1);
+            }
+        }
+        for (; r < hi; ++r) acc0 = fma(p[r * st], x[r], acc0);
+        for (r = hi; r < b; ++r) acc1 = fma(p[r * st], x[r], acc1);
+    } else {
+        for (int64_t r = a; r < b; ++r) acc0 = fma(p[r * st], x[r], acc0);
+    }
+    return acc0 + acc1;
+}
+
+// Two dot products sharing the loads of p.
+template <int STRIDE1>
+__device__ __forceinline__ void dot2_range(const double* __restrict__ p, int64_t stride,
+                                           const double* x, const double* y, int64_t a, int64_t b,
+                                           int64_t lo, int64_t hi, bool act, double& ox, double& oy)
+{
+    double ax0 = 0.0, ax1 = 0.0, ay0 = 0.0, ay1 = 0.0;
+    ox = oy = 0.0;
+    if (!act) return;
+    const int64_t st = STRIDE1 ? 1 : stride;
+    if (lo < hi && lo >= a && hi <= b) {
+        for (int64_t r = a; r < lo; ++r) {
+            const double v = p[r * st];
+            ax0 = fma(v, x[r], ax0);
+            ay0 = fma(v, y[r], ay0);
+        }
+        int64_t r = lo;
+        for (; r + 8 <= hi; r += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = p[(r + u) * st];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                ax0 = fma(v[u], x[r + u], ax0);
+                ay0 = fma(v[u], y[r + u], ay0);
+                ax1 = fma(v[u + 1], x[r + u + 1], ax1);
+                ay1 = fma(v[u + 1], y[r + u + 1], ay1);
+            }
+        }
+        for (; r < b; ++r) {
+            const double v = p[r * st];
+            ax1 = fma(v, x[r], ax1);
+            ay1 = fma(v, y[r], ay1);
+        }
+    } else {
+        for (int64_t r = a; r < b; ++r) {
+            const double v = p[r * st];
+            ax0 = fma(v, x[r], ax0);
+            ay0 = fma(v, y[r], ay0);
+        }
+    }
+    ox = ax0 + ax1;
+    oy = ay0 + ay1;
+}
+
+// ------------------------------------------------------------------------------------------
+// CTA-wide products used by the reorthogonalization.
+//
+// coldots: out(i, sum_{rho in R(i)} A[rho + i lda] x[rho]) for columns i in [c0, c1), with
+//   R(i) = [max(rlo, i), rhi)    (LOWER: the nonzeros of a lower-trapezoidal column), or
+//   R(i) = [rlo, min(rhi, i+1))  (UPPER: the nonzeros of an upper-triangular column).
+//   One thread per (column, row segment): each thread streams down its own column.
+// rowdots: out(rho, sum_{i in C(rho)} A[rho + i lda] x[i]) for rows rho in [r0, r1), with
+//   C(rho) = [0, min(ccap, rho+1))  (LOWERCOL),  [rho, ccap)  (UPPERCOL),  [0, ccap)  (ALL).
+//   One thread per (row, column segment): a warp reads 32 consecutive rows of a column.
+// When there are fewer columns (rows) than threads, each is split into S segments whose
+// partial sums are added in segment order; `red` holds >= 2*blockDim doubles.
+// ------------------------------------------------------------------------------------------
 template <int KIND, class Out>
 __device__ void cta_coldots(const double* __restrict__ A, int64_t lda, int64_t c0, int64_t c1,
                             int64_t rlo, int64_t rhi, const double* x, double* red, Out out)
@@ -332,13 +698,15 @@ __device__ void cta_coldots(const double* __restrict__ A, int64_t lda, int64_t c
     const int64_t nc = c1 - c0;
     if (nc <= 0) return;
     if (nc >= B) {
-        for (int64_t i = c0 + t; i < c1; i += B) {
-            const int64_t lo = (KIND == kLower) ? max(rlo, i) : rlo;
-            const int64_t hi = (KIND == kLower) ? rhi : min(rhi, i + 1);
-            const double* a = A + i * lda;
-            double acc = 0.0;
-            for (int64_t r = lo; r < hi; ++r) acc = fma(a[r], x[r], acc);
-            out(i, acc);
+        for (int64_t base = c0; base < c1; base += B) {
+            const int64_t i = base + t;
+            const bool act = i < c1;
+            const int64_t a = act ? ((KIND == kLower) ? max(rlo, i) : rlo) : 0;
+            const int64_t b = act ? ((KIND == kLower) ? rhi : min(rhi, i + 1)) : 0;
+            int64_t lo, hi;
+            warp_core(a, b, act && a < b, lo, hi);
+            const double s = dot_range<1>(A + (act ? i : 0) * lda, 1, x, a, b, lo, hi, act);
+            if (act) out(i, s);
         }
         __syncthreads();
         return;
@@ -347,24 +715,27 @@ __device__ void cta_coldots(const double* __restrict__ A, int64_t lda, int64_t c
     while (S < 32 && (int64_t)(2 * S) * nc <= B) S *= 2;
     const int64_t ci = t % nc;
     const int sg = (int)(t / nc);
-    if (sg < S) {
-        const int64_t i = c0 + ci;
-        const int64_t lo = (KIND == kLower) ? max(rlo, i) : rlo;
-        const int64_t hi = (KIND == kLower) ? rhi : min(rhi, i + 1);
-        const int64_t len = hi > lo ? hi - lo : 0;
+    const bool act = sg < S;
+    int64_t a = 0, b = 0;
+    const int64_t i = c0 + ci;
+    if (act) {
+        const int64_t lo0 = (KIND == kLower) ? max(rlo, i) : rlo;
+        const int64_t hi0 = (KIND == kLower) ? rhi : min(rhi, i + 1);
+        const int64_t len = hi0 > lo0 ? hi0 - lo0 : 0;
         const int64_t seg = (len + S - 1) / S;
-        const int64_t a0 = lo + sg * seg;
-        const int64_t a1 = min(hi, a0 + seg);
-        const double* a = A + i * lda;
-        double acc = 0.0;
-        for (int64_t r = a0; r < a1; ++r) acc = fma(a[r], x[r], acc);
-        red[sg * nc + ci] = acc;
+        a = lo0 + sg * seg;
+        b = min(hi0, a + seg);
+        if (b < a) b = a;
     }
+    int64_t lo, hi;
+    warp_core(a, b, act && a < b, lo, hi);
+    const double s = dot_range<1>(A + i * lda, 1, x, a, b, lo, hi, act);
+    if (act) red[sg * nc + ci] = s;
     __syncthreads();
     if (t < nc) {
-        double s = red[t];
-        for (int q = 1; q < S; ++q) s += red[q * nc + t];
-        out(c0 + t, s);
+        double v = red[t];
+        for (int q = 1; q < S; ++q) v += red[q * nc + t];
+        out(c0 + t, v);
     }
     __syncthreads();
 }
@@ -377,16 +748,19 @@ __device__ void cta_rowdots(const double* __restrict__ A, int64_t lda, int64_t r
     const int64_t nr = r1 - r0;
     if (nr <= 0) return;
     if (nr >= B) {
-        for (int64_t rho = r0 + t; rho < r1; rho += B) {
-            const int64_t cb = (KIND == kUpperCol) ? rho : 0;
-            const int64_t ce = (KIND == kLowerCol) ? min(ccap, rho + 1) : ccap;
-            double acc0 = 0.0, acc1 = 0.0;
-            for (int64_t i = cb; i < ce; ++i) {
-                const double a = A[rho + i * lda];
-                acc0 = fma(a, x0[i], acc0);
-                if (NV == 2) acc1 = fma(a, x1[i], acc1);
-            }
-            out(rho, acc0, acc1);
+        for (int64_t base = r0; base < r1; base += B) {
+            const int64_t rho = base + t;
+            const bool act = rho < r1;
+            const int64_t a = act ? ((KIND == kUpperCol) ? rho : 0) : 0;
+            const int64_t b = act ? ((KIND == kLowerCol) ? min(ccap, rho + 1) : ccap) : 0;
+            int64_t lo, hi;
+            warp_core(a, b, act && a < b, lo, hi);
+            double s0, s1 = 0.0;
+            if (NV == 2)
+                dot2_range<0>(A + (act ? rho : 0), lda, x0, x1, a, b, lo, hi, act, s0, s1);
+            else
+                s0 = dot_range<0>(A + (act ? rho : 0), lda, x0, a, b, lo, hi, act);
+            if (act) out(rho, s0, s1);
         }
         __syncthreads();
         return;
@@ -395,8 +769,10 @@ __device__ void cta_rowdots(const double* __restrict__ A, int64_t lda, int64_t r
     while (S < 32 && (int64_t)(2 * S) * nr <= B) S *= 2;
     const int64_t ri = t % nr;
     const int sg = (int)(t / nr);
-    if (sg < S) {
-        const int64_t rho = r0 + ri;
+    const bool act = sg < S;
+    const int64_t rho = r0 + ri;
+    int64_t a = 0, b = 0;
+    if (act) {
         // fixed column grid over the columns any row of [r0, r1) can touch
         const int64_t gb = (KIND == kUpperCol) ? r0 : 0;
         const int64_t ge = (KIND == kLowerCol) ? min(ccap, r1) : ccap;
@@ -406,25 +782,29 @@ __device__ void cta_rowdots(const double* __restrict__ A, int64_t lda, int64_t r
         const int64_t s1 = min(ge, s0 + seg);
         const int64_t cb = (KIND == kUpperCol) ? rho : 0;
         const int64_t ce = (KIND == kLowerCol) ? min(ccap, rho + 1) : ccap;
-        double acc0 = 0.0, acc1 = 0.0;
-        for (int64_t i = s0; i < s1; ++i) {
-            if (i >= cb && i < ce) {
-                const double a = A[rho + i * lda];
-                acc0 = fma(a, x0[i], acc0);
-                if (NV == 2) acc1 = fma(a, x1[i], acc1);
-            }
-        }
-        red[(sg * nr + ri) * NV] = acc0;
-        if (NV == 2) red[(sg * nr + ri) * NV + 1] = acc1;
+        a = max(s0, cb);
+        b = min(s1, ce);
+        if (b < a) b = a;
+    }
+    int64_t lo, hi;
+    warp_core(a, b, act && a < b, lo, hi);
+    double s0, s1 = 0.0;
+    if (NV == 2)
+        dot2_range<0>(A + rho, lda, x0, x1, a, b, lo, hi, act, s0, s1);
+    else
+        s0 = dot_range<0>(A + rho, lda, x0, a, b, lo, hi, act);
+    if (act) {
+        red[(sg * nr + ri) * NV] = s0;
+        if (NV == 2) red[(sg * nr + ri) * NV + 1] = s1;
     }
     __syncthreads();
     if (t < nr) {
-        double s0 = red[t * NV], s1 = (NV == 2) ? red[t * NV + 1] : 0.0;
+        double v0 = red[t * NV], v1 = (NV == 2) ? red[t * NV + 1] : 0.0;
         for (int q = 1; q < S; ++q) {
-            s0 += red[(q * nr + t) * NV];
-            if (NV == 2) s1 += red[(q * nr + t) * NV + 1];
+            v0 += red[(q * nr + t) * NV];
+            if (NV == 2) v1 += red[(q * nr + t) * NV + 1];
         }
-        out(r0 + t, s0, s1);
+        out(r0 + t, v0, v1);
     }
     __syncthreads();
 }

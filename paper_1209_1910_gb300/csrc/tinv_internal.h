@@ -23,7 +23,7 @@ enum ChainMode : int32_t { kModeInvit = 0, kModeOrth = 1 };
 struct Layout {
     size_t scal, wp, head, clstart, clsize, cltoff, sched, queue, ctr, bar;
     size_t fl, fu1, fu2, fr, fpiv, u0n;
-    size_t Y, T, partS, partG, partScal, vecS, vecX, vecR, qbuf, gvec;
+    size_t Y, T, partS, partG, partScal, vecS, vecX, vecR, qbuf, vbuf, tpub, gvec;
     size_t total;
 };
 
@@ -70,6 +70,8 @@ struct Ws {
     double *partS, *partG;  // [P*n]
     double* partScal;       // [P*kScalTeam]
     double *vecS, *vecX, *vecR, *qbuf;  // [P*n]
+    double* vbuf;     // [P*n]  solved iterate of each team (rows of all CTAs)
+    double* tpub;     // [P*8]  published solve maps of each team (2 + 6 doubles per rank)
     double* gvec;     // [P*2n] global fallback for the per-CTA vectors (large n)
     int32_t P;        // persistent grid size the schedule was made for
     int32_t use_smem; // per-CTA vectors live in shared memory

@@ -12,6 +12,7 @@
 //              Alg. 1, on one CTA per cluster).
 #include <cooperative_groups.h>
 #include <math.h>
+#include <stdio.h>
 
 #include "tinv_device.cuh"
 
@@ -428,6 +429,31 @@ __global__ void __launch_bounds__(kFirstWarps * 32) k_solve_rhs(int64_t n, int64
 // ==========================================================================================
 // Persistent cluster kernel
 // ==========================================================================================
+// Phase profiling (separate diagnostic build with -DTINV_PHASE_PROFILE): thread 0 of each CTA
+// accumulates clock64() per phase and prints the totals when the kernel ends.
+#ifdef TINV_PHASE_PROFILE
+enum { kPhLoad, kPhSolve, kPhA, kPhB1, kPhT1, kPhB2, kPhB, kPhB3, kPhT2, kPhB4, kPhC, kPhB5, kPhEnd, kPhN };
+#define PROF_MARK(acc, i)                                   \
+    do {                                                    \
+        if (threadIdx.x == 0) {                             \
+            long long _n = clock64();                       \
+            (acc).c[i] += (unsigned long long)(_n - (acc).t); \
+            (acc).t = _n;                                   \
+        }                                                   \
+    } while (0)
+struct Prof {
+    unsigned long long c[kPhN];
+    long long t;
+};
+#else
+#define PROF_MARK(acc, i) \
+    do {                  \
+    } while (0)
+struct Prof {
+    long long t;
+};
+#endif
+
 struct Team {
     int32_t leader, G, rank;
     uint32_t* bar;
@@ -444,6 +470,7 @@ struct ChainCtx {
     double* s1;    // [n] staging vector (shared or global)
     double* red;   // [2048] reduction / solve scratch (shared)
     int* err;
+    Prof prof;
 };
 
 __device__ __forceinline__ int64_t part_lo(int64_t a, int64_t b, int r, int G)
@@ -497,6 +524,9 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
     double* vecX = w.vecX + (size_t)leader * n;
     double* vecR = w.vecR + (size_t)leader * n;
     double* qbuf = w.qbuf + (size_t)leader * n;
+    double* vbuf = w.vbuf + (size_t)leader * n;
+    double* pubf = w.tpub + (size_t)leader * 8;  // 2 doubles per rank, then 6 per rank
+    double* pubb = pubf + 2 * G;
     double* myS = w.partS + (size_t)(leader + rank) * n;
     double* myG = w.partG + (size_t)(leader + rank) * n;
     double* scal_t = w.partScal + (size_t)leader * kScalTeam;  // rank r at + r*kScalTeam
@@ -559,23 +589,27 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
         const int maxits = orth ? 1 : kMaxIts;
         while (its < maxits) {
             ++its;
-            // ---- the iterate v (full vector in every CTA of the team) ----
-            if (orth) {
-                for (int64_t r = t; r < n; r += B) vsm[r] = cx.V[r + kk * cx.ldv];
-                __syncthreads();
-            } else if (its == 1) {
-                for (int64_t r = t; r < n; r += B) vsm[r] = p.Z[r + j * p.ldz];
-                __syncthreads();
+            // ---- the iterate v: rows [ra0, ra1) in shared memory, all rows in vsrc ----
+            PROF_MARK(cx.prof, kPhEnd);
+            const double* vsrc = orth ? cx.V + kk * cx.ldv : (its == 1 ? p.Z + j * p.ldz : vbuf);
+            if (!orth && its > 1) {
+                PROF_MARK(cx.prof, kPhLoad);
+                TeamRef tr{tm.bar, &tm.target, G, rank, cx.err};
+                if (!team_solve(n, f, qbuf, fac_next, vsm, vbuf, ra0, ra1, pubf, pubb, tr, red))
+                    return false;
+                PROF_MARK(cx.prof, kPhSolve);
             } else {
-                for (int64_t r = t; r < n; r += B) vsm[r] = __ldcg(&qbuf[r]) * fac_next;
+                for (int64_t r = ra0 + t; r < ra1; r += B) vsm[r] = __ldcg(&vsrc[r]);
                 __syncthreads();
-                chunk_solve(n, f, vsm, red, t, solve_group_size(n), CtaSync());
             }
+            PROF_MARK(cx.prof, kPhLoad);
             if (k > 0) {
                 // ---- pass A: s = Y_k^T v = L_k^T v_check + Yhat_k^T v_hat (team partials) ----
                 cta_coldots<kLower>(Yc, n, 0, k, ra0, ra1, vsm, red,
                                     [&](int64_t i, double s) { myS[i] = s; });
+                PROF_MARK(cx.prof, kPhA);
                 if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+                PROF_MARK(cx.prof, kPhB1);
                 // ---- s' = T_k^T s, columns split over the team ----
                 const int64_t c0 = tri_col_lo(k, rank, G), c1 = tri_col_lo(k, rank + 1, G);
                 for (int64_t l = t; l < c1; l += B) {
@@ -586,12 +620,16 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 __syncthreads();
                 cta_coldots<kUpper>(Tc, ldt, c0, c1, 0, k, s1, red,
                                     [&](int64_t i, double s) { vecS[i] = s; });
+                PROF_MARK(cx.prof, kPhT1);
                 if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+                PROF_MARK(cx.prof, kPhB2);
                 for (int64_t l = t; l < k; l += B) s1[l] = __ldcg(&vecS[l]);
                 __syncthreads();
             }
             // ---- pass B: u_hat = v_hat - Yhat_k s' (rows [k, n) split over the team) ----
             const int64_t rb0 = part_lo(k, n, rank, G), rb1 = part_lo(k, n, rank + 1, G);
+            for (int64_t r = rb0 + t; r < rb1; r += B) vsm[r] = __ldcg(&vsrc[r]);
+            __syncthreads();
             if (k > 0) {
                 cta_rowdots<kAllCols, 1>(Yc, n, rb0, rb1, k, s1, nullptr, red,
                                          [&](int64_t rho, double a, double) { vsm[rho] -= a; });
@@ -608,7 +646,9 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 scal_t[rank * kScalTeam + 0] = uu;
                 scal_t[rank * kScalTeam + 1] = (rb0 <= k && k < rb1) ? vsm[k] : 0.0;
             }
+            PROF_MARK(cx.prof, kPhB);
             if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+            PROF_MARK(cx.prof, kPhB3);
             // ---- reflector (Eq. yt with t = 1/(c^2 - u_kk c), Sec. 3.3.2) ----
             if (t == 0) {
                 double tot = 0.0, ukk = 0.0;
@@ -659,7 +699,9 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 if (r == k) y = ykk;
                 Yc[r + kk * n] = y;
             }
+            PROF_MARK(cx.prof, kPhT2);
             if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+            PROF_MARK(cx.prof, kPhB4);
             // ---- pass C: q = (Y_{k+1} T_{k+1} Y_{k+1}^T - I) e_k = Y_{k+1} x_T - e_k ----
             for (int64_t l = t; l <= k; l += B) s1[l] = __ldcg(&vecX[l]);
             __syncthreads();
@@ -703,7 +745,9 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                     }
                 }
             }
+            PROF_MARK(cx.prof, kPhC);
             if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+            PROF_MARK(cx.prof, kPhB5);
             if (orth) {
                 for (int64_t r = ra0 + t; r < ra1; r += B)
                     p.Z[r + kk * p.ldz] = qbuf[r];
@@ -785,9 +829,10 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
                 for (int64_t r = t; r < n; r += B) as += fabs(v[r]);
                 as = block_sum(as, red);
                 const double scl = ((double)n * onenrm) * fmax(kEps, u0n) / as;
-                for (int64_t r = t; r < n; r += B) v[r] *= scl;
-                __syncthreads();
-                chunk_solve(n, f, v, red, t, solve_group_size(n), CtaSync());
+                uint32_t tgt = 0;
+                TeamRef tr{nullptr, &tgt, 1, 0, cx.err};
+                if (!team_solve(n, f, v, scl, v, nullptr, 0, n, nullptr, nullptr, tr, red))
+                    return false;
             }
             // Alg. 1 lines 9-11: v <- v - <v, z_i> z_i for the previous members, in order
             for (int64_t i = s0; i < j; ++i) {
@@ -887,6 +932,11 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_chain(Problem p, Ws w, int
     }
     cx.err = (int*)&w.ctr[kCtrErr];
     __shared__ int s_c;
+#ifdef TINV_PHASE_PROFILE
+    for (int i = 0; i < kPhN; ++i) cx.prof.c[i] = 0;
+    const long long t_begin = clock64();
+#endif
+    cx.prof.t = clock64();
 
     const int32_t tf = w.sched[4 * b + 0], tg = w.sched[4 * b + 1], tr = w.sched[4 * b + 2],
                   tc = w.sched[4 * b + 3];
@@ -910,6 +960,14 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_chain(Problem p, Ws w, int
         const bool ok = (METHOD == 0) ? cwy_cluster(cx, c, tm) : mgs_cluster(cx, c);
         if (!ok) return;
     }
+#ifdef TINV_PHASE_PROFILE
+    if (t == 0)
+        printf("PROF cta=%d team=%d G=%d total=%lld load=%llu solve=%llu A=%llu b1=%llu T1=%llu b2=%llu "
+               "B=%llu b3=%llu T2=%llu b4=%llu C=%llu b5=%llu end=%llu\n",
+               b, tc, tg, clock64() - t_begin, cx.prof.c[kPhLoad], cx.prof.c[kPhSolve], cx.prof.c[kPhA],
+               cx.prof.c[kPhB1], cx.prof.c[kPhT1], cx.prof.c[kPhB2], cx.prof.c[kPhB], cx.prof.c[kPhB3],
+               cx.prof.c[kPhT2], cx.prof.c[kPhB4], cx.prof.c[kPhC], cx.prof.c[kPhB5], cx.prof.c[kPhEnd]);
+#endif
 }
 
 // ==========================================================================================

@@ -133,8 +133,9 @@ def test_orth_cwy_matches_oracle(gpu, orc, n, m, kappa, max_team):
     Qo, Yo, To, _ = orc.orth(V, "cwy_new")
     tol = 10 * n * EPS * kap
     assert np.abs(Q - Qo).max() <= tol
-    assert np.abs(np.tril(Y) - np.tril(Yo)).max() <= tol
-    assert np.abs(np.triu(T) - np.triu(To)).max() <= tol * 10
+    assert np.abs(np.tril(Y) - np.tril(Yo)).max() <= tol * np.abs(Yo).max()
+    # T grows with the conditioning of Y; compare it relative to its size
+    assert np.abs(np.triu(T) - np.triu(To)).max() <= tol * np.abs(To).max()
     assert np.abs(Q.T @ Q - np.eye(m)).max() <= 10 * n * EPS
 
 
