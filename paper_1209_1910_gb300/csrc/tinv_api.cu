@@ -49,6 +49,7 @@ Layout make_layout(int64_t n, int64_t m, int32_t P, bool need_chain)
     L.fr = take(mm * nn * sizeof(double));
     L.fpiv = take(mm * nn);
     L.u0n = take(mm * sizeof(double));
+    L.tolv = take(mm * sizeof(double));
     if (need_chain) {
         L.Y = take(nn * mm * sizeof(double));
         L.T = take(mm * mm * sizeof(double));
@@ -88,6 +89,7 @@ Ws bind_layout(void* base, const Layout& L, int64_t n, int64_t m, int32_t P)
     w.fr = (double*)(b + L.fr);
     w.fpiv = (uint8_t*)(b + L.fpiv);
     w.u0n = (double*)(b + L.u0n);
+    w.tolv = (double*)(b + L.tolv);
     if (L.Y) {
         w.Y = (double*)(b + L.Y);
         w.T = (double*)(b + L.T);
@@ -195,7 +197,7 @@ int enqueue_tinv(const Problem& p, void* ws, int32_t P, int32_t max_team, cudaSt
     if (e == cudaSuccess) e = launch_plan(p, w, max_team, st);
     if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[1], st);
     if (e == cudaSuccess)
-        e = launch_lu(p.n, p.d, p.e, p.m, w.wp, w.fl, w.fr, w.fu1, w.fu2, w.fpiv, w.u0n, 1, st);
+        e = launch_lu(p.n, p.d, p.e, p.m, w.wp, w.fl, w.fr, w.fu1, w.fu2, w.fpiv, w.u0n, w.tolv, st);
     if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[2], st);
     if (e == cudaSuccess) e = launch_first(p, w, st);
     if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[3], st);
@@ -472,7 +474,7 @@ int tinv_lu(int64_t n, const double* d, const double* e, int64_t m, const double
     if (m == 0) return 0;
     if (op.o.device_ptrs) {
         cudaStream_t st = (cudaStream_t)op.o.stream;
-        return cuda_code(launch_lu(n, d, e, m, s, l, u0, u1, u2, piv, nullptr, 0, st));
+        return cuda_code(launch_lu(n, d, e, m, s, l, u0, u1, u2, piv, nullptr, nullptr, st));
     }
     if (!all_finite(d, n) || (n > 1 && !all_finite(e, n - 1))) return -2;
     cudaStream_t st;
@@ -499,7 +501,7 @@ int tinv_lu(int64_t n, const double* d, const double* e, int64_t m, const double
             if (ce == cudaSuccess)
                 ce = launch_lu(n, (double*)dd.p, (double*)de.p, m, (double*)ds.p, (double*)dl.p,
                                (double*)d0.p, (double*)d1.p, (double*)d2.p, (uint8_t*)dp.p, nullptr,
-                               0, st);
+                               nullptr, st);
             if (ce == cudaSuccess) ce = cudaMemcpyAsync(l, dl.p, mn * sizeof(double), cudaMemcpyDeviceToHost, st);
             if (ce == cudaSuccess) ce = cudaMemcpyAsync(u0, d0.p, mn * sizeof(double), cudaMemcpyDeviceToHost, st);
             if (ce == cudaSuccess) ce = cudaMemcpyAsync(u1, d1.p, mn * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -574,7 +576,7 @@ int tinv_solve(int64_t n, const double* d, const double* e, int64_t m, const dou
         if (!rc) rc = cuda_code(launch_norm(p, wsb, st));
         if (!rc)
             rc = cuda_code(launch_lu(n, p.d, p.e, m, p.w, wsb.fl, wsb.fr, wsb.fu1, wsb.fu2, wsb.fpiv,
-                                     wsb.u0n, 1, st));
+                                     wsb.u0n, wsb.tolv, st));
         if (!rc) rc = cuda_code(launch_solve_rhs(n, m, wsb, X_dev, ldx_dev, scale, st));
         if (!rc && !op.o.device_ptrs) {
             ce = cudaMemcpy2DAsync(X, ldx * sizeof(double), X_dev, n * sizeof(double),

@@ -132,6 +132,11 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p)
     return *(volatile const int*)p;
 }
 
+__device__ __forceinline__ void red_release_add_u32(uint32_t* p, uint32_t v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __noinline__ bool team_sync(uint32_t* ctr, uint32_t& target, int G, int* err)
 {
     __shared__ int s_ok;
@@ -139,24 +144,25 @@ __device__ __noinline__ bool team_sync(uint32_t* ctr, uint32_t& target, int G, i
     if (G <= 1) return ld_volatile_i32(err) == 0;
     if (threadIdx.x == 0) {
         target += (uint32_t)G;
-        __threadfence();
-        atomicAdd(ctr, 1u);
+        red_release_add_u32(ctr, 1u);  // the CTA's writes (ordered by the barrier) go first
         int ok = 1;
-        uint64_t t0 = globaltimer_ns();
+        uint64_t t0 = 0;
         uint32_t spins = 0;
         while ((int32_t)(ld_acquire_u32(ctr) - target) < 0) {
-            if (ld_volatile_i32(err) != 0) {
-                ok = 0;
-                break;
+            if ((++spins & 63u) == 0) {
+                if (ld_volatile_i32(err) != 0) {
+                    ok = 0;
+                    break;
+                }
+                const uint64_t now = globaltimer_ns();
+                if (t0 == 0) t0 = now;
+                if (spins > kSpinLimit || now - t0 > kSpinTimeoutNs) {
+                    atomicOr(err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
             }
-            if (++spins > kSpinLimit || globaltimer_ns() - t0 > kSpinTimeoutNs) {
-                atomicOr(err, kErrTimeout);
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -573,17 +579,6 @@ __device__ bool team_solve(int64_t n, const Fac& f, const double* bsrc, double f
     return true;
 }
 
-// ------------------------------------------------------------------------------------------
-// CTA-wide products used by the reorthogonalization.
-//
-// coldots: out(i, sum_{rho in R(i)} A[rho + i lda] x[rho]) for columns i in [c0, c1), with
-//   R(i) = [max(rlo, i), rhi)    (LOWER: the nonzeros of a lower-trapezoidal column), or
-//   R(i) = [rlo, min(rhi, i+1))  (UPPER: the nonzeros of an upper-triangular column).
-// rowdots: out(rho, sum_{i in C(rho)} A[rho + i lda] x[i]) for rows rho in [r0, r1), with
-//   C(rho) = [0, min(ccap, rho+1))  (LOWERCOL),  [rho, ccap)  (UPPERCOL),  [0, ccap)  (ALL).
-// When there are fewer columns (rows) than threads, each is split into S segments whose
-// partial sums are added in segment order; `red` holds >= 2*blockDim doubles.
-// ------------------------------------------------------------------------------------------
 enum ColKind { kLower = 0, kUpper = 1 };
 enum RowKind { kLowerCol = 0, kUpperCol = 1, kAllCols = 2 };
 
@@ -687,17 +682,19 @@ __device__ __forceinline__ void dot2_range(const double* __restrict__ p, int64_t
 // rowdots: out(rho, sum_{i in C(rho)} A[rho + i lda] x[i]) for rows rho in [r0, r1), with
 //   C(rho) = [0, min(ccap, rho+1))  (LOWERCOL),  [rho, ccap)  (UPPERCOL),  [0, ccap)  (ALL).
 //   One thread per (row, column segment): a warp reads 32 consecutive rows of a column.
-// When there are fewer columns (rows) than threads, each is split into S segments whose
-// partial sums are added in segment order; `red` holds >= 2*blockDim doubles.
+// When there are fewer columns (rows) than threads, each is split into S segments, each
+// segment a whole number of warps, whose partial sums are added by a fixed-shape tree (so the
+// result does not depend on scheduling); `red` holds >= 2*blockDim doubles.
 // ------------------------------------------------------------------------------------------
 template <int KIND, class Out>
 __device__ void cta_coldots(const double* __restrict__ A, int64_t lda, int64_t c0, int64_t c1,
                             int64_t rlo, int64_t rhi, const double* x, double* red, Out out)
 {
-    const int B = blockDim.x, t = threadIdx.x;
+    const int B = blockDim.x, t = threadIdx.x, nW = B >> 5, wid = t >> 5, lane = t & 31;
     const int64_t nc = c1 - c0;
     if (nc <= 0) return;
-    if (nc >= B) {
+    const int64_t wpc = (nc + 31) / 32;  // warps that cover the columns once
+    if (wpc >= nW) {
         for (int64_t base = c0; base < c1; base += B) {
             const int64_t i = base + t;
             const bool act = i < c1;
@@ -711,13 +708,16 @@ __device__ void cta_coldots(const double* __restrict__ A, int64_t lda, int64_t c
         __syncthreads();
         return;
     }
+    // S row segments per column, each segment a whole number of warps
     int S = 1;
-    while (S < 32 && (int64_t)(2 * S) * nc <= B) S *= 2;
-    const int64_t ci = t % nc;
-    const int sg = (int)(t / nc);
-    const bool act = sg < S;
+    while (S < 32 && (int64_t)(2 * S) * wpc <= nW) S *= 2;
+    const int W = (int)wpc * 32;
+    const int sg = wid / (int)wpc;
+    const int64_t ci = (int64_t)(wid % (int)wpc) * 32 + lane;
+    const bool inseg = sg < S;
+    const bool act = inseg && ci < nc;
+    const int64_t i = c0 + (act ? ci : 0);
     int64_t a = 0, b = 0;
-    const int64_t i = c0 + ci;
     if (act) {
         const int64_t lo0 = (KIND == kLower) ? max(rlo, i) : rlo;
         const int64_t hi0 = (KIND == kLower) ? rhi : min(rhi, i + 1);
@@ -730,13 +730,13 @@ __device__ void cta_coldots(const double* __restrict__ A, int64_t lda, int64_t c
     int64_t lo, hi;
     warp_core(a, b, act && a < b, lo, hi);
     const double s = dot_range<1>(A + i * lda, 1, x, a, b, lo, hi, act);
-    if (act) red[sg * nc + ci] = s;
+    if (inseg) red[sg * W + (int)ci] = act ? s : 0.0;
     __syncthreads();
-    if (t < nc) {
-        double v = red[t];
-        for (int q = 1; q < S; ++q) v += red[q * nc + t];
-        out(c0 + t, v);
+    for (int st = S >> 1; st >= 1; st >>= 1) {  // fixed-shape tree over the segments
+        if (sg < st) red[sg * W + (int)ci] += red[(sg + st) * W + (int)ci];
+        __syncthreads();
     }
+    if (sg == 0 && act) out(c0 + ci, red[ci]);
     __syncthreads();
 }
 
@@ -744,10 +744,11 @@ template <int KIND, int NV, class Out>
 __device__ void cta_rowdots(const double* __restrict__ A, int64_t lda, int64_t r0, int64_t r1,
                             int64_t ccap, const double* x0, const double* x1, double* red, Out out)
 {
-    const int B = blockDim.x, t = threadIdx.x;
+    const int B = blockDim.x, t = threadIdx.x, nW = B >> 5, wid = t >> 5, lane = t & 31;
     const int64_t nr = r1 - r0;
     if (nr <= 0) return;
-    if (nr >= B) {
+    const int64_t wpr = (nr + 31) / 32;  // warps that cover the rows once
+    if (wpr >= nW) {
         for (int64_t base = r0; base < r1; base += B) {
             const int64_t rho = base + t;
             const bool act = rho < r1;
@@ -766,11 +767,13 @@ __device__ void cta_rowdots(const double* __restrict__ A, int64_t lda, int64_t r
         return;
     }
     int S = 1;
-    while (S < 32 && (int64_t)(2 * S) * nr <= B) S *= 2;
-    const int64_t ri = t % nr;
-    const int sg = (int)(t / nr);
-    const bool act = sg < S;
-    const int64_t rho = r0 + ri;
+    while (S < 32 && (int64_t)(2 * S) * wpr <= nW) S *= 2;
+    const int W = (int)wpr * 32;
+    const int sg = wid / (int)wpr;
+    const int64_t ri = (int64_t)(wid % (int)wpr) * 32 + lane;
+    const bool inseg = sg < S;
+    const bool act = inseg && ri < nr;
+    const int64_t rho = r0 + (act ? ri : 0);
     int64_t a = 0, b = 0;
     if (act) {
         // fixed column grid over the columns any row of [r0, r1) can touch
@@ -793,19 +796,19 @@ __device__ void cta_rowdots(const double* __restrict__ A, int64_t lda, int64_t r
         dot2_range<0>(A + rho, lda, x0, x1, a, b, lo, hi, act, s0, s1);
     else
         s0 = dot_range<0>(A + rho, lda, x0, a, b, lo, hi, act);
-    if (act) {
-        red[(sg * nr + ri) * NV] = s0;
-        if (NV == 2) red[(sg * nr + ri) * NV + 1] = s1;
+    if (inseg) {
+        red[(sg * W + (int)ri) * NV] = act ? s0 : 0.0;
+        if (NV == 2) red[(sg * W + (int)ri) * NV + 1] = act ? s1 : 0.0;
     }
     __syncthreads();
-    if (t < nr) {
-        double v0 = red[t * NV], v1 = (NV == 2) ? red[t * NV + 1] : 0.0;
-        for (int q = 1; q < S; ++q) {
-            v0 += red[(q * nr + t) * NV];
-            if (NV == 2) v1 += red[(q * nr + t) * NV + 1];
+    for (int st = S >> 1; st >= 1; st >>= 1) {
+        if (sg < st) {
+            red[(sg * W + (int)ri) * NV] += red[((sg + st) * W + (int)ri) * NV];
+            if (NV == 2) red[(sg * W + (int)ri) * NV + 1] += red[((sg + st) * W + (int)ri) * NV + 1];
         }
-        out(r0 + t, v0, v1);
+        __syncthreads();
     }
+    if (sg == 0 && act) out(r0 + ri, red[(int)ri * NV], (NV == 2) ? red[(int)ri * NV + 1] : 0.0);
     __syncthreads();
 }
 

@@ -22,7 +22,7 @@ enum ChainMode : int32_t { kModeInvit = 0, kModeOrth = 1 };
 // Byte offsets of every device array inside one workspace allocation.
 struct Layout {
     size_t scal, wp, head, clstart, clsize, cltoff, sched, queue, ctr, bar;
-    size_t fl, fu1, fu2, fr, fpiv, u0n;
+    size_t fl, fu1, fu2, fr, fpiv, u0n, tolv;
     size_t Y, T, partS, partG, partScal, vecS, vecX, vecR, qbuf, vbuf, tpub, gvec;
     size_t total;
 };
@@ -65,6 +65,7 @@ struct Ws {
     double *fl, *fu1, *fu2, *fr;  // [m*n] LU factors, row j = shift j
     uint8_t* fpiv;    // [m*n]
     double* u0n;      // [m]   |u_nn| before perturbation
+    double* tolv;     // [m]   tiny-pivot threshold eps max|U| per shift
     double* Y;        // [n*m]
     double* T;        // [m*m]
     double *partS, *partG;  // [P*n]
@@ -82,9 +83,12 @@ Ws bind_layout(void* base, const Layout& L, int64_t n, int64_t m, int32_t P);
 
 // Kernel launchers (tinv_kernels.cu).  All enqueue on `st` and return cudaGetLastError().
 cudaError_t launch_plan(const Problem& p, const Ws& w, int32_t max_team, cudaStream_t st);
+// LU of T - shift_j I for all j.  With tolv != null the diagonal is turned into perturbed
+// reciprocals r = 1/u0 (solve-ready) and tolv[j] receives the tiny-pivot threshold; with
+// tolv == null u0 is left as is.
 cudaError_t launch_lu(int64_t n, const double* d, const double* e, int64_t m, const double* shift,
                       double* l, double* u0_or_r, double* u1, double* u2, uint8_t* piv,
-                      double* u0n, int store_reciprocal, cudaStream_t st);
+                      double* u0n, double* tolv, cudaStream_t st);
 cudaError_t launch_first(const Problem& p, const Ws& w, cudaStream_t st);
 cudaError_t launch_chain(const Problem& p, const Ws& w, int32_t mode, const double* V, int64_t ldv,
                          cudaStream_t st);

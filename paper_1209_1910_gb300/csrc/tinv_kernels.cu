@@ -261,10 +261,38 @@ __global__ void k_orth_plan(int64_t m, Ws w, int32_t method)
 // LU of T - s I with scaled partial pivoting, one thread per shift (bit-exact: explicit
 // round-to-nearest operations, no contraction).  Row j of each output holds shift j.
 // ==========================================================================================
+
+// Interchange decision of the scaled pivoting rule: true iff fl(|c|/s2) > fl(|a|/s1) (the rule
+// written with correctly rounded quotients; a zero numerator counts as 0).  Most steps are
+// decided from the cross products |c| s1 and |a| s2: when they differ by more than a relative
+// 2^-49 the rounded quotients are ordered the same way (each quotient and product carries at
+// most 2^-53 relative rounding error), so the divisions are only evaluated inside that band or
+// when a product is not a normal number.
+__device__ __forceinline__ bool lu_interchange(double aa, double s1, double cc, double s2)
+{
+    if (cc == 0.0) return false;
+    if (aa == 0.0) return true;
+    const double P = __dmul_rn(cc, s1);  // |c| s1
+    const double Q = __dmul_rn(aa, s2);  // |a| s2
+    const double kMarg = 1.0 + 1.7763568394002505e-15;  // 1 + 2^-49
+    const bool normal = (P >= 2.2250738585072014e-308) && (Q >= 2.2250738585072014e-308) &&
+                        (P <= 1.0e300) && (Q <= 1.0e300);
+    if (normal) {
+        if (P > __dmul_rn(Q, kMarg)) return true;
+        if (Q > __dmul_rn(P, kMarg)) return false;
+    }
+    return __ddiv_rn(cc, s2) > __ddiv_rn(aa, s1);
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
 __global__ void k_lu(int64_t n, const double* __restrict__ d, const double* __restrict__ e,
                      int64_t m, const double* __restrict__ shift, double* __restrict__ L,
                      double* __restrict__ U0, double* __restrict__ U1, double* __restrict__ U2,
-                     uint8_t* __restrict__ PV, double* __restrict__ u0n, int store_reciprocal)
+                     uint8_t* __restrict__ PV, double* __restrict__ u0n, double* __restrict__ tolv)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
@@ -277,18 +305,16 @@ __global__ void k_lu(int64_t n, const double* __restrict__ d, const double* __re
     uint8_t* pv = PV + base;
     double ak = __dsub_rn(d[0], lam);
     double bk = (n > 1) ? e[0] : 0.0;
-    double umax = 0.0;
+    unsigned long long umax = 0;  // max |U entry| as the bit pattern of a non-negative double
     for (int64_t k = 0; k + 1 < n; ++k) {
         const double ck = e[k];
         const double a1 = __dsub_rn(d[k + 1], lam);
         const double b1 = (k + 2 < n) ? e[k + 1] : 0.0;
         const double scale1 = __dadd_rn(fabs(ak), fabs(bk));
         const double scale2 = __dadd_rn(__dadd_rn(fabs(ck), fabs(a1)), fabs(b1));
-        const double piv1 = (ak == 0.0) ? 0.0 : __ddiv_rn(fabs(ak), scale1);
-        const double piv2 = (ck == 0.0) ? 0.0 : __ddiv_rn(fabs(ck), scale2);
         double lk, w0, w1, w2;
         uint8_t sw;
-        if (piv2 <= piv1) {
+        if (!lu_interchange(fabs(ak), scale1, fabs(ck), scale2)) {
             lk = (ck == 0.0) ? 0.0 : __ddiv_rn(ck, ak);
             w0 = ak;
             w1 = bk;
@@ -310,23 +336,34 @@ __global__ void k_lu(int64_t n, const double* __restrict__ d, const double* __re
         u1[k] = w1;
         u2[k] = w2;
         pv[k] = sw;
-        umax = fmax(umax, fmax(fabs(w0), fmax(fabs(w1), fabs(w2))));
+        umax = max(umax, max(abs_bits(w0), max(abs_bits(w1), abs_bits(w2))));
     }
     u0[n - 1] = ak;
     l[n - 1] = 0.0;
     u1[n - 1] = 0.0;
     u2[n - 1] = 0.0;
     pv[n - 1] = 0;
-    umax = fmax(umax, fabs(ak));
+    umax = max(umax, abs_bits(ak));
     if (u0n) u0n[j] = fabs(ak);
-    if (store_reciprocal) {
-        // tiny pivots: |u0_k| < tol = eps * max|U| -> sign(u0_k) * tol (sign(0) = +)
-        double tol = __dmul_rn(kEps, umax);
+    if (tolv) {
+        // tiny-pivot threshold tol = eps * max|U| (eps if U = 0)
+        double tol = __dmul_rn(kEps, __longlong_as_double((long long)umax));
         if (tol == 0.0) tol = kEps;
-        for (int64_t k = 0; k < n; ++k) {
-            double a = u0[k];
+        tolv[j] = tol;
+    }
+}
+
+// r = 1/u0 with tiny pivots |u0| < tol replaced by sign(u0) tol (sign(0) = +), in place,
+// for every (shift, row): all m*n entries in parallel.
+__global__ void k_recip(int64_t n, int64_t m, double* __restrict__ U0R, const double* __restrict__ tolv)
+{
+    for (int64_t j = blockIdx.x; j < m; j += gridDim.x) {
+        const double tol = tolv[j];
+        double* row = U0R + (size_t)j * (size_t)n;
+        for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+            double a = row[k];
             if (fabs(a) < tol) a = (a >= 0.0) ? tol : -tol;
-            u0[k] = __drcp_rn(a);
+            row[k] = __drcp_rn(a);
         }
     }
 }
@@ -506,6 +543,16 @@ struct QStats {
     int64_t arg;
 };
 
+// Warp-wide sum of slot `slot` of the per-rank scalar blocks of a team (lane-strided partial
+// sums, then a fixed xor tree); called by a whole warp, every lane receives the result.
+__device__ __forceinline__ double team_sum_slot(const double* scal_t, int G, int slot)
+{
+    const int lane = threadIdx.x & 31;
+    double a = 0.0;
+    for (int r = lane; r < G; r += 32) a += __ldcg(&scal_t[r * kScalTeam + slot]);
+    return warp_sum(a);
+}
+
 // ---- compact-WY processing of one cluster by a team (Alg. 4, Sec. 3.3.2) -----------------
 __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
 {
@@ -550,17 +597,18 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
         ss = block_sum(ss, red);
         if (t == 0) scal_t[rank * kScalTeam + 6] = ss;
         if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
-        if (t == 0) {
-            double tot = 0.0;
-            for (int r = 0; r < G; ++r) tot += __ldcg(&scal_t[r * kScalTeam + 6]);
+        if (t < 32) {
+            const double tot = team_sum_slot(scal_t, G, 6);
             const double nrm = sqrt(tot);
             const double z0 = z[0];
             const bool broke = !(nrm > 0.0) || !isfinite(nrm);
             const double cc = broke ? -1.0 : -sgn(z0) * nrm;
             const double u11 = broke ? 1.0 : z0;
-            s_b[0] = cc;
-            s_b[1] = 1.0 / (cc * cc - u11 * cc);
-            s_b[2] = broke ? 1.0 : 0.0;
+            if (t == 0) {
+                s_b[0] = cc;
+                s_b[1] = 1.0 / (cc * cc - u11 * cc);
+                s_b[2] = broke ? 1.0 : 0.0;
+            }
         }
         __syncthreads();
         const double cc = s_b[0];
@@ -650,20 +698,19 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
             PROF_MARK(cx.prof, kPhB3);
             // ---- reflector (Eq. yt with t = 1/(c^2 - u_kk c), Sec. 3.3.2) ----
-            if (t == 0) {
-                double tot = 0.0, ukk = 0.0;
-                for (int r = 0; r < G; ++r) {
-                    tot += __ldcg(&scal_t[r * kScalTeam + 0]);
-                    ukk += __ldcg(&scal_t[r * kScalTeam + 1]);
-                }
+            if (t < 32) {
+                const double tot = team_sum_slot(scal_t, G, 0);
+                const double ukk = team_sum_slot(scal_t, G, 1);
                 const double nrm = sqrt(tot);
                 const bool broke = !(nrm > 0.0) || !isfinite(nrm);
                 const double cc = broke ? -1.0 : -sgn(ukk) * nrm;
                 const double ue = broke ? 1.0 : ukk;
-                s_b[0] = cc;
-                s_b[1] = 1.0 / (cc * cc - ue * cc);  // t_k
-                s_b[2] = ue - cc;                    // y_kk
-                s_b[3] = broke ? 1.0 : 0.0;
+                if (t == 0) {
+                    s_b[0] = cc;
+                    s_b[1] = 1.0 / (cc * cc - ue * cc);  // t_k
+                    s_b[2] = ue - cc;                    // y_kk
+                    s_b[3] = broke ? 1.0 : 0.0;
+                }
             }
             __syncthreads();
             const double cc = s_b[0], tk = s_b[1], ykk = s_b[2];
@@ -754,12 +801,12 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 break;
             }
             // ---- team statistics, convergence test on x = -c q (||x||_inf = |c| max|q|) ----
-            if (t == 0) {
-                double A1 = 0.0, S2 = 0.0, M = -1.0;
+            if (t < 32) {
+                const double A1 = team_sum_slot(scal_t, G, 2);
+                const double S2 = team_sum_slot(scal_t, G, 5);
+                double M = -1.0;
                 int64_t I = n;
-                for (int r = 0; r < G; ++r) {
-                    A1 += __ldcg(&scal_t[r * kScalTeam + 2]);
-                    S2 += __ldcg(&scal_t[r * kScalTeam + 5]);
+                for (int r = t; r < G; r += 32) {
                     const double mr = __ldcg(&scal_t[r * kScalTeam + 3]);
                     const int64_t ir = (int64_t)__ldcg(&scal_t[r * kScalTeam + 4]);
                     if (mr > M || (mr == M && ir < I)) {
@@ -767,10 +814,13 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                         I = ir;
                     }
                 }
-                s_b[4] = A1;
-                s_b[5] = M;
-                s_b[6] = S2;
-                s_arg = (I >= 0 && I < n) ? I : 0;  // all-NaN guard
+                warp_argmax(M, I);
+                if (t == 0) {
+                    s_b[4] = A1;
+                    s_b[5] = M;
+                    s_b[6] = S2;
+                    s_arg = (I >= 0 && I < n) ? I : 0;  // all-NaN guard
+                }
             }
             __syncthreads();
             const double A1 = s_b[4], M = s_b[5], S2 = s_b[6];
@@ -1013,12 +1063,19 @@ cudaError_t launch_orth_plan(int64_t m, const Ws& w, int32_t method, cudaStream_
 
 cudaError_t launch_lu(int64_t n, const double* d, const double* e, int64_t m, const double* shift,
                       double* l, double* u0_or_r, double* u1, double* u2, uint8_t* piv,
-                      double* u0n, int store_reciprocal, cudaStream_t st)
+                      double* u0n, double* tolv, cudaStream_t st)
 {
     if (m <= 0) return cudaSuccess;
-    const int th = 128;
+    const int th = 32;  // one warp per block spreads the sequential factorizations over SMs
     const unsigned blocks = (unsigned)((m + th - 1) / th);
-    k_lu<<<blocks, th, 0, st>>>(n, d, e, m, shift, l, u0_or_r, u1, u2, piv, u0n, store_reciprocal);
+    k_lu<<<blocks, th, 0, st>>>(n, d, e, m, shift, l, u0_or_r, u1, u2, piv, u0n, tolv);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess || !tolv) return err;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned rb = (unsigned)min(m, (int64_t)(sms > 0 ? sms : 1) * 8);
+    k_recip<<<rb, 256, 0, st>>>(n, m, u0_or_r, tolv);
     return cudaGetLastError();
 }
 
