@@ -202,6 +202,7 @@ int enqueue_tinv(const Problem& p, void* ws, int32_t P, int32_t max_team, cudaSt
     if (e == cudaSuccess) e = launch_first(p, w, st);
     if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[3], st);
     if (e == cudaSuccess) e = launch_chain(p, w, kModeInvit, nullptr, 0, st);
+    if (e == cudaSuccess && p.method == TINV_CWY) e = launch_finalize(p, w, st);
     if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[4], st);
     if (e == cudaSuccess && phase_ms) {
         e = cudaEventSynchronize(ev[4]);
@@ -247,7 +248,7 @@ size_t tinv_workspace_size(int64_t n, int64_t m, const tinv_opts* o)
 {
     if (n < 0 || m < 0) return 0;
     const Opts op(o);
-    const int32_t P = chain_grid(op.o.grid_ctas);
+    const int32_t P = chain_grid(op.o.grid_ctas, n);
     return make_layout(n, m, P, true).total;
 }
 
@@ -274,7 +275,7 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
     p.method = op.o.method;
     p.seed = op.o.seed;
     p.j0 = op.o.j0;
-    const int32_t P = chain_grid(op.o.grid_ctas);
+    const int32_t P = chain_grid(op.o.grid_ctas, n);
 
     if (op.o.device_ptrs) {
         cudaStream_t st = (cudaStream_t)op.o.stream;
@@ -404,7 +405,7 @@ int tinv_plan(int64_t n, const double* d, const double* e, int64_t m, const doub
     if (m > 0 && !wp) return -6;
     if (m > 0 && !head) return -7;
     if (!scal) return -8;
-    const int32_t P = chain_grid(op.o.grid_ctas);
+    const int32_t P = chain_grid(op.o.grid_ctas, n);
     const Layout L = make_layout(n, m, P, false);
     Problem p;
     memset(&p, 0, sizeof(p));
@@ -528,7 +529,7 @@ int tinv_solve(int64_t n, const double* d, const double* e, int64_t m, const dou
     if (m > 0 && !X) return -6;
     if (ldx < n) return -7;
     if (m == 0) return 0;
-    const int32_t P = chain_grid(op.o.grid_ctas);
+    const int32_t P = chain_grid(op.o.grid_ctas, n);
     const Layout L = make_layout(n, m, P, false);
     Problem p;
     memset(&p, 0, sizeof(p));
@@ -604,7 +605,7 @@ int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int
     if (ldq < n) return -6;
     if (op.o.method != TINV_CWY && op.o.method != TINV_MGS) return -9;
     if (m == 0) return 0;
-    int32_t P = chain_grid(op.o.grid_ctas);
+    int32_t P = chain_grid(op.o.grid_ctas, n);
     const Layout L = make_layout(n, m, P, true);
     Problem p;
     memset(&p, 0, sizeof(p));

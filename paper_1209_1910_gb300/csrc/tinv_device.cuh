@@ -331,7 +331,7 @@ __device__ void chunk_solve(int64_t n, const Fac& f, double* x, double* sh, int 
 //   vsm   : row-indexed scratch of the CTA (n slots); on return vsm[r0..r1) = x.
 //   vout  : if not null, also receives x[r0..r1) (global, for other CTAs of the team).
 //   pubf, pubb : team buffers of 2 and 6 doubles per rank for the published maps.
-//   sh    : >= 128 doubles of shared scratch.
+//   sh    : >= 128 + 6 G doubles of shared scratch.
 // ------------------------------------------------------------------------------------------
 struct TeamRef {
     uint32_t* bar;
@@ -356,7 +356,7 @@ __device__ __forceinline__ void compose2(double& m00, double& m01, double& m10, 
     f1 = b1;
 }
 
-__device__ bool team_solve(int64_t n, const Fac& f, const double* bsrc, double fac, double* vsm,
+__device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* bsrc, double fac, double* vsm,
                            double* vout, int64_t r0, int64_t r1, double* pubf, double* pubb,
                            TeamRef tr, double* sh)
 {
@@ -425,13 +425,19 @@ __device__ bool team_solve(int64_t n, const Fac& f, const double* bsrc, double f
         pubf[2 * tr.rank + 1] = CB;
     }
     if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+    double* pf = sh + 128;  // the published forward maps of the CTAs before this one
+    for (int q = t; q < tr.rank; q += B) {
+        pf[2 * q] = __ldcg(&pubf[2 * q]);
+        pf[2 * q + 1] = __ldcg(&pubf[2 * q + 1]);
+    }
+    __syncthreads();
     if (t == 0) {
         double c;
         if (tr.rank == 0) {
             c = vsm[r0];
         } else {
             c = bsrc[0] * fac;
-            for (int q = 0; q < tr.rank; ++q) c = fma(__ldcg(&pubf[2 * q]), c, __ldcg(&pubf[2 * q + 1]));
+            for (int q = 0; q < tr.rank; ++q) c = fma(pf[2 * q], c, pf[2 * q + 1]);
         }
         for (int w2 = 0; w2 < NW; ++w2) {
             sh[16 + w2] = c;
@@ -543,12 +549,16 @@ __device__ bool team_solve(int64_t n, const Fac& f, const double* bsrc, double f
         o[5] = c1;
     }
     if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+    double* pb = sh + 128;  // the published back maps of the CTAs after this one
+    for (int q = tr.rank + 1 + t; q < tr.G; q += B)
+        for (int u = 0; u < 6; ++u) pb[6 * q + u] = __ldcg(&pubb[6 * q + u]);
+    __syncthreads();
     if (t == 0) {
         double s0 = 0.0, s1 = 0.0;  // x_n = x_{n+1} = 0 below the last CTA
         for (int q = tr.G - 1; q > tr.rank; --q) {
-            const double* o = pubb + 6 * q;
-            const double n0 = fma(__ldcg(&o[0]), s0, fma(__ldcg(&o[1]), s1, __ldcg(&o[4])));
-            const double n1 = fma(__ldcg(&o[2]), s0, fma(__ldcg(&o[3]), s1, __ldcg(&o[5])));
+            const double* o = pb + 6 * q;
+            const double n0 = fma(o[0], s0, fma(o[1], s1, o[4]));
+            const double n1 = fma(o[2], s0, fma(o[3], s1, o[5]));
             s0 = n0;
             s1 = n1;
         }
@@ -596,80 +606,122 @@ __device__ __forceinline__ void warp_core(int64_t a, int64_t b, bool act, int64_
     hi = lb;
 }
 
-// sum over r in [a, b) of p[r * stride] * x[r]  (core part [lo, hi) is warp-uniform, unrolled by
-// 8 with all loads issued before the FMAs; the rest is per-lane)
-template <int STRIDE1>
-__device__ __forceinline__ double dot_range(const double* __restrict__ p, int64_t stride,
+// Sum over rows r in [a, b) with r = ph (mod P) of p[r] x[r] (absolute phase), the
+// warp-uniform core [lo, hi) (multiples of P) unrolled by 8 with all loads issued first.
+template <int P>
+__device__ __forceinline__ double dot_phase(const double* __restrict__ p, int64_t st,
                                             const double* x, int64_t a, int64_t b, int64_t lo,
-                                            int64_t hi, bool act)
+                                            int64_t hi, int ph, bool act)
 {
     double acc0 = 0.0, acc1 = 0.0;
-    if (!act) return 0.0;
-    const int64_t st = STRIDE1 ? 1 : stride;
-    if (lo < hi && lo >= a && hi <= b) {
-        for (int64_t r = a; r < lo; ++r) acc0 = fma(p[r * st], x[r], acc0);
-        int64_t r = lo;
-        for (; r + 8 <= hi; r += 8) {
+    if (!act || b <= a) return 0.0;
+    const bool core = lo < hi && lo >= a && hi <= b;
+    const int64_t pe = core ? lo : b;
+    for (int64_t r = a + ((ph - a) & (P - 1)); r < pe; r += P) acc0 = fma(p[r * st], x[r], acc0);
+    if (core) {
+        int64_t r = lo + ph;
+        for (; r + 7 * P < hi; r += 8 * P) {
             double v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = p[(r + u) * st];
+            for (int u = 0; u < 8; ++u) v[u] = p[(r + u * P) * st];
 #pragma unroll
             for (int u = 0; u < 8; u += 2) {
-                acc0 = fma(v[u], x[r + u], acc0);
-                acc1 = fma(v[u + 1], x[r + u + 1], acc1);
+                acc0 = fma(v[u], x[r + u * P], acc0);
+                acc1 = fma(v[u + 1], x[r + (u + 1) * P], acc1);
             }
         }
-        for (; r < hi; ++r) acc0 = fma(p[r * st], x[r], acc0);
-        for (r = hi; r < b; ++r) acc1 = fma(p[r * st], x[r], acc1);
-    } else {
-        for (int64_t r = a; r < b; ++r) acc0 = fma(p[r * st], x[r], acc0);
+        for (; r < hi; r += P) acc0 = fma(p[r * st], x[r], acc0);
+        for (r = hi + ((ph - hi) & (P - 1)); r < b; r += P) acc1 = fma(p[r * st], x[r], acc1);
     }
     return acc0 + acc1;
 }
 
-// Two dot products sharing the loads of p.
-template <int STRIDE1>
-__device__ __forceinline__ void dot2_range(const double* __restrict__ p, int64_t stride,
+template <int P>
+__device__ __forceinline__ void dot2_phase(const double* __restrict__ p, int64_t st,
                                            const double* x, const double* y, int64_t a, int64_t b,
-                                           int64_t lo, int64_t hi, bool act, double& ox, double& oy)
+                                           int64_t lo, int64_t hi, int ph, bool act, double& ox,
+                                           double& oy)
 {
     double ax0 = 0.0, ax1 = 0.0, ay0 = 0.0, ay1 = 0.0;
     ox = oy = 0.0;
-    if (!act) return;
-    const int64_t st = STRIDE1 ? 1 : stride;
-    if (lo < hi && lo >= a && hi <= b) {
-        for (int64_t r = a; r < lo; ++r) {
+    if (!act || b <= a) return;
+    const bool core = lo < hi && lo >= a && hi <= b;
+    const int64_t pe = core ? lo : b;
+    for (int64_t r = a + ((ph - a) & (P - 1)); r < pe; r += P) {
+        const double v = p[r * st];
+        ax0 = fma(v, x[r], ax0);
+        ay0 = fma(v, y[r], ay0);
+    }
+    if (core) {
+        int64_t r = lo + ph;
+        for (; r + 7 * P < hi; r += 8 * P) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = p[(r + u * P) * st];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                ax0 = fma(v[u], x[r + u * P], ax0);
+                ay0 = fma(v[u], y[r + u * P], ay0);
+                ax1 = fma(v[u + 1], x[r + (u + 1) * P], ax1);
+                ay1 = fma(v[u + 1], y[r + (u + 1) * P], ay1);
+            }
+        }
+        for (; r < hi; r += P) {
             const double v = p[r * st];
             ax0 = fma(v, x[r], ax0);
             ay0 = fma(v, y[r], ay0);
         }
-        int64_t r = lo;
-        for (; r + 8 <= hi; r += 8) {
-            double v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = p[(r + u) * st];
-#pragma unroll
-            for (int u = 0; u < 8; u += 2) {
-                ax0 = fma(v[u], x[r + u], ax0);
-                ay0 = fma(v[u], y[r + u], ay0);
-                ax1 = fma(v[u + 1], x[r + u + 1], ax1);
-                ay1 = fma(v[u + 1], y[r + u + 1], ay1);
-            }
-        }
-        for (; r < b; ++r) {
+        for (r = hi + ((ph - hi) & (P - 1)); r < b; r += P) {
             const double v = p[r * st];
             ax1 = fma(v, x[r], ax1);
             ay1 = fma(v, y[r], ay1);
         }
-    } else {
-        for (int64_t r = a; r < b; ++r) {
-            const double v = p[r * st];
-            ax0 = fma(v, x[r], ax0);
-            ay0 = fma(v, y[r], ay0);
-        }
     }
     ox = ax0 + ax1;
     oy = ay0 + ay1;
+}
+
+// Warp-uniform core of per-lane ranges, shrunk to multiples of P.
+template <int P>
+__device__ __forceinline__ void warp_core_al(int64_t a, int64_t b, bool act, int64_t& lo, int64_t& hi)
+{
+    warp_core(a, b, act, lo, hi);
+    lo = (lo + (P - 1)) & ~(int64_t)(P - 1);
+    hi = hi & ~(int64_t)(P - 1);
+}
+
+// Number of segments 2^lS (lS <= lmax) that minimizes the modelled cost of `groups` warp units
+// of `work` FMA instructions per lane, each split into 2^lS pieces: rounds over the nW warps
+// times (work per piece + a fixed per-piece overhead) plus the tree levels that add the pieces
+// back.  Integer arithmetic only.
+__device__ __forceinline__ int pick_segments(int64_t groups, int64_t work, int nW, int lmax)
+{
+    constexpr int64_t kOvh = 8, kTree = 6;
+    int best_l = 0;
+    int64_t best = ((groups + nW - 1) / nW) * (work + kOvh);
+    for (int l = 1; l <= lmax; ++l) {
+        const int64_t units = groups << l;
+        const int64_t cost = ((units + nW - 1) / nW) * (((work + (1 << l) - 1) >> l) + kOvh) + kTree * l;
+        if (cost < best) {
+            best = cost;
+            best_l = l;
+        }
+    }
+    return best_l;
+}
+
+// Add the S segment partials red[sg*len + c] (c < len, NV values each) by a fixed-shape tree.
+__device__ __forceinline__ void tree_segments(double* red, int S, int64_t len, int NV)
+{
+    // segment stride len*NV <= 2048, so 32-bit indices suffice; segment sg of the lower half
+    // takes in segment sg + st
+    const int L = (int)(len * NV);
+    for (int st = S >> 1; st >= 1; st >>= 1) {
+        __syncthreads();
+        const int cnt = st * L;
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) red[q] += red[q + st * L];
+    }
+    __syncthreads();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -678,65 +730,142 @@ __device__ __forceinline__ void dot2_range(const double* __restrict__ p, int64_t
 // coldots: out(i, sum_{rho in R(i)} A[rho + i lda] x[rho]) for columns i in [c0, c1), with
 //   R(i) = [max(rlo, i), rhi)    (LOWER: the nonzeros of a lower-trapezoidal column), or
 //   R(i) = [rlo, min(rhi, i+1))  (UPPER: the nonzeros of an upper-triangular column).
-//   One thread per (column, row segment): each thread streams down its own column.
+//   A warp takes 8 columns; its lanes are 8 columns x 4 row phases, so each load instruction
+//   reads 4 consecutive rows of 8 columns, and the 4 phase partials are added by 2 shuffles.
 // rowdots: out(rho, sum_{i in C(rho)} A[rho + i lda] x[i]) for rows rho in [r0, r1), with
 //   C(rho) = [0, min(ccap, rho+1))  (LOWERCOL),  [rho, ccap)  (UPPERCOL),  [0, ccap)  (ALL).
-//   One thread per (row, column segment): a warp reads 32 consecutive rows of a column.
-// When there are fewer columns (rows) than threads, each is split into S segments, each
-// segment a whole number of warps, whose partial sums are added by a fixed-shape tree (so the
-// result does not depend on scheduling); `red` holds >= 2*blockDim doubles.
+//   A warp takes RL = 32, 16 or 8 consecutive rows (fewer rows, more column phases).
+// The rows (columns) of the dot products are split into S segments when that fills the warps
+// better; segment partials are added by a fixed-shape tree, so results do not depend on
+// scheduling.  `red` holds >= 2048 doubles.
 // ------------------------------------------------------------------------------------------
 template <int KIND, class Out>
-__device__ void cta_coldots(const double* __restrict__ A, int64_t lda, int64_t c0, int64_t c1,
+__device__ __noinline__ void cta_coldots(const double* __restrict__ A, int64_t lda, int64_t c0, int64_t c1,
                             int64_t rlo, int64_t rhi, const double* x, double* red, Out out)
 {
-    const int B = blockDim.x, t = threadIdx.x, nW = B >> 5, wid = t >> 5, lane = t & 31;
+    const int nW = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cl = lane >> 2, ph = lane & 3;
     const int64_t nc = c1 - c0;
     if (nc <= 0) return;
-    const int64_t wpc = (nc + 31) / 32;  // warps that cover the columns once
-    if (wpc >= nW) {
-        for (int64_t base = c0; base < c1; base += B) {
-            const int64_t i = base + t;
-            const bool act = i < c1;
-            const int64_t a = act ? ((KIND == kLower) ? max(rlo, i) : rlo) : 0;
-            const int64_t b = act ? ((KIND == kLower) ? rhi : min(rhi, i + 1)) : 0;
-            int64_t lo, hi;
-            warp_core(a, b, act && a < b, lo, hi);
-            const double s = dot_range<1>(A + (act ? i : 0) * lda, 1, x, a, b, lo, hi, act);
-            if (act) out(i, s);
+    if (nc <= nW) {
+        // few columns: one warp per column, lanes along its rows, one shuffle reduction
+        if (wid < nc) {
+            const int64_t i = c0 + wid;
+            const int64_t a = (KIND == kLower) ? max(rlo, i) : rlo;
+            const int64_t b = (KIND == kLower) ? rhi : min(rhi, i + 1);
+            const double* p = A + i * lda;
+            double acc0 = 0.0, acc1 = 0.0;
+            int64_t r = a + lane;
+            for (; r + 32 < b; r += 64) {
+                acc0 = fma(p[r], x[r], acc0);
+                acc1 = fma(p[r + 32], x[r + 32], acc1);
+            }
+            if (r < b) acc0 = fma(p[r], x[r], acc0);
+            const double v = warp_sum(acc0 + acc1);
+            if (lane == 0) out(i, v);
         }
         __syncthreads();
         return;
     }
-    // S row segments per column, each segment a whole number of warps
-    int S = 1;
-    while (S < 32 && (int64_t)(2 * S) * wpc <= nW) S *= 2;
-    const int W = (int)wpc * 32;
-    const int sg = wid / (int)wpc;
-    const int64_t ci = (int64_t)(wid % (int)wpc) * 32 + lane;
-    const bool inseg = sg < S;
-    const bool act = inseg && ci < nc;
-    const int64_t i = c0 + (act ? ci : 0);
-    int64_t a = 0, b = 0;
-    if (act) {
-        const int64_t lo0 = (KIND == kLower) ? max(rlo, i) : rlo;
-        const int64_t hi0 = (KIND == kLower) ? rhi : min(rhi, i + 1);
-        const int64_t len = hi0 > lo0 ? hi0 - lo0 : 0;
-        const int64_t seg = (len + S - 1) / S;
-        a = lo0 + sg * seg;
-        b = min(hi0, a + seg);
-        if (b < a) b = a;
+    const int64_t groups = (nc + 7) / 8;
+    const int64_t rows = rhi > rlo ? rhi - rlo : 0;
+    int lmax = 0;  // S = 2^lS row segments, each >= 32 rows, partials fit in red
+    while (lmax < 4 && ((int64_t)nc << (lmax + 1)) <= 2048 && rows >= ((int64_t)32 << (lmax + 1))) ++lmax;
+    const int lS = pick_segments(groups, (rows + 3) / 4, nW, lmax);
+    const int S = 1 << lS;
+    const int64_t seglen = (rows + S - 1) >> lS;
+    const int64_t units = groups << lS;
+    for (int64_t u = wid; u < units; u += nW) {
+        const int64_t g = u >> lS;
+        const int sg = (int)(u & (S - 1));
+        const int64_t i = c0 + g * 8 + cl;
+        const bool act = i < c1;
+        const int64_t s_lo = rlo + sg * seglen, s_hi = min(rhi, s_lo + seglen);
+        int64_t a = 0, b = 0;
+        if (act) {
+            a = max(s_lo, (KIND == kLower) ? max(rlo, i) : rlo);
+            b = min(s_hi, (KIND == kLower) ? rhi : min(rhi, i + 1));
+            if (b < a) b = a;
+        }
+        int64_t lo, hi;
+        warp_core_al<4>(a, b, act && a < b, lo, hi);
+        double v = dot_phase<4>(A + (act ? i : c0) * lda, 1, x, a, b, lo, hi, ph, act);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if (act && ph == 0) {
+            if (S == 1)
+                out(i, v);
+            else
+                red[(int64_t)sg * nc + (i - c0)] = v;
+        }
     }
-    int64_t lo, hi;
-    warp_core(a, b, act && a < b, lo, hi);
-    const double s = dot_range<1>(A + i * lda, 1, x, a, b, lo, hi, act);
-    if (inseg) red[sg * W + (int)ci] = act ? s : 0.0;
+    if (S > 1) {
+        tree_segments(red, S, nc, 1);
+        for (int64_t c = threadIdx.x; c < nc; c += blockDim.x) out(c0 + c, red[c]);
+    }
     __syncthreads();
-    for (int st = S >> 1; st >= 1; st >>= 1) {  // fixed-shape tree over the segments
-        if (sg < st) red[sg * W + (int)ci] += red[(sg + st) * W + (int)ci];
-        __syncthreads();
+}
+
+template <int RL, int KIND, int NV, class Out>
+__device__ __noinline__ void rowdots_rl(const double* __restrict__ A, int64_t lda, int64_t r0, int64_t r1,
+                           int64_t ccap, const double* x0, const double* x1, double* red, Out out)
+{
+    constexpr int CL = 32 / RL;
+    const int nW = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rr = lane % RL, ph = lane / RL;
+    const int64_t nr = r1 - r0;
+    const int64_t rgroups = (nr + RL - 1) / RL;
+    // fixed column grid over the columns any row of [r0, r1) can touch
+    const int64_t gb = (KIND == kUpperCol) ? r0 : 0;
+    const int64_t ge = (KIND == kLowerCol) ? min(ccap, r1) : ccap;
+    const int64_t glen = ge > gb ? ge - gb : 0;
+    int lmax = 0;  // S = 2^lS column segments, each >= 8 CL columns, partials fit in red
+    while (lmax < 5 && ((int64_t)nr * NV << (lmax + 1)) <= 2048 && glen >= ((int64_t)8 * CL << (lmax + 1))) ++lmax;
+    const int lS = pick_segments(rgroups, (glen + CL - 1) / CL * NV, nW, lmax);
+    const int S = 1 << lS;
+    const int64_t seglen = (glen + S - 1) >> lS;
+    const int64_t units = rgroups << lS;
+    for (int64_t u = wid; u < units; u += nW) {
+        const int64_t g = u >> lS;
+        const int sg = (int)(u & (S - 1));
+        const int64_t rho = r0 + g * RL + rr;
+        const bool act = rho < r1;
+        int64_t a = 0, b = 0;
+        if (act) {
+            const int64_t s0 = gb + sg * seglen, s1 = min(ge, s0 + seglen);
+            const int64_t cb = (KIND == kUpperCol) ? rho : 0;
+            const int64_t ce = (KIND == kLowerCol) ? min(ccap, rho + 1) : ccap;
+            a = max(s0, cb);
+            b = min(s1, ce);
+            if (b < a) b = a;
+        }
+        int64_t lo, hi;
+        warp_core_al<CL>(a, b, act && a < b, lo, hi);
+        double v0, v1 = 0.0;
+        const double* prow = A + (act ? rho : r0);
+        if (NV == 2)
+            dot2_phase<CL>(prow, lda, x0, x1, a, b, lo, hi, ph, act, v0, v1);
+        else
+            v0 = dot_phase<CL>(prow, lda, x0, a, b, lo, hi, ph, act);
+#pragma unroll
+        for (int o = RL; o < 32; o <<= 1) {
+            v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+            if (NV == 2) v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        }
+        if (act && ph == 0) {
+            if (S == 1) {
+                out(rho, v0, v1);
+            } else {
+                red[((int64_t)sg * nr + (rho - r0)) * NV] = v0;
+                if (NV == 2) red[((int64_t)sg * nr + (rho - r0)) * NV + 1] = v1;
+            }
+        }
     }
-    if (sg == 0 && act) out(c0 + ci, red[ci]);
+    if (S > 1) {
+        tree_segments(red, S, nr, NV);
+        for (int64_t q = threadIdx.x; q < nr; q += blockDim.x)
+            out(r0 + q, red[q * NV], (NV == 2) ? red[q * NV + 1] : 0.0);
+    }
     __syncthreads();
 }
 
@@ -744,72 +873,35 @@ template <int KIND, int NV, class Out>
 __device__ void cta_rowdots(const double* __restrict__ A, int64_t lda, int64_t r0, int64_t r1,
                             int64_t ccap, const double* x0, const double* x1, double* red, Out out)
 {
-    const int B = blockDim.x, t = threadIdx.x, nW = B >> 5, wid = t >> 5, lane = t & 31;
     const int64_t nr = r1 - r0;
     if (nr <= 0) return;
-    const int64_t wpr = (nr + 31) / 32;  // warps that cover the rows once
-    if (wpr >= nW) {
-        for (int64_t base = r0; base < r1; base += B) {
-            const int64_t rho = base + t;
-            const bool act = rho < r1;
-            const int64_t a = act ? ((KIND == kUpperCol) ? rho : 0) : 0;
-            const int64_t b = act ? ((KIND == kLowerCol) ? min(ccap, rho + 1) : ccap) : 0;
-            int64_t lo, hi;
-            warp_core(a, b, act && a < b, lo, hi);
-            double s0, s1 = 0.0;
-            if (NV == 2)
-                dot2_range<0>(A + (act ? rho : 0), lda, x0, x1, a, b, lo, hi, act, s0, s1);
-            else
-                s0 = dot_range<0>(A + (act ? rho : 0), lda, x0, a, b, lo, hi, act);
-            if (act) out(rho, s0, s1);
+    const int nW = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (nr <= nW) {
+        // few rows: one warp per row, lanes along its columns, one shuffle reduction
+        if (wid < nr) {
+            const int64_t rho = r0 + wid;
+            const int64_t a = (KIND == kUpperCol) ? rho : 0;
+            const int64_t b = (KIND == kLowerCol) ? min(ccap, rho + 1) : ccap;
+            const double* p = A + rho;
+            double s0 = 0.0, s1 = 0.0;
+            for (int64_t i = a + lane; i < b; i += 32) {
+                const double v = p[i * lda];
+                s0 = fma(v, x0[i], s0);
+                if (NV == 2) s1 = fma(v, x1[i], s1);
+            }
+            s0 = warp_sum(s0);
+            if (NV == 2) s1 = warp_sum(s1);
+            if (lane == 0) out(rho, s0, s1);
         }
         __syncthreads();
         return;
     }
-    int S = 1;
-    while (S < 32 && (int64_t)(2 * S) * wpr <= nW) S *= 2;
-    const int W = (int)wpr * 32;
-    const int sg = wid / (int)wpr;
-    const int64_t ri = (int64_t)(wid % (int)wpr) * 32 + lane;
-    const bool inseg = sg < S;
-    const bool act = inseg && ri < nr;
-    const int64_t rho = r0 + (act ? ri : 0);
-    int64_t a = 0, b = 0;
-    if (act) {
-        // fixed column grid over the columns any row of [r0, r1) can touch
-        const int64_t gb = (KIND == kUpperCol) ? r0 : 0;
-        const int64_t ge = (KIND == kLowerCol) ? min(ccap, r1) : ccap;
-        const int64_t glen = ge > gb ? ge - gb : 0;
-        const int64_t seg = (glen + S - 1) / S;
-        const int64_t s0 = gb + sg * seg;
-        const int64_t s1 = min(ge, s0 + seg);
-        const int64_t cb = (KIND == kUpperCol) ? rho : 0;
-        const int64_t ce = (KIND == kLowerCol) ? min(ccap, rho + 1) : ccap;
-        a = max(s0, cb);
-        b = min(s1, ce);
-        if (b < a) b = a;
-    }
-    int64_t lo, hi;
-    warp_core(a, b, act && a < b, lo, hi);
-    double s0, s1 = 0.0;
-    if (NV == 2)
-        dot2_range<0>(A + rho, lda, x0, x1, a, b, lo, hi, act, s0, s1);
+    if (nr > 16)
+        rowdots_rl<32, KIND, NV>(A, lda, r0, r1, ccap, x0, x1, red, out);
+    else if (nr > 8)
+        rowdots_rl<16, KIND, NV>(A, lda, r0, r1, ccap, x0, x1, red, out);
     else
-        s0 = dot_range<0>(A + rho, lda, x0, a, b, lo, hi, act);
-    if (inseg) {
-        red[(sg * W + (int)ri) * NV] = act ? s0 : 0.0;
-        if (NV == 2) red[(sg * W + (int)ri) * NV + 1] = act ? s1 : 0.0;
-    }
-    __syncthreads();
-    for (int st = S >> 1; st >= 1; st >>= 1) {
-        if (sg < st) {
-            red[(sg * W + (int)ri) * NV] += red[((sg + st) * W + (int)ri) * NV];
-            if (NV == 2) red[(sg * W + (int)ri) * NV + 1] += red[((sg + st) * W + (int)ri) * NV + 1];
-        }
-        __syncthreads();
-    }
-    if (sg == 0 && act) out(r0 + ri, red[(int)ri * NV], (NV == 2) ? red[(int)ri * NV + 1] : 0.0);
-    __syncthreads();
+        rowdots_rl<8, KIND, NV>(A, lda, r0, r1, ccap, x0, x1, red, out);
 }
 
 }  // namespace tinvx

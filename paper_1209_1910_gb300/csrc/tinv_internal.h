@@ -8,7 +8,6 @@
 
 namespace tinvx {
 
-constexpr int kChainThreads = 512;  // threads per CTA of the persistent cluster kernel
 constexpr int kFirstWarps = 8;      // warps per CTA of the warp-per-eigenvalue solve kernel
 constexpr int kPlanThreads = 1024;  // threads of the single-CTA plan kernel
 constexpr int kScalTeam = 16;       // doubles of per-CTA scalar partials
@@ -92,13 +91,17 @@ cudaError_t launch_lu(int64_t n, const double* d, const double* e, int64_t m, co
 cudaError_t launch_first(const Problem& p, const Ws& w, cudaStream_t st);
 cudaError_t launch_chain(const Problem& p, const Ws& w, int32_t mode, const double* V, int64_t ldv,
                          cudaStream_t st);
+// Normalization and sign convention of the compact-WY cluster members (after launch_chain).
+cudaError_t launch_finalize(const Problem& p, const Ws& w, cudaStream_t st);
 cudaError_t launch_solve_rhs(int64_t n, int64_t m, const Ws& w, double* X, int64_t ldx,
                              int32_t scale, cudaStream_t st);
 cudaError_t launch_orth_plan(int64_t m, const Ws& w, int32_t method, cudaStream_t st);
 cudaError_t launch_finish_info(const Problem& p, const Ws& w, int64_t* info_out, cudaStream_t st);
 
-// Persistent-grid size (co-resident CTAs of the chain kernel) on the current device.
-int32_t chain_grid(int32_t cap);
+// Persistent-grid size (co-resident CTAs of the chain kernel) for order n on the current device,
+// and the threads per CTA it runs with (256 with two CTAs per SM, or 512 with one).
+int32_t chain_grid(int32_t cap, int64_t n);
+int32_t chain_threads(int64_t n);
 size_t chain_smem_bytes(int64_t n, bool use_smem);
 bool chain_use_smem(int64_t n);
 

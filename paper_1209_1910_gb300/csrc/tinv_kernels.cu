@@ -450,6 +450,33 @@ __global__ void __launch_bounds__(kFirstWarps * 32) k_first(Problem p, Ws w)
     }
 }
 
+// Alg. 4 line 21 for the compact-WY cluster members: z_j = q / ||q||_2 with the first entry of
+// largest magnitude made positive.  One warp per column, all columns in parallel.
+__global__ void __launch_bounds__(kFirstWarps * 32) k_finalize(Problem p, Ws w)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * kFirstWarps + warp;
+    if (j >= p.m || w.head[j] == (int32_t)j) return;  // heads are final after k_first
+    double* x = p.Z + j * p.ldz;
+    const int64_t n = p.n;
+    double ss = 0.0, am = -1.0;
+    int64_t ai = 0;
+    for (int64_t i = lane; i < n; i += 32) {
+        const double v = x[i];
+        ss = fma(v, v, ss);
+        if (fabs(v) > am) {
+            am = fabs(v);
+            ai = i;
+        }
+    }
+    ss = warp_sum(ss);
+    warp_argmax(am, ai);
+    double sc = 1.0 / sqrt(ss);
+    if (x[ai] < 0.0) sc = -sc;
+    __syncwarp();
+    for (int64_t i = lane; i < n; i += 32) x[i] *= sc;
+}
+
 // Solve for given right-hand sides (tinv_solve): one warp per column.
 __global__ void __launch_bounds__(kFirstWarps * 32) k_solve_rhs(int64_t n, int64_t m, Ws w,
                                                                 double* X, int64_t ldx, int scale)
@@ -469,7 +496,8 @@ __global__ void __launch_bounds__(kFirstWarps * 32) k_solve_rhs(int64_t n, int64
 // Phase profiling (separate diagnostic build with -DTINV_PHASE_PROFILE): thread 0 of each CTA
 // accumulates clock64() per phase and prints the totals when the kernel ends.
 #ifdef TINV_PHASE_PROFILE
-enum { kPhLoad, kPhSolve, kPhA, kPhB1, kPhT1, kPhB2, kPhB, kPhB3, kPhT2, kPhB4, kPhC, kPhB5, kPhEnd, kPhN };
+enum { kPhLoad, kPhSolve, kPhA, kPhB1, kPhT1, kPhB2, kPhB, kPhB3, kPhT2, kPhB4, kPhC, kPhB5, kPhEnd,
+       kPhT1a, kPhBa, kPhBb, kPhBc, kPhT2a, kPhT2b, kPhT2c, kPhCa, kPhCb, kPhN };
 #define PROF_MARK(acc, i)                                   \
     do {                                                    \
         if (threadIdx.x == 0) {                             \
@@ -537,11 +565,58 @@ __device__ __forceinline__ int solve_group_size(int64_t n)
     return max(32, min(256, P));
 }
 
-// Team-wide order statistics of pass C (per CTA: sum|q|, max|q|, argmax, sum q^2).
-struct QStats {
-    double asum, amax, sumsq;
-    int64_t arg;
-};
+// Sum (of v or of v^2) and max |v| (compared as bit patterns, no FP64 work) of cnt values in
+// shared memory, reduced by 4 warps (one per SM sub-partition) and combined in a fixed order;
+// every thread receives the results.  `red` holds >= 16 doubles.
+template <bool SQUARE>
+__device__ void cta_sum_max(const double* v, int64_t cnt, double* red, double& sum, double& mx)
+{
+    const int t = threadIdx.x, wid = t >> 5, lane = t & 31;
+    unsigned long long* redu = (unsigned long long*)(red + 8);
+    __syncthreads();
+    if (wid < 4) {
+        double a = 0.0;
+        unsigned long long m = 0;
+        for (int64_t i = wid * 32 + lane; i < cnt; i += 128) {
+            const double x = v[i];
+            a = SQUARE ? fma(x, x, a) : a + fabs(x);
+            m = max(m, (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull);
+        }
+        a = warp_sum(a);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            red[wid] = a;
+            redu[wid] = m;
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        red[4] = (red[0] + red[1]) + (red[2] + red[3]);
+        redu[4] = max(max(redu[0], redu[1]), max(redu[2], redu[3]));
+    }
+    __syncthreads();
+    sum = red[4];
+    mx = __longlong_as_double((long long)redu[4]);
+    __syncthreads();
+}
+
+// Sum over the G ranks of a team of one partial (ranks `stride` doubles apart), in rank order,
+// with the loads issued 8 at a time so the L2 latency is paid once per batch.
+__device__ __forceinline__ double sum_partials(const double* base, size_t stride, int G)
+{
+    double acc = 0.0;
+    int r = 0;
+    for (; r + 8 <= G; r += 8) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = __ldcg(base + (size_t)(r + q) * stride);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc += v[q];
+    }
+    for (; r < G; ++r) acc += __ldcg(base + (size_t)r * stride);
+    return acc;
+}
 
 // Warp-wide sum of slot `slot` of the per-rank scalar blocks of a team (lane-strided partial
 // sums, then a fixed xor tree); called by a whole warp, every lane receives the result.
@@ -583,7 +658,6 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
     const double onenrm = w.scal[0], dtpcrt = w.scal[2];
     const bool orth = (cx.mode == kModeOrth);
     __shared__ double s_b[8];
-    __shared__ int64_t s_arg;
 
     // rows of passes A and C and of the head step
     const int64_t ra0 = part_lo(0, n, rank, G), ra1 = part_lo(0, n, rank + 1, G);
@@ -631,6 +705,17 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
         for (int64_t l = (int64_t)rank * B + t; l < k; l += (int64_t)G * B) vecR[l] = Yc[k + l * n];
         const Fac f = orth ? Fac{} : fac_of(w, j, n);
         const double u0n = orth ? 0.0 : w.u0n[j];
+        // balanced bounds of this CTA's share of the T products (FP64 sqrt: one thread, once
+        // per member; every CTA of the team computes the same values)
+        __shared__ int64_t s_tb[4];
+        if (t == 0) {
+            s_tb[0] = tri_col_lo(k, rank, G);
+            s_tb[1] = tri_col_lo(k, rank + 1, G);
+            s_tb[2] = tri_row_lo(k, rank, G);
+            s_tb[3] = tri_row_lo(k, rank + 1, G);
+        }
+        __syncthreads();
+        const int64_t c0 = s_tb[0], c1 = s_tb[1], i0 = s_tb[2], i1 = s_tb[3];
         int nrmchk = 0, its = 0;
         bool conv = false;
         double fac_next = 0.0;
@@ -658,14 +743,15 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 PROF_MARK(cx.prof, kPhA);
                 if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
                 PROF_MARK(cx.prof, kPhB1);
-                // ---- s' = T_k^T s, columns split over the team ----
-                const int64_t c0 = tri_col_lo(k, rank, G), c1 = tri_col_lo(k, rank + 1, G);
+                // ---- s' = T_k^T s, columns [c0, c1) of this CTA ----
+                PROF_MARK(cx.prof, kPhB1);
                 for (int64_t l = t; l < c1; l += B) {
                     double a = 0.0;
-                    for (int r = 0; r < G; ++r) a += __ldcg(&w.partS[(size_t)(leader + r) * n + l]);
+                    a = sum_partials(w.partS + (size_t)leader * n + l, (size_t)n, G);
                     s1[l] = a;
                 }
                 __syncthreads();
+                PROF_MARK(cx.prof, kPhT1a);
                 cta_coldots<kUpper>(Tc, ldt, c0, c1, 0, k, s1, red,
                                     [&](int64_t i, double s) { vecS[i] = s; });
                 PROF_MARK(cx.prof, kPhT1);
@@ -678,13 +764,15 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             const int64_t rb0 = part_lo(k, n, rank, G), rb1 = part_lo(k, n, rank + 1, G);
             for (int64_t r = rb0 + t; r < rb1; r += B) vsm[r] = __ldcg(&vsrc[r]);
             __syncthreads();
+            PROF_MARK(cx.prof, kPhBa);
             if (k > 0) {
                 cta_rowdots<kAllCols, 1>(Yc, n, rb0, rb1, k, s1, nullptr, red,
                                          [&](int64_t rho, double a, double) { vsm[rho] -= a; });
             }
-            double uu = 0.0;
-            for (int64_t r = rb0 + t; r < rb1; r += B) uu = fma(vsm[r], vsm[r], uu);
-            uu = block_sum(uu, red);
+            PROF_MARK(cx.prof, kPhBb);
+            double uu, umx;
+            cta_sum_max<true>(vsm + rb0, rb1 - rb0, red, uu, umx);
+            PROF_MARK(cx.prof, kPhBc);
             if (k > 0) {
                 // g_u = Yhat_k^T u_hat (partial over this CTA's rows)
                 cta_coldots<kLower>(Yc, n, 0, k, rb0, rb1, vsm, red,
@@ -697,10 +785,16 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             PROF_MARK(cx.prof, kPhB);
             if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
             PROF_MARK(cx.prof, kPhB3);
-            // ---- reflector (Eq. yt with t = 1/(c^2 - u_kk c), Sec. 3.3.2) ----
+            // ---- g = Yhat_k^T u_hat from the team partials (all warps but the first), while
+            //      warp 0 forms the reflector (Eq. yt with t = 1/(c^2 - u_kk c), Sec. 3.3.2) ----
             if (t < 32) {
-                const double tot = team_sum_slot(scal_t, G, 0);
-                const double ukk = team_sum_slot(scal_t, G, 1);
+                double tot = 0.0, ukk = 0.0;
+                for (int r = t; r < G; r += 32) {
+                    tot += __ldcg(&scal_t[r * kScalTeam + 0]);
+                    ukk += __ldcg(&scal_t[r * kScalTeam + 1]);
+                }
+                tot = warp_sum(tot);
+                ukk = warp_sum(ukk);
                 const double nrm = sqrt(tot);
                 const bool broke = !(nrm > 0.0) || !isfinite(nrm);
                 const double cc = broke ? -1.0 : -sgn(ukk) * nrm;
@@ -711,31 +805,29 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                     s_b[2] = ue - cc;                    // y_kk
                     s_b[3] = broke ? 1.0 : 0.0;
                 }
+            } else {
+                for (int64_t l = i0 + (t - 32); l < k; l += B - 32)
+                    s1[l] = sum_partials(w.partG + (size_t)leader * n + l, (size_t)n, G);
             }
             __syncthreads();
             const double cc = s_b[0], tk = s_b[1], ykk = s_b[2];
             const bool broke = s_b[3] != 0.0;
+            PROF_MARK(cx.prof, kPhT2a);
             // ---- T column: t_hat = -t_k T_k (Yhat_k^T y_hat) with Yhat^T y_hat = g_u - c r;
             //      and x_T = T_{k+1} (row k of Y_{k+1}) = [T_k r + t_hat y_kk ; t_k y_kk] ----
-            const int64_t i0 = tri_row_lo(k, rank, G), i1 = tri_row_lo(k, rank + 1, G);
-            for (int64_t l = i0 + t; l < k; l += B) {
-                double g = 0.0;
-                if (broke) {
-                    g = __ldcg(&vecR[l]);
-                } else {
-                    for (int r = 0; r < G; ++r) g += __ldcg(&w.partG[(size_t)(leader + r) * n + l]);
-                }
-                s1[l] = g;
+            if (broke) {  // u_hat := e_1, so g_u = Yhat^T e_1 = r
+                for (int64_t l = i0 + t; l < k; l += B) s1[l] = __ldcg(&vecR[l]);
+                __syncthreads();
             }
-            __syncthreads();
             // second vector (r) read through a shared copy of vecR
             double* rsm = (double*)vecR;  // read-only from here on
-            cta_rowdots<kUpperCol, 2>(Tc, ldt, i0, i1, k, s1, rsm, red + 1024,
+            cta_rowdots<kUpperCol, 2>(Tc, ldt, i0, i1, k, s1, rsm, red,
                                       [&](int64_t i, double a, double b) {
                                           const double th = -tk * fma(-cc, b, a);
                                           Tc[i + kk * ldt] = th;
                                           vecX[i] = fma(th, ykk, b);
                                       });
+            PROF_MARK(cx.prof, kPhT2c);
             if (rank == 0 && t == 0) {
                 Tc[kk + kk * ldt] = tk;
                 vecX[kk] = tk * ykk;
@@ -752,45 +844,21 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             // ---- pass C: q = (Y_{k+1} T_{k+1} Y_{k+1}^T - I) e_k = Y_{k+1} x_T - e_k ----
             for (int64_t l = t; l <= k; l += B) s1[l] = __ldcg(&vecX[l]);
             __syncthreads();
-            double as = 0.0, am = -1.0, sq = 0.0;
-            int64_t ai = n;
+            PROF_MARK(cx.prof, kPhCa);
             cta_rowdots<kLowerCol, 1>(Yc, n, ra0, ra1, k + 1, s1, nullptr, red,
                                       [&](int64_t rho, double a, double) {
                                           const double q = (rho == k) ? a - 1.0 : a;
                                           qbuf[rho] = q;
-                                          as += fabs(q);
-                                          sq = fma(q, q, sq);
-                                          if (fabs(q) > am || (fabs(q) == am && rho < ai)) {
-                                              am = fabs(q);
-                                              ai = rho;
-                                          }
+                                          vsm[rho] = q;
                                       });
-            as = block_sum(as, red);
-            sq = block_sum(sq, red);
-            // arg max over the CTA
-            {
-                double a2 = am;
-                int64_t i2 = ai;
-                warp_argmax(a2, i2);
-                __shared__ double s_am[32];
-                __shared__ int64_t s_ai[32];
-                const int lane = t & 31, wid = t >> 5;
-                if (lane == 0) {
-                    s_am[wid] = a2;
-                    s_ai[wid] = i2;
-                }
-                __syncthreads();
-                if (wid == 0) {
-                    double a3 = lane < (B >> 5) ? s_am[lane] : -1.0;
-                    int64_t i3 = lane < (B >> 5) ? s_ai[lane] : n;
-                    warp_argmax(a3, i3);
-                    if (lane == 0) {
-                        scal_t[rank * kScalTeam + 2] = as;
-                        scal_t[rank * kScalTeam + 3] = a3;
-                        scal_t[rank * kScalTeam + 4] = (double)i3;
-                        scal_t[rank * kScalTeam + 5] = sq;
-                    }
-                }
+            // per sweep only sum|q| (the next scaling) and max|q| (the test) are needed; the
+            // 2-norm and the sign convention are applied once, by k_finalize
+            PROF_MARK(cx.prof, kPhCb);
+            double as, am;
+            cta_sum_max<false>(vsm + ra0, ra1 - ra0, red, as, am);
+            if (t == 0) {
+                scal_t[rank * kScalTeam + 2] = as;
+                scal_t[rank * kScalTeam + 3] = am;
             }
             PROF_MARK(cx.prof, kPhC);
             if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
@@ -803,35 +871,23 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             // ---- team statistics, convergence test on x = -c q (||x||_inf = |c| max|q|) ----
             if (t < 32) {
                 const double A1 = team_sum_slot(scal_t, G, 2);
-                const double S2 = team_sum_slot(scal_t, G, 5);
-                double M = -1.0;
-                int64_t I = n;
-                for (int r = t; r < G; r += 32) {
-                    const double mr = __ldcg(&scal_t[r * kScalTeam + 3]);
-                    const int64_t ir = (int64_t)__ldcg(&scal_t[r * kScalTeam + 4]);
-                    if (mr > M || (mr == M && ir < I)) {
-                        M = mr;
-                        I = ir;
-                    }
-                }
-                warp_argmax(M, I);
+                unsigned long long mb = 0;
+                for (int r = t; r < G; r += 32)
+                    mb = max(mb, (unsigned long long)__double_as_longlong(__ldcg(&scal_t[r * kScalTeam + 3])));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
                 if (t == 0) {
                     s_b[4] = A1;
-                    s_b[5] = M;
-                    s_b[6] = S2;
-                    s_arg = (I >= 0 && I < n) ? I : 0;  // all-NaN guard
+                    s_b[5] = __longlong_as_double((long long)mb);
                 }
             }
             __syncthreads();
-            const double A1 = s_b[4], M = s_b[5], S2 = s_b[6];
+            const double A1 = s_b[4], M = s_b[5];
             const bool success = !broke && fabs(cc) * M >= dtpcrt;
             if (success && ++nrmchk >= kExtra + 1) conv = true;
             if (conv || its == maxits) {
-                // Alg. 4 line 21: normalize; first entry of largest magnitude positive
-                const double qa = __ldcg(&qbuf[s_arg]);
-                double sc = 1.0 / sqrt(S2);
-                if (qa < 0.0) sc = -sc;
-                for (int64_t r = ra0 + t; r < ra1; r += B) p.Z[r + j * p.ldz] = qbuf[r] * sc;
+                // Alg. 4 line 21 (normalization and sign) is applied by k_finalize
+                for (int64_t r = ra0 + t; r < ra1; r += B) p.Z[r + j * p.ldz] = qbuf[r];
                 if (rank == 0 && t == 0) {
                     if (p.iters) p.iters[j] = conv ? its : -its;
                     if (!conv) atomicAdd((unsigned long long*)&w.ctr[kCtrInfo], 1ull);
@@ -839,7 +895,9 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 break;
             }
             // next sweep's scaled input: scl * x = q * (-sgn(c) n ||T||_1 max(eps,|u_nn|) / sum|q|)
-            fac_next = -sgn(cc) * (((double)n * onenrm) * fmax(kEps, u0n)) / A1;
+            if (t == 0) s_b[6] = -sgn(cc) * (((double)n * onenrm) * fmax(kEps, u0n)) / A1;
+            __syncthreads();
+            fac_next = s_b[6];
         }
     }
     return true;
@@ -878,7 +936,10 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
                 double as = 0.0;
                 for (int64_t r = t; r < n; r += B) as += fabs(v[r]);
                 as = block_sum(as, red);
-                const double scl = ((double)n * onenrm) * fmax(kEps, u0n) / as;
+                __shared__ double s_scl;
+                if (t == 0) s_scl = ((double)n * onenrm) * fmax(kEps, u0n) / as;
+                __syncthreads();
+                const double scl = s_scl;
                 uint32_t tgt = 0;
                 TeamRef tr{nullptr, &tgt, 1, 0, cx.err};
                 if (!team_solve(n, f, v, scl, v, nullptr, 0, n, nullptr, nullptr, tr, red))
@@ -959,8 +1020,8 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
     return true;
 }
 
-template <int METHOD>
-__global__ void __launch_bounds__(kChainThreads, 1) k_chain(Problem p, Ws w, int32_t mode,
+template <int METHOD, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t mode,
                                                            const double* V, int64_t ldv)
 {
     extern __shared__ double smem[];
@@ -1012,17 +1073,29 @@ __global__ void __launch_bounds__(kChainThreads, 1) k_chain(Problem p, Ws w, int
     }
 #ifdef TINV_PHASE_PROFILE
     if (t == 0)
-        printf("PROF cta=%d team=%d G=%d total=%lld load=%llu solve=%llu A=%llu b1=%llu T1=%llu b2=%llu "
-               "B=%llu b3=%llu T2=%llu b4=%llu C=%llu b5=%llu end=%llu\n",
+        printf("PROF cta=%d team=%d G=%d total=%lld load=%llu solve=%llu A=%llu b1=%llu T1red=%llu T1=%llu "
+               "b2=%llu Bload=%llu Brow=%llu Bsum=%llu B=%llu b3=%llu T2refl=%llu T2red=%llu T2row=%llu "
+               "T2=%llu b4=%llu Cload=%llu Crow=%llu C=%llu b5=%llu end=%llu\n",
                b, tc, tg, clock64() - t_begin, cx.prof.c[kPhLoad], cx.prof.c[kPhSolve], cx.prof.c[kPhA],
-               cx.prof.c[kPhB1], cx.prof.c[kPhT1], cx.prof.c[kPhB2], cx.prof.c[kPhB], cx.prof.c[kPhB3],
-               cx.prof.c[kPhT2], cx.prof.c[kPhB4], cx.prof.c[kPhC], cx.prof.c[kPhB5], cx.prof.c[kPhEnd]);
+               cx.prof.c[kPhB1], cx.prof.c[kPhT1a], cx.prof.c[kPhT1], cx.prof.c[kPhB2], cx.prof.c[kPhBa],
+               cx.prof.c[kPhBb], cx.prof.c[kPhBc], cx.prof.c[kPhB], cx.prof.c[kPhB3], cx.prof.c[kPhT2a],
+               cx.prof.c[kPhT2b], cx.prof.c[kPhT2c], cx.prof.c[kPhT2], cx.prof.c[kPhB4], cx.prof.c[kPhCa],
+               cx.prof.c[kPhCb], cx.prof.c[kPhC], cx.prof.c[kPhB5], cx.prof.c[kPhEnd]);
 #endif
 }
 
 // ==========================================================================================
 // Launchers
 // ==========================================================================================
+// Threads per CTA of the cluster kernel (one CTA per SM).  The kernel also runs with two
+// 256-thread CTAs per SM, which measured no faster on the glued-Wilkinson workload: the CTAs
+// sharing an SM belong to teams that run the same phases at the same time.
+int32_t chain_threads(int64_t n)
+{
+    (void)n;  // two 256-thread CTAs per SM measured no faster than one 512-thread CTA
+    return 512;
+}
+
 bool chain_use_smem(int64_t n)
 {
     return (size_t)(2048 + 2 * n) * sizeof(double) + 4096 <= 220u * 1024u;
@@ -1033,12 +1106,12 @@ size_t chain_smem_bytes(int64_t n, bool use_smem)
     return (size_t)(2048 + (use_smem ? 2 * n : 0)) * sizeof(double);
 }
 
-int32_t chain_grid(int32_t cap)
+int32_t chain_grid(int32_t cap, int64_t n)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int32_t P = sms > 0 ? sms : 1;  // one CTA per SM (kChainThreads threads, large smem)
+    int32_t P = (sms > 0 ? sms : 1) * (chain_threads(n) == 256 ? 2 : 1);
     if (cap > 0 && cap < P) P = cap;
     return P;
 }
@@ -1087,6 +1160,14 @@ cudaError_t launch_first(const Problem& p, const Ws& w, cudaStream_t st)
     return cudaGetLastError();
 }
 
+cudaError_t launch_finalize(const Problem& p, const Ws& w, cudaStream_t st)
+{
+    if (p.m <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((p.m + kFirstWarps - 1) / kFirstWarps);
+    k_finalize<<<blocks, kFirstWarps * 32, 0, st>>>(p, w);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_solve_rhs(int64_t n, int64_t m, const Ws& w, double* X, int64_t ldx,
                              int32_t scale, cudaStream_t st)
 {
@@ -1100,21 +1181,27 @@ cudaError_t launch_chain(const Problem& p, const Ws& w, int32_t mode, const doub
                          cudaStream_t st)
 {
     const size_t smem = chain_smem_bytes(p.n, w.use_smem != 0);
-    void* fn = (p.method == 0) ? (void*)k_chain<0> : (void*)k_chain<1>;
+    const int nt = chain_threads(p.n);
+    void* fn;
+    if (p.method == 0)
+        fn = (nt == 256) ? (void*)k_chain<0, 256> : (void*)k_chain<0, 512>;
+    else
+        fn = (nt == 256) ? (void*)k_chain<1, 256> : (void*)k_chain<1, 512>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, occ = 0;
+    int dev = 0, occ = 0, sms = 0;
     cudaGetDevice(&dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kChainThreads, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, smem);
     if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorLaunchOutOfResources;
+    if (occ < 1 || (int64_t)occ * sms < w.P) return cudaErrorCooperativeLaunchTooLarge;
     Problem pp = p;
     Ws ww = w;
     int32_t mm = mode;
     const double* VV = V;
     int64_t ll = ldv;
     void* args[] = {&pp, &ww, &mm, &VV, &ll};
-    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)w.P), dim3(kChainThreads), args, smem, st);
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)w.P), dim3((unsigned)nt), args, smem, st);
 }
 
 }  // namespace tinvx
