@@ -22,7 +22,7 @@
  *     listed below.  tinv_strerror() gives a message for any code.
  *   - Thread safety: calls on different streams may run concurrently from different host
  *     threads; the library keeps no global mutable state besides a per-device cache of the
- *     number of SMs.
+ *     number of SMs, and the shared scratch of tinv_solve_noalloc (see there).
  */
 #ifndef TINV_H
 #define TINV_H
@@ -135,6 +135,26 @@ int tinv_lu(int64_t n, const double* d, const double* e, int64_t m, const double
  */
 int tinv_solve(int64_t n, const double* d, const double* e, int64_t m, const double* s,
                double* X, int64_t ldx, int32_t scale, const tinv_opts* o);
+
+/*
+ * tinv_solve_noalloc -- tinv_solve for device pointers that allocates no memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot have a library allocate device
+ * memory, e.g. code whose device memory is all owned by a framework's caching allocator or by a
+ * fixed arena, or code on a path where the implicit synchronization of cudaMalloc/cudaFree is
+ * not acceptable.
+ *   n, d, e, m, s, X, ldx, scale : as tinv_solve; d, e, s and X are DEVICE pointers of the
+ *                                  current device.
+ *   stream : cudaStream_t the work is enqueued on; the call returns without synchronizing.
+ * Scratch: a fixed 16 MiB array in device memory, part of the library image (every GPU that
+ * loads the library holds it until the process exits); it takes m * n <= 262144 and
+ * m <= 131072 (for example 512 shifts of order 512).  Larger sizes return TINV_ENOTSUP.  The call performs no cudaMalloc
+ * or cudaFree.  The first call on a device looks up the array's device address (with that
+ * device current) and caches it; make that first call before any stream capture.  All calls on
+ * a device share the array and it keeps the last call's contents (each call writes every entry
+ * it reads), so calls whose work overlaps on the GPU race: serialize them, e.g. on one stream.
+ */
+int tinv_solve_noalloc(int64_t n, const double* d, const double* e, int64_t m, const double* s,
+                       double* X, int64_t ldx, int32_t scale, void* stream);
 
 /*
  * tinv_orth -- incremental orthogonalization of the columns of V (n x m, ldv) by the GPU

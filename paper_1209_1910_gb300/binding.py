@@ -25,7 +25,8 @@ ERRORS = {-101: "ENOMEM", -102: "ECUDA", -103: "ETIMEDOUT", -104: "EAGAIN", -105
 
 # every function include/tinv.h declares
 EXPORTS = ["tinv_opts_default", "tinv_strerror", "tinv_version", "tinv", "tinv_ex",
-           "tinv_workspace_size", "tinv_plan", "tinv_lu", "tinv_solve", "tinv_orth"]
+           "tinv_workspace_size", "tinv_plan", "tinv_lu", "tinv_solve", "tinv_solve_noalloc",
+           "tinv_orth"]
 
 
 class TinvError(RuntimeError):
@@ -72,6 +73,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             lib.tinv_lu.restype = ctypes.c_int
             lib.tinv_solve.argtypes = [I64, P, P, I64, P, P, I64, I32, ctypes.POINTER(Opts)]
             lib.tinv_solve.restype = ctypes.c_int
+            lib.tinv_solve_noalloc.argtypes = [I64, P, P, I64, P, P, I64, I32, P]
+            lib.tinv_solve_noalloc.restype = ctypes.c_int
             lib.tinv_orth.argtypes = [I64, I64, P, I64, P, I64, P, P, ctypes.POINTER(Opts)]
             lib.tinv_orth.restype = ctypes.c_int
             _lib = lib
