@@ -35,6 +35,7 @@ from paper_1209_1910_gb300 import inputs  # noqa: E402
 
 WORKLOADS = {
     "glued4200": "glued Wilkinson 200 x W21+ (glue 1e-10), n=4200, all eigenvectors",
+    "glued2100": "glued Wilkinson 100 x W21+ (glue 1e-10), n=2100, all eigenvectors",
     "uniform1000": "uniform[-1,1] d,e (seed 1), n=1000, all eigenvectors",
     "toeplitz4200": "Toeplitz d=2 e=1, n=4200, all eigenvectors (one cluster)",
     "uniform10000": "uniform[-1,1] d,e (seed 1), n=10000, all eigenvectors",

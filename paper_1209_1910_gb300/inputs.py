@@ -72,6 +72,8 @@ def workload(name: str):
         d, e = uniform(1000, seed=1)
     elif name == "glued4200":
         d, e = glued_wilkinson(200, 1e-10)
+    elif name == "glued2100":
+        d, e = glued_wilkinson(100, 1e-10)
     elif name == "toeplitz4200":
         d, e = toeplitz(4200, 2.0, 1.0)
         return d, e, toeplitz_eigenpairs(4200, 2.0, 1.0)[0]
