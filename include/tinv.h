@@ -107,7 +107,7 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
 size_t tinv_workspace_size(int64_t n, int64_t m, const tinv_opts* o);
 
 /*
- * tinv_plan -- step a1/a2 alone (Sec. 2.1; Alg. 4 lines 8-9 and 17-18): ||T||_1, the cluster
+ * tinv_plan -- step a1/a2 alone (Sec. 2.1; Alg. 4): ||T||_1, the cluster
  * tolerance, the convergence threshold and the cluster head of every eigenvalue.
  *   wp    : [m] perturbed shifts w' (coincident approximations are separated by 10 eps |w|).
  *   head  : [m] index of the first member of the cluster of j (j itself for a cluster head).

@@ -24,7 +24,7 @@
  *
  * Readings of points the paper leaves open (each is also listed in the design notes):
  *   - q_j is formed with T_j, not T_j^T (Sec. 3.3.1/3.3.2 print T^T; Eq. cwy2 needs T).
- *   - Alg. 3 line 3 uses e_1 (printed e_j).
+ *   - the first q of Alg. 3 is formed with e_1 (printed e_j).
  *   - "Normalize v" before the solve is DSTEIN's 1-norm scaling
  *       v <- v * n*||T||_1*max(eps,|u_nn|) / ||v||_1.
  *   - "Until some condition": success when ||x||_inf >= sqrt(0.1/n); stop after EXTRA+1 = 3
@@ -149,7 +149,7 @@ void orc_bisect(int64_t n, const double* d, const double* e, double* w)
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Cluster plan (Sec. 2.1, Alg. 1 lines 8-14, Alg. 4 lines 8-9, 17-18)                    */
+/* Cluster plan (Sec. 2.1, Alg. 1, Alg. 4)                                              */
 /* ------------------------------------------------------------------------------------ */
 
 void orc_plan(int64_t n, const double* d, const double* e, int64_t m, const double* w,
@@ -580,7 +580,7 @@ int64_t orc_tinv(int64_t n, const double* d, const double* e, int64_t m, const d
     int64_t info = 0;
     for (int64_t j = 0; j < m; ++j) {
         int64_t j1 = head[j];
-        int64_t jc = j - j1; /* position inside the cluster (Alg. 4 line 9) */
+        int64_t jc = j - j1; /* position inside the cluster (Alg. 4) */
         double xj = wp[j];
         orc_lagtf(n, d, e, xj, u0, u1, u2, l, piv);
         double unn = fabs(u0[n - 1]);
@@ -588,7 +588,7 @@ int64_t orc_tinv(int64_t n, const double* d, const double* e, int64_t m, const d
         for (int64_t r = 0; r < n; ++r) v[r] = orc_start_value(seed, j0 + j, attempt, r);
 
         if (jc == 1 && method != ORC_MGS) {
-            /* Alg. 4 lines 10-12: Y_1 = [y_1], T_1 = [t_1] from the (final) head vector */
+            /* Alg. 4: Y_1 = [y_1], T_1 = [t_1] from the (final) head vector */
             const double* zh = Z + j1 * ldz;
             int broke;
             double c = reflector(n, zh, Y, &broke);
@@ -611,7 +611,7 @@ int64_t orc_tinv(int64_t n, const double* d, const double* e, int64_t m, const d
             int success_allowed = 1;
             if (jc > 0) {
                 if (method == ORC_MGS) {
-                    /* Alg. 1 lines 9-11 */
+                    /* Alg. 1: MGS against the previous members of the cluster */
                     for (int64_t i = j1; i < j; ++i) {
                         const double* zi = Z + i * ldz;
                         double h = dot(n, v, zi);
@@ -628,7 +628,7 @@ int64_t orc_tinv(int64_t n, const double* d, const double* e, int64_t m, const d
                         if (st) st->breakdowns++;
                     }
                 } else if (method == ORC_CWY) {
-                    /* Alg. 4 lines 13-16 with the new implementation of Sec. 3.3.2 */
+                    /* Alg. 4 with the new implementation of Sec. 3.3.2 */
                     int broke;
                     for (int64_t i = jc + 1; i < mcmax; ++i) T[i + jc * mcmax] = 0.0;
                     double fl = 0.0;
@@ -676,7 +676,7 @@ int64_t orc_tinv(int64_t n, const double* d, const double* e, int64_t m, const d
             if (ifail) ifail[info] = j;
             info++;
         }
-        /* Alg. 1 line 16 / Alg. 4 line 21: normalize; the first entry of largest magnitude
+        /* Alg. 1 / Alg. 4: normalize; the first entry of largest magnitude
            is made positive (DSTEIN's convention). */
         double nr = nrm2(n, v);
         int64_t jmax = 0;
