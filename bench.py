@@ -40,7 +40,11 @@ WORKLOADS = {
     "toeplitz4200": "Toeplitz d=2 e=1, n=4200, all eigenvectors (one cluster)",
     "uniform10000": "uniform[-1,1] d,e (seed 1), n=10000, all eigenvectors",
     "zero10000": "Toeplitz d=0 e=1, n=10000, all eigenvectors (one cluster)",
+    "batch512": "512 problems, n log-uniform [64,4096] (seed 2), even U[-1,1] d,e, odd glued "
+                "W21+ (glue 1e-10); all eigenvectors of every problem, one tinv_batch call",
 }
+# kernels one call enqueues: plan (2), LU (2), first sweep, cluster kernel, CWY finalize, status
+LAUNCHES = {"cwy": 8, "mgs": 7}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (vector and tensor alike), TFLOP/s
 
 
@@ -170,14 +174,19 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    d, e, w = inputs.workload(args.workload)
+    if args.workload == "batch512":
+        probs = inputs.batch_matrices()
+        sample = lambda: cpu_sample_batch(args.method, probs)
+    else:
+        d, e, w = inputs.workload(args.workload)
+        sample = lambda: cpu_sample(args.workload, args.method, d, e, w)
     for _ in range(args.warmup):
-        cpu_sample(args.workload, args.method, d, e, w)
+        sample()
     vals = []
     desc = ""
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, desc = cpu_sample(args.workload, args.method, d, e, w)
+        v, desc = sample()
         vals.append(v)
     el = time.perf_counter() - t0
     value = float(statistics.mean(vals))
@@ -195,8 +204,200 @@ def reference_arm(args):
     print(json.dumps(out), flush=True)
 
 
+def batch_arm(args):
+    """tinv_batch over the 512-problem workload: one launch sequence per step, against
+    one-problem-at-a-time calls of the same problems."""
+    import torch
+
+    from paper_1209_1910_gb300 import binding, build
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    build.build()
+    binding.load()
+    probs = inputs.batch_matrices()
+    ns, off_de, off_z = binding.pack_offsets([len(p[0]) for p in probs])
+    M, nprob = int(ns.sum()), len(ns)
+    D = np.zeros(M)
+    E = np.zeros(M)
+    for q, (d, e) in enumerate(probs):
+        D[off_de[q]:off_de[q] + ns[q]] = d
+        E[off_de[q]:off_de[q] + ns[q] - 1] = e
+    td, te = torch.from_numpy(D).to(dev), torch.from_numpy(E).to(dev)
+    tw = torch.zeros(M, dtype=torch.float64, device=dev)
+    binding.bisect_batch_device(ns, off_de, td, te, tw)  # eigenvalues (setup, untimed)
+    tz = torch.zeros(int((ns * ns).sum()), dtype=torch.float64, device=dev)
+    info = torch.zeros(nprob, dtype=torch.int64, device=dev)
+    iters = torch.zeros(M, dtype=torch.int32, device=dev)
+    ws = torch.empty(binding.batch_workspace_size(ns), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    phase = np.zeros(4, dtype=np.float32)
+
+    def step(with_phase):
+        kw = {"phase_ms": phase.ctypes.data} if with_phase else {}
+        binding.tinv_batch_device(ns, off_de, off_z, td, te, tw, tz, method=args.method,
+                                  info=info, workspace=ws, iters=iters, **kw)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    bad = int((info != 0).sum().item())
+    if bad:
+        raise RuntimeError("warm-up: %d problems with info != 0" % bad)
+    st = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(None)
+    step_ms, chain_ms = [], []
+    torch.cuda.synchronize()
+    sampler.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        step(True)
+        b.record(st)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        chain_ms.append(float(phase[3]))
+    torch.cuda.synchronize()
+    sampler.stop()
+    total_ms = float(sum(step_ms))
+    value = M * args.steps / (total_ms * 1e-3)
+
+    # checks: status of every problem; residual and orthogonality ratios of a sample
+    nonconv = int(info.sum().item())
+    W = tw.cpu().numpy()
+    it = iters.cpu().numpy()
+    eps = float(np.finfo(np.float64).eps)
+    order = np.argsort(-ns)
+    sample = sorted(set(order[:8].tolist() + list(range(0, nprob, 32))))
+    worst_r = worst_o = 0.0
+    flops = 0.0
+    for q in range(nprob):
+        n, a0 = int(ns[q]), int(off_de[q])
+        head = binding.plan(D[a0:a0 + n], E[a0:a0 + n - 1], W[a0:a0 + n])[1]
+        flops += algorithmic_flops(n, head, it[a0:a0 + n], args.method)
+    for q in sample:
+        n, a0, z0 = int(ns[q]), int(off_de[q]), int(off_z[q])
+        Z = tz[z0:z0 + n * n].view(n, n).T  # column j = eigenvector j
+        dq, eq, wq = td[a0:a0 + n], te[a0:a0 + n - 1], tw[a0:a0 + n]
+        R = dq[:, None] * Z
+        R[:-1] += eq[:, None] * Z[1:]
+        R[1:] += eq[:, None] * Z[:-1]
+        R -= Z * wq[None, :]
+        dh, eh = D[a0:a0 + n], E[a0:a0 + n - 1]
+        nrm = float(np.max(np.abs(dh) + np.r_[0, np.abs(eh)] + np.r_[np.abs(eh), 0]))
+        worst_r = max(worst_r, float(R.abs().max()) / (n * eps * nrm))
+        G = Z.T @ Z
+        G.diagonal().sub_(1.0)
+        worst_o = max(worst_o, float(G.abs().max()) / (n * eps))
+    kern_ms = float(statistics.mean(chain_ms))
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    out = {
+        "metric": "eigvecs_per_s", "value": value, "unit": "eigvec/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS["batch512"], "method": args.method,
+                   "problems": nprob, "eigenvectors": M, "parallelism": "single",
+                   "inputs": "resident in HBM (eigenvalues by GPU bisection, untimed)",
+                   "l2": "flushed by a 512 MiB write between steps"},
+        "problems_per_s": nprob * args.steps / (total_ms * 1e-3),
+        "check": {"nonconverged": nonconv, "sampled_problems": len(sample),
+                  "worst_residual_ratio": worst_r, "worst_orth_ratio": worst_o,
+                  "sweeps": int(np.abs(it).sum())},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_chain", "kernel_ms": kern_ms, "flops_per_launch": flops,
+                     "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (derived in the design notes)",
+                     "phase_ms": {"plan": float(phase[0]), "lu": float(phase[1]),
+                                  "first": float(phase[2]), "chain": float(phase[3])}},
+        "gpu_launches": LAUNCHES[args.method] * args.steps,
+        "clocks": sampler.summary(),
+    }
+
+    # the same problems one call at a time (each call a full launch sequence), same stream
+    if not args.no_compare:
+        def one_at_a_time():
+            for q in range(nprob):
+                n, a0, z0 = int(ns[q]), int(off_de[q]), int(off_z[q])
+                binding.tinv_device(td[a0:a0 + n], te[a0:a0 + n - 1], tw[a0:a0 + n],
+                                    tz[z0:z0 + n * n], method=args.method)
+        one_at_a_time()
+        torch.cuda.synchronize()
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        one_at_a_time()
+        b.record(st)
+        b.synchronize()
+        t1 = a.elapsed_time(b)
+        out["compare"] = {"one_at_a_time": {"value": M / (t1 * 1e-3), "ms": t1,
+                                            "problems_per_s": nprob / (t1 * 1e-3)}}
+
+    # end to end through the host-pointer C ABI (pinned buffers, copies inside the timed region)
+    if not args.no_e2e:
+        import ctypes
+
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hd, he, hw = pin(D), pin(E), pin(W)
+        hz = torch.empty(int((ns * ns).sum()), dtype=torch.float64).pin_memory()
+        hinfo = np.zeros(nprob, dtype=np.int64)
+        lib = binding.load()
+        o = binding._opts(args.method)
+        P = ctypes.c_void_p
+
+        def e2e_call():
+            rc = lib.tinv_batch(nprob, binding._ptr(ns), binding._ptr(off_de), binding._ptr(off_z),
+                                P(hd.data_ptr()), P(he.data_ptr()), P(hw.data_ptr()),
+                                P(hz.data_ptr()), binding._ptr(hinfo), ctypes.byref(o))
+            if rc != 0:
+                raise RuntimeError("tinv_batch returned %d" % rc)
+        e2e_call()
+        el = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_call()
+            el += time.perf_counter() - t0
+        out["e2e"] = {"value": M * args.steps / el, "unit": "eigvec/s",
+                      "h2d_bytes_per_step": 3 * M * 8 + nprob * 112,
+                      "d2h_bytes_per_step": int((ns * ns).sum()) * 8 + nprob * 8 + 64}
+        del hz
+
+    if not args.no_cpu_baseline:
+        v, desc = cpu_sample_batch(args.method, probs)
+        out["cpu_baseline"] = {"value": v, "unit": "eigvec/s", "cores": 1, "kind": "oracle",
+                               "sample": desc}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_sample_batch(method, probs, stride=32):
+    """Bounded oracle sample of the batch: every stride-th uniform and every stride-th glued
+    problem (problems q with q mod stride in {0, 1}), whole; eigenvalues by the oracle's
+    bisection (untimed)."""
+    import oracle
+
+    oracle.build()
+    pick = [q for q in range(len(probs)) if q % stride in (0, 1)]
+    ws = {q: oracle.bisect(*probs[q]) for q in pick}
+    tot = 0
+    t0 = time.perf_counter()
+    for q in pick:
+        d, e = probs[q]
+        oracle.tinv(d, e, ws[q], method)
+        tot += len(d)
+    dt = time.perf_counter() - t0
+    return tot / dt, ("oracle on %d whole problems of the batch (q mod %d in {0,1}; %d "
+                      "eigenvectors)" % (len(pick), stride, tot))
+
+
 def ours_arm(args):
     import torch
+    if args.workload == "batch512":
+        return batch_arm(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -310,7 +511,7 @@ def ours_arm(args):
         "check": {"nonconverged": nonconv, "residual_ratio": res_ratio, "orth_ratio": orth_ratio,
                   "sweeps": int(np.abs(it).sum())},
         "roofline": roof,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": LAUNCHES[args.method] * args.steps,
         "clocks": sampler.summary(),
     }
 
@@ -334,7 +535,6 @@ def ours_arm(args):
         out["e2e"] = {"value": world * m * args.steps / el, "unit": "eigvec/s",
                       "h2d_bytes_per_step": (n + (n - 1) + m) * 8,
                       "d2h_bytes_per_step": n * m * 8 + m * 4 + 64}
-        out["gpu_launches"] += 4 * args.steps
 
     # the MGS comparison on the same workload (Alg. 1 on the GPU), fewer steps
     if not args.no_compare and args.method == "cwy" and world == 1:
@@ -352,7 +552,6 @@ def ours_arm(args):
             ms.append(a.elapsed_time(b))
         out["compare"] = {"mgs": {"value": m / (statistics.mean(ms) * 1e-3),
                                   "ms_per_step": statistics.mean(ms)}}
-        out["gpu_launches"] += 4 * 3
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc = cpu_sample(args.workload, args.method, d, e, w)

@@ -107,6 +107,60 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
 size_t tinv_workspace_size(int64_t n, int64_t m, const tinv_opts* o);
 
 /*
+ * tinv_batch -- all eigenvectors of nprob independent problems of uneven order, computed together
+ * by one launch sequence: each problem is Sec. 2.1's problem (every lambda_j of its T), solved as
+ * tinv_ex would solve it alone; clusters never span problems, and the clusters and eigenvalues of
+ * all problems share the persistent kernels' work (large clusters get CTA teams, the rest are
+ * queued largest first).
+ *   nprob   : number of problems, >= 0 (0 is a no-op).
+ *   n       : HOST array [nprob], order of each problem (>= 0).
+ *   off_de  : HOST array [nprob], offset of problem q's entries in the packed d, e and w arrays:
+ *             d[off_de[q] .. +n[q]), e[off_de[q] .. +n[q]-1), w[off_de[q] .. +n[q]) (ascending).
+ *   off_z   : HOST array [nprob], offset of problem q's eigenvector matrix in the packed Z array:
+ *             n[q] x n[q], column-major, leading dimension n[q].  Regions must not overlap.
+ *   d, e, w : packed inputs;  Z : packed outputs (caller-allocated).
+ *   info    : optional [nprob]: per problem, the number of vectors that did not converge, or
+ *             TINV_ETIMEDOUT for every problem if a bounded device wait expired.
+ *   o       : options as tinv_ex (method, seed and j0 apply to every problem, so each problem gets
+ *             the start vectors, and hence the result, of a tinv_ex call with the same options);
+ *             o->iters, if given, has sum(n) entries in problem order.
+ * d, e, w, Z, info and o->iters are host or device memory following o->device_ptrs; n, off_de
+ * and off_z are always host memory (the workspace layout depends on them).  With device pointers
+ * the call is asynchronous on o->stream (the problem table is copied from host memory first).
+ * Returns 0, -k for an invalid argument k (a problem with non-finite or non-ascending inputs is
+ * reported as its array's argument), the total number of non-converged vectors (> 0), or a
+ * runtime error code.
+ */
+int tinv_batch(int64_t nprob, const int64_t* n, const int64_t* off_de, const int64_t* off_z,
+               const double* d, const double* e, const double* w, double* Z, int64_t* info,
+               const tinv_opts* o);
+
+/* Bytes of device workspace tinv_batch needs for the problem orders n[0..nprob). */
+size_t tinv_batch_workspace_size(int64_t nprob, const int64_t* n, const tinv_opts* o);
+
+/*
+ * tinv_bisect -- all n eigenvalues of T, ascending, by Sturm-count bisection (the eigenvalue step
+ * that precedes inverse iteration; the paper computes it with LAPACK's bisection, Sec. 5.1).
+ *   d, e : T as above;  w : [n] receives the eigenvalue approximations, ascending.
+ * Eigenvalue k is halved from the Gershgorin interval (widened by 2 eps n max|bound| + 2 pivmin)
+ * until the bracket is at most max(2 eps max(|lo|,|hi|), eps ||T||_1), and the midpoint is
+ * returned; a pivot of the Sturm sequence smaller than pivmin = DBL_MIN max(1, max e_i^2) in
+ * magnitude counts as -pivmin.  Each eigenvalue is computed independently, with IEEE binary64
+ * round-to-nearest operations in a fixed order, so results do not depend on the launch.
+ * Pointers follow o->device_ptrs (NULL o: host pointers, synchronous).
+ * Returns 0, -k for invalid argument k, or a runtime error code.
+ */
+int tinv_bisect(int64_t n, const double* d, const double* e, double* w, const tinv_opts* o);
+
+/*
+ * tinv_bisect_batch -- tinv_bisect for nprob problems in one launch.  n, off_de are HOST arrays
+ * as for tinv_batch; problem q's eigenvalues go to w[off_de[q] .. +n[q]), so w is ready to be
+ * passed to tinv_batch.  At most 65535 problems per call (else TINV_ENOTSUP).
+ */
+int tinv_bisect_batch(int64_t nprob, const int64_t* n, const int64_t* off_de, const double* d,
+                      const double* e, double* w, const tinv_opts* o);
+
+/*
  * tinv_plan -- step a1/a2 alone (Sec. 2.1; Alg. 4): ||T||_1, the cluster
  * tolerance, the convergence threshold and the cluster head of every eigenvalue.
  *   wp    : [m] perturbed shifts w' (coincident approximations are separated by 10 eps |w|).

@@ -25,8 +25,9 @@ ERRORS = {-101: "ENOMEM", -102: "ECUDA", -103: "ETIMEDOUT", -104: "EAGAIN", -105
 
 # every function include/tinv.h declares
 EXPORTS = ["tinv_opts_default", "tinv_strerror", "tinv_version", "tinv", "tinv_ex",
-           "tinv_workspace_size", "tinv_plan", "tinv_lu", "tinv_solve", "tinv_solve_noalloc",
-           "tinv_orth"]
+           "tinv_workspace_size", "tinv_batch", "tinv_batch_workspace_size", "tinv_bisect",
+           "tinv_bisect_batch", "tinv_plan",
+           "tinv_lu", "tinv_solve", "tinv_solve_noalloc", "tinv_orth"]
 
 
 class TinvError(RuntimeError):
@@ -73,6 +74,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
             lib.tinv_lu.restype = ctypes.c_int
             lib.tinv_solve.argtypes = [I64, P, P, I64, P, P, I64, I32, ctypes.POINTER(Opts)]
             lib.tinv_solve.restype = ctypes.c_int
+            lib.tinv_bisect.argtypes = [I64, P, P, P, ctypes.POINTER(Opts)]
+            lib.tinv_bisect.restype = ctypes.c_int
+            lib.tinv_bisect_batch.argtypes = [I64, P, P, P, P, P, ctypes.POINTER(Opts)]
+            lib.tinv_bisect_batch.restype = ctypes.c_int
+            lib.tinv_batch.argtypes = [I64, P, P, P, P, P, P, P, P, ctypes.POINTER(Opts)]
+            lib.tinv_batch.restype = ctypes.c_int
+            lib.tinv_batch_workspace_size.argtypes = [I64, P, ctypes.POINTER(Opts)]
+            lib.tinv_batch_workspace_size.restype = ctypes.c_size_t
             lib.tinv_solve_noalloc.argtypes = [I64, P, P, I64, P, P, I64, I32, P]
             lib.tinv_solve_noalloc.restype = ctypes.c_int
             lib.tinv_orth.argtypes = [I64, I64, P, I64, P, I64, P, P, ctypes.POINTER(Opts)]
@@ -205,3 +214,82 @@ def tinv_device(d, e, w, Z, method="cwy", seed=0, j0=0, workspace=None, iters=No
               iters=_ptr(iters), info=_ptr(info), **kw)
     return _check(load().tinv_ex(n, _ptr(d), _ptr(e), m, _ptr(w), _ptr(Z), n, ctypes.byref(o),
                                  None), "tinv_ex")
+
+
+# ------------------------------------------------------------------------------------------
+# batched API: many independent problems of uneven order in one launch sequence
+# ------------------------------------------------------------------------------------------
+def pack_offsets(ns):
+    """Packed offsets of d/e/w (sum of n) and of Z (sum of n^2) for problem orders ns."""
+    ns = np.asarray(ns, dtype=np.int64)
+    off_de = np.zeros(len(ns), dtype=np.int64)
+    off_z = np.zeros(len(ns), dtype=np.int64)
+    if len(ns):
+        off_de[1:] = np.cumsum(ns)[:-1]
+        off_z[1:] = np.cumsum(ns * ns)[:-1]
+    return ns, off_de, off_z
+
+
+def batch_workspace_size(ns, **kw) -> int:
+    ns = np.ascontiguousarray(ns, dtype=np.int64)
+    return int(load().tinv_batch_workspace_size(len(ns), _ptr(ns), ctypes.byref(_opts(**kw))))
+
+
+def tinv_batch(ds, es, ws, method="cwy", seed=0, j0=0, return_info=False, **kw):
+    """All eigenvectors of each problem (host arrays; lists of d, e, w).  Returns the list of
+    Z_q (n_q x n_q, Fortran order), or (Zs, rc, info, iters) with return_info."""
+    ns, off_de, off_z = pack_offsets([len(d) for d in ds])
+    tot = int(ns.sum())
+    d = np.zeros(max(tot, 1))
+    e = np.zeros(max(tot, 1))
+    w = np.zeros(max(tot, 1))
+    for q in range(len(ns)):
+        a, k = int(off_de[q]), int(ns[q])
+        d[a:a + k] = ds[q]
+        e[a:a + max(k - 1, 0)] = es[q][:max(k - 1, 0)]
+        w[a:a + k] = ws[q]
+    Z = np.zeros(max(int((ns * ns).sum()), 1))
+    info = np.zeros(max(len(ns), 1), dtype=np.int64)
+    iters = np.zeros(max(tot, 1), dtype=np.int32)
+    o = _opts(method, seed, j0, iters=iters.ctypes.data, **kw)
+    rc = _check(load().tinv_batch(len(ns), _ptr(ns), _ptr(off_de), _ptr(off_z), _ptr(d), _ptr(e),
+                                  _ptr(w), _ptr(Z), _ptr(info), ctypes.byref(o)), "tinv_batch")
+    Zs = [Z[int(off_z[q]):int(off_z[q] + ns[q] * ns[q])].reshape((int(ns[q]), int(ns[q])), order="F")
+          for q in range(len(ns))]
+    if return_info:
+        return Zs, rc, info[:len(ns)], iters[:tot]
+    return Zs
+
+
+def tinv_batch_device(ns, off_de, off_z, d, e, w, Z, method="cwy", seed=0, j0=0, info=None,
+                      workspace=None, iters=None, **kw):
+    """Enqueue a batch on torch CUDA tensors (packed float64 d, e, w, Z; int64 info[nprob]);
+    ns, off_de and off_z are host int64 arrays.  Returns immediately."""
+    ns = np.ascontiguousarray(ns, dtype=np.int64)
+    off_de = np.ascontiguousarray(off_de, dtype=np.int64)
+    off_z = np.ascontiguousarray(off_z, dtype=np.int64)
+    o = _opts(method, seed, j0, device=True, stream=_stream_of(d),
+              workspace=_ptr(workspace),
+              workspace_bytes=(workspace.numel() * workspace.element_size()) if workspace is not None else 0,
+              iters=_ptr(iters), **kw)
+    return _check(load().tinv_batch(len(ns), _ptr(ns), _ptr(off_de), _ptr(off_z), _ptr(d), _ptr(e),
+                                    _ptr(w), _ptr(Z), _ptr(info), ctypes.byref(o)), "tinv_batch")
+
+
+def bisect(d, e, **kw):
+    """All eigenvalues of T (host arrays), ascending, by GPU Sturm bisection."""
+    d, e = _f64(d), _f64(e)
+    n = len(d)
+    w = np.zeros(max(n, 1))
+    _check(load().tinv_bisect(n, _ptr(d), _ptr(e), _ptr(w), ctypes.byref(_opts(**kw))), "tinv_bisect")
+    return w[:n]
+
+
+def bisect_batch_device(ns, off_de, d, e, w, **kw):
+    """Enqueue bisection of packed problems on torch CUDA tensors (w receives the eigenvalues in
+    the layout tinv_batch expects); ns and off_de are host int64 arrays.  Returns immediately."""
+    ns = np.ascontiguousarray(ns, dtype=np.int64)
+    off_de = np.ascontiguousarray(off_de, dtype=np.int64)
+    o = _opts(device=True, stream=_stream_of(d), **kw)
+    return _check(load().tinv_bisect_batch(len(ns), _ptr(ns), _ptr(off_de), _ptr(d), _ptr(e),
+                                           _ptr(w), ctypes.byref(o)), "tinv_bisect_batch")

@@ -1,4 +1,4 @@
-"""Build libtinv.so in-tree with nvcc for sm_103a (two translation units compiled in parallel).
+"""Build libtinv.so in-tree with nvcc for sm_103a (its translation units compiled in parallel).
 
     python -m paper_1209_1910_gb300.build [--force] [--verbose]
 """
@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libtinv.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["tinv_kernels.cu", "tinv_api.cu", "tinv_noalloc.cu"]
+SOURCES = ["tinv_kernels.cu", "tinv_api.cu", "tinv_noalloc.cu", "tinv_bisect.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -18,11 +18,21 @@
 
 namespace tinvx {
 
-cudaError_t launch_norm(const Problem& p, const Ws& w, cudaStream_t st);
-
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-Layout make_layout(int64_t n, int64_t m, int32_t P, bool need_chain)
+Dims single_dims(int64_t n, int64_t m, int32_t P)
+{
+    Dims D;
+    D.nmax = n;
+    D.M = m;
+    D.F = n * m;
+    D.TT = m * m;
+    D.nseg = 1;
+    D.P = P;
+    return D;
+}
+
+Layout make_layout(const Dims& D, bool need_chain)
 {
     Layout L;
     memset(&L, 0, sizeof(L));
@@ -32,7 +42,10 @@ Layout make_layout(int64_t n, int64_t m, int32_t P, bool need_chain)
         off = align_up(off + (bytes ? bytes : 1), 256);
         return o;
     };
-    const size_t nn = (size_t)n, mm = (size_t)m, pp = (size_t)P;
+    const size_t nn = (size_t)D.nmax, mm = (size_t)D.M, ff = (size_t)D.F, pp = (size_t)D.P;
+    L.segs = take((size_t)D.nseg * sizeof(Seg));
+    L.segj = take(mm * sizeof(int32_t));
+    L.sinfo = take((size_t)D.nseg * sizeof(int64_t));
     L.scal = take(4 * sizeof(double));
     L.wp = take(mm * sizeof(double));
     L.head = take(mm * sizeof(int32_t));
@@ -43,16 +56,16 @@ Layout make_layout(int64_t n, int64_t m, int32_t P, bool need_chain)
     L.queue = take(mm * sizeof(int32_t));
     L.ctr = take(kCtrCount * sizeof(int64_t));
     L.bar = take(pp * sizeof(uint32_t));
-    L.fl = take(mm * nn * sizeof(double));
-    L.fu1 = take(mm * nn * sizeof(double));
-    L.fu2 = take(mm * nn * sizeof(double));
-    L.fr = take(mm * nn * sizeof(double));
-    L.fpiv = take(mm * nn);
+    L.fl = take(ff * sizeof(double));
+    L.fu1 = take(ff * sizeof(double));
+    L.fu2 = take(ff * sizeof(double));
+    L.fr = take(ff * sizeof(double));
+    L.fpiv = take(ff);
     L.u0n = take(mm * sizeof(double));
     L.tolv = take(mm * sizeof(double));
     if (need_chain) {
-        L.Y = take(nn * mm * sizeof(double));
-        L.T = take(mm * mm * sizeof(double));
+        L.Y = take(ff * sizeof(double));
+        L.T = take((size_t)D.TT * sizeof(double));
         L.partS = take(pp * nn * sizeof(double));
         L.partG = take(pp * nn * sizeof(double));
         L.partScal = take(pp * kScalTeam * sizeof(double));
@@ -62,17 +75,20 @@ Layout make_layout(int64_t n, int64_t m, int32_t P, bool need_chain)
         L.qbuf = take(pp * nn * sizeof(double));
         L.vbuf = take(pp * nn * sizeof(double));
         L.tpub = take(pp * 8 * sizeof(double));
-        if (!chain_use_smem(n)) L.gvec = take(pp * 2 * nn * sizeof(double));
+        if (!chain_use_smem(D.nmax)) L.gvec = take(pp * 2 * nn * sizeof(double));
     }
     L.total = off;
     return L;
 }
 
-Ws bind_layout(void* base, const Layout& L, int64_t n, int64_t m, int32_t P)
+Ws bind_layout(void* base, const Layout& L, const Dims& D)
 {
     char* b = (char*)base;
     Ws w;
     memset(&w, 0, sizeof(w));
+    w.segs = (Seg*)(b + L.segs);
+    w.segj = (int32_t*)(b + L.segj);
+    w.sinfo = (int64_t*)(b + L.sinfo);
     w.scal = (double*)(b + L.scal);
     w.wp = (double*)(b + L.wp);
     w.head = (int32_t*)(b + L.head);
@@ -104,8 +120,8 @@ Ws bind_layout(void* base, const Layout& L, int64_t n, int64_t m, int32_t P)
         w.tpub = (double*)(b + L.tpub);
         w.gvec = L.gvec ? (double*)(b + L.gvec) : nullptr;
     }
-    w.P = P;
-    w.use_smem = chain_use_smem(n) ? 1 : 0;
+    w.P = D.P;
+    w.use_smem = chain_use_smem(D.nmax) ? 1 : 0;
     return w;
 }
 
@@ -168,6 +184,15 @@ __global__ void k_finish(const int64_t* ctr, int64_t* info)
     *info = err ? (int64_t)TINV_ETIMEDOUT : ctr[kCtrInfo];
 }
 
+// Per-problem results of a batch: the non-converged count, or the timeout code for all.
+__global__ void k_finish_batch(const int64_t* ctr, const int64_t* sinfo, int64_t nprob, int64_t* info)
+{
+    const int64_t err = ctr[kCtrErr];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nprob;
+         q += (int64_t)gridDim.x * blockDim.x)
+        info[q] = err ? (int64_t)TINV_ETIMEDOUT : sinfo[q];
+}
+
 struct Opts {
     tinv_opts o;
     explicit Opts(const tinv_opts* src)
@@ -179,15 +204,16 @@ struct Opts {
     }
 };
 
-// Enqueue the full inverse-iteration path on `st` for a problem whose arrays are all on the
-// device.  `ws` must hold make_layout(n, m, P, true).total bytes.
+// Enqueue the full inverse-iteration path on `st` for problems whose arrays are all on the
+// device.  `ws` must hold make_layout(D, true).total bytes; with p.seg_preset the problem table
+// must already be in the workspace (copied on `st`).
 // When phase_ms is given, CUDA events bracket each launch and the elapsed device times are
 // stored after synchronizing on the last event.
-int enqueue_tinv(const Problem& p, void* ws, int32_t P, int32_t max_team, cudaStream_t st,
+int enqueue_tinv(const Problem& p, void* ws, const Dims& D, int32_t max_team, cudaStream_t st,
                  float* phase_ms)
 {
-    const Layout L = make_layout(p.n, p.m, P, true);
-    const Ws w = bind_layout(ws, L, p.n, p.m, P);
+    const Layout L = make_layout(D, true);
+    const Ws w = bind_layout(ws, L, D);
     cudaEvent_t ev[5] = {};
     cudaError_t e = cudaSuccess;
     if (phase_ms) {
@@ -196,8 +222,7 @@ int enqueue_tinv(const Problem& p, void* ws, int32_t P, int32_t max_team, cudaSt
     }
     if (e == cudaSuccess) e = launch_plan(p, w, max_team, st);
     if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[1], st);
-    if (e == cudaSuccess)
-        e = launch_lu(p.n, p.d, p.e, p.m, w.wp, w.fl, w.fr, w.fu1, w.fu2, w.fpiv, w.u0n, w.tolv, st);
+    if (e == cudaSuccess) e = launch_lu_seg(p, w, st);
     if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[2], st);
     if (e == cudaSuccess) e = launch_first(p, w, st);
     if (e == cudaSuccess && phase_ms) e = cudaEventRecord(ev[3], st);
@@ -211,6 +236,43 @@ int enqueue_tinv(const Problem& p, void* ws, int32_t P, int32_t max_team, cudaSt
     for (int i = 0; i < 5; ++i)
         if (ev[i]) cudaEventDestroy(ev[i]);
     return cuda_code(e);
+}
+
+// Sizes and problem table of a batch (host arrays n, off_de, off_z), with the argument checks
+// that need no array contents.  Returns 0 or the error code.
+int batch_tables(int64_t nprob, const int64_t* n, const int64_t* off_de, const int64_t* off_z,
+                 const tinv_opts& o, int32_t P, Dims* D, std::vector<Seg>* segs)
+{
+    Dims d;
+    memset(&d, 0, sizeof(d));
+    d.nseg = nprob;
+    d.P = P;
+    segs->assign((size_t)nprob, Seg{});
+    for (int64_t q = 0; q < nprob; ++q) {
+        const int64_t nq = n[q];
+        if (nq < 0 || nq > (int64_t)INT32_MAX / 2) return -2;
+        if (off_de[q] < 0) return -3;
+        if (off_z[q] < 0) return -4;
+        Seg& g = (*segs)[(size_t)q];
+        g.n = nq;
+        g.m = nq;
+        g.de = off_de[q];
+        g.wo = off_de[q];
+        g.z = off_z[q];
+        g.ldz = nq > 0 ? nq : 1;
+        g.j0 = d.M;
+        g.foff = d.F;
+        g.kj0 = o.j0;
+        g.seed = o.seed;
+        d.nmax = nq > d.nmax ? nq : d.nmax;
+        d.M += nq;
+        d.F += nq * nq;
+        d.TT += nq * nq;
+    }
+    if (d.M > (int64_t)INT32_MAX / 2) return TINV_ENOTSUP;
+    if (d.nmax < 1) d.nmax = 1;
+    *D = d;
+    return 0;
 }
 
 }  // namespace
@@ -242,14 +304,14 @@ const char* tinv_strerror(int code)
     return "some eigenvectors did not converge";
 }
 
-const char* tinv_version(void) { return "tinv 0.1 (sm_103a, FP64)"; }
+const char* tinv_version(void) { return "tinv 0.2 (sm_103a, FP64)"; }
 
 size_t tinv_workspace_size(int64_t n, int64_t m, const tinv_opts* o)
 {
     if (n < 0 || m < 0) return 0;
     const Opts op(o);
     const int32_t P = chain_grid(op.o.grid_ctas, n);
-    return make_layout(n, m, P, true).total;
+    return make_layout(single_dims(n, m, P), true).total;
 }
 
 int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double* w, double* Z,
@@ -275,7 +337,10 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
     p.method = op.o.method;
     p.seed = op.o.seed;
     p.j0 = op.o.j0;
+    p.nseg = 1;
+    p.M = m;
     const int32_t P = chain_grid(op.o.grid_ctas, n);
+    const Dims D = single_dims(n, m, P);
 
     if (op.o.device_ptrs) {
         cudaStream_t st = (cudaStream_t)op.o.stream;
@@ -295,7 +360,7 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
         p.w = w;
         p.Z = Z;
         p.iters = op.o.iters;
-        const size_t need = make_layout(n, m, P, true).total;
+        const size_t need = make_layout(D, true).total;
         DevBuf own;
         void* ws = op.o.workspace;
         if (ws) {
@@ -305,10 +370,10 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
             if (ce != cudaSuccess) return TINV_ENOMEM;
             ws = own.p;
         }
-        int rc = enqueue_tinv(p, ws, P, op.o.max_team, st, op.o.phase_ms);
+        int rc = enqueue_tinv(p, ws, D, op.o.max_team, st, op.o.phase_ms);
         if (rc != 0) return rc;
         if (op.o.info) {
-            const Ws wsb = bind_layout(ws, make_layout(n, m, P, true), n, m, P);
+            const Ws wsb = bind_layout(ws, make_layout(D, true), D);
             k_finish<<<1, 1, 0, st>>>(wsb.ctr, op.o.info);
             if (cudaGetLastError() != cudaSuccess) return TINV_ECUDA;
         }
@@ -327,7 +392,7 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return TINV_ENODEV;
     int rc = 0;
     {
-        const Layout L = make_layout(n, m, P, true);
+        const Layout L = make_layout(D, true);
         DevBuf dd, de, dw, dz, dit, ws;
         cudaError_t ce = dd.alloc(n * sizeof(double), st, true);
         if (ce == cudaSuccess) ce = de.alloc((n - 1) * sizeof(double), st, true);
@@ -351,12 +416,12 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
             p.Z = (double*)dz.p;
             p.ldz = n;
             p.iters = (int32_t*)dit.p;
-            rc = enqueue_tinv(p, ws.p, P, op.o.max_team, st, op.o.phase_ms);
+            rc = enqueue_tinv(p, ws.p, D, op.o.max_team, st, op.o.phase_ms);
         }
         int64_t ctr[kCtrCount];
         std::vector<int32_t> its(m);
         if (!rc) {
-            const Ws wsb = bind_layout(ws.p, L, n, m, P);
+            const Ws wsb = bind_layout(ws.p, L, D);
             ce = cudaMemcpy2DAsync(Z, ldz * sizeof(double), dz.p, n * sizeof(double),
                                    n * sizeof(double), m, cudaMemcpyDeviceToHost, st);
             if (ce == cudaSuccess)
@@ -393,6 +458,173 @@ int tinv(int64_t n, const double* d, const double* e, const double* w, double* Z
     return tinv_ex(n, d, e, n, w, Z, n > 0 ? n : 1, nullptr, nullptr);
 }
 
+size_t tinv_batch_workspace_size(int64_t nprob, const int64_t* n, const tinv_opts* o)
+{
+    if (nprob < 0 || (nprob > 0 && !n)) return 0;
+    const Opts op(o);
+    int64_t nmax = 1;
+    for (int64_t q = 0; q < nprob; ++q) nmax = n[q] > nmax ? n[q] : nmax;
+    std::vector<int64_t> zeros((size_t)(nprob > 0 ? nprob : 1), 0);
+    Dims D;
+    std::vector<Seg> segs;
+    if (batch_tables(nprob, n, zeros.data(), zeros.data(), op.o, chain_grid(op.o.grid_ctas, nmax),
+                     &D, &segs) != 0)
+        return 0;
+    return make_layout(D, true).total;
+}
+
+int tinv_batch(int64_t nprob, const int64_t* n, const int64_t* off_de, const int64_t* off_z,
+               const double* d, const double* e, const double* w, double* Z, int64_t* info,
+               const tinv_opts* o)
+{
+    const Opts op(o);
+    if (nprob < 0) return -1;
+    if (nprob == 0) return 0;
+    if (!n) return -2;
+    if (!off_de) return -3;
+    if (!off_z) return -4;
+    if (op.o.method != TINV_CWY && op.o.method != TINV_MGS) return -10;
+    int64_t nmax = 1, de_len = 0, e_len = 0, z_len = 0;
+    for (int64_t q = 0; q < nprob; ++q) {
+        if (n[q] < 0) return -2;
+        nmax = n[q] > nmax ? n[q] : nmax;
+        if (n[q] == 0) continue;
+        de_len = off_de[q] + n[q] > de_len ? off_de[q] + n[q] : de_len;
+        e_len = off_de[q] + n[q] - 1 > e_len ? off_de[q] + n[q] - 1 : e_len;
+        z_len = off_z[q] + n[q] * n[q] > z_len ? off_z[q] + n[q] * n[q] : z_len;
+    }
+    if (de_len > 0 && !d) return -5;
+    if (e_len > 0 && !e) return -6;
+    if (de_len > 0 && !w) return -7;
+    if (z_len > 0 && !Z) return -8;
+    const int32_t P = chain_grid(op.o.grid_ctas, nmax);
+    Dims D;
+    std::vector<Seg> segs;
+    int rc = batch_tables(nprob, n, off_de, off_z, op.o, P, &D, &segs);
+    if (rc != 0) return rc;
+    if (D.M == 0) return 0;
+
+    Problem p;
+    memset(&p, 0, sizeof(p));
+    p.n = D.nmax;
+    p.method = op.o.method;
+    p.seg_preset = 1;
+    p.nseg = nprob;
+    p.M = D.M;
+    const Layout L = make_layout(D, true);
+
+    if (op.o.device_ptrs) {
+        cudaStream_t st = (cudaStream_t)op.o.stream;
+        p.d = d;
+        p.e = e;
+        p.w = w;
+        p.Z = Z;
+        p.iters = op.o.iters;
+        DevBuf own;
+        void* ws = op.o.workspace;
+        if (ws) {
+            if (op.o.workspace_bytes < L.total) return TINV_EWORKSPACE;
+        } else {
+            cudaError_t ce = own.alloc(L.total, st, true);
+            if (ce != cudaSuccess) return TINV_ENOMEM;
+            ws = own.p;
+        }
+        const Ws wsb = bind_layout(ws, L, D);
+        cudaError_t ce = cudaMemcpyAsync(wsb.segs, segs.data(), segs.size() * sizeof(Seg),
+                                         cudaMemcpyHostToDevice, st);
+        if (ce != cudaSuccess) return cuda_code(ce);
+        rc = enqueue_tinv(p, ws, D, op.o.max_team, st, op.o.phase_ms);
+        if (rc != 0) return rc;
+        if (info) {
+            k_finish_batch<<<(unsigned)((nprob + 255) / 256), 256, 0, st>>>(wsb.ctr, wsb.sinfo, nprob, info);
+            if (cudaGetLastError() != cudaSuccess) return TINV_ECUDA;
+        }
+        if (op.o.info) {
+            k_finish<<<1, 1, 0, st>>>(wsb.ctr, op.o.info);
+            if (cudaGetLastError() != cudaSuccess) return TINV_ECUDA;
+        }
+        return 0;
+    }
+
+    // ---- host pointers: validate values, copy in, run, copy out ----
+    for (int64_t q = 0; q < nprob; ++q) {
+        const int64_t nq = n[q];
+        if (nq == 0) continue;
+        if (!all_finite(d + off_de[q], nq)) return -5;
+        if (nq > 1 && !all_finite(e + off_de[q], nq - 1)) return -6;
+        if (!all_finite(w + off_de[q], nq) || !ascending(w + off_de[q], nq)) return -7;
+    }
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return TINV_ENODEV;
+    rc = 0;
+    {
+        DevBuf dd, de, dw, dz, dit, ws;
+        cudaError_t ce = dd.alloc((size_t)de_len * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = de.alloc((size_t)(e_len > 0 ? e_len : 1) * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = dw.alloc((size_t)de_len * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = dz.alloc((size_t)z_len * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = dit.alloc((size_t)D.M * sizeof(int32_t), st, true);
+        if (ce == cudaSuccess) ce = ws.alloc(L.total, st, true);
+        if (ce != cudaSuccess) rc = TINV_ENOMEM;
+        const Ws wsb = bind_layout(ws.p, L, D);
+        if (!rc) {
+            ce = cudaMemcpyAsync(dd.p, d, (size_t)de_len * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess && e_len > 0)
+                ce = cudaMemcpyAsync(de.p, e, (size_t)e_len * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(dw.p, w, (size_t)de_len * sizeof(double), cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(wsb.segs, segs.data(), segs.size() * sizeof(Seg),
+                                     cudaMemcpyHostToDevice, st);
+            rc = cuda_code(ce);
+        }
+        if (!rc) {
+            p.d = (const double*)dd.p;
+            p.e = (const double*)de.p;
+            p.w = (const double*)dw.p;
+            p.Z = (double*)dz.p;
+            p.iters = (int32_t*)dit.p;
+            rc = enqueue_tinv(p, ws.p, D, op.o.max_team, st, op.o.phase_ms);
+        }
+        int64_t ctr[kCtrCount];
+        std::vector<int64_t> sinfo((size_t)nprob);
+        std::vector<int32_t> its;
+        if (!rc) {
+            for (int64_t q = 0; q < nprob && ce == cudaSuccess; ++q)
+                if (n[q] > 0)
+                    ce = cudaMemcpyAsync(Z + off_z[q], (double*)dz.p + off_z[q],
+                                         (size_t)(n[q] * n[q]) * sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(ctr, wsb.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(sinfo.data(), wsb.sinfo, (size_t)nprob * sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess && op.o.iters)
+                ce = cudaMemcpyAsync(op.o.iters, dit.p, (size_t)D.M * sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, st);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+            rc = cuda_code(ce);
+        }
+        if (!rc) {
+            if (ctr[kCtrErr]) {
+                rc = TINV_ETIMEDOUT;
+                if (info)
+                    for (int64_t q = 0; q < nprob; ++q) info[q] = TINV_ETIMEDOUT;
+            } else {
+                int64_t cnt = 0;
+                for (int64_t q = 0; q < nprob; ++q) {
+                    if (info) info[q] = sinfo[(size_t)q];
+                    cnt += sinfo[(size_t)q];
+                }
+                rc = cnt > INT32_MAX ? INT32_MAX : (int)cnt;
+            }
+        }
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return rc;
+}
+
 int tinv_plan(int64_t n, const double* d, const double* e, int64_t m, const double* w,
               double* wp, int32_t* head, double* scal, const tinv_opts* o)
 {
@@ -406,12 +638,16 @@ int tinv_plan(int64_t n, const double* d, const double* e, int64_t m, const doub
     if (m > 0 && !head) return -7;
     if (!scal) return -8;
     const int32_t P = chain_grid(op.o.grid_ctas, n);
-    const Layout L = make_layout(n, m, P, false);
+    const Dims D = single_dims(n, m, P);
+    const Layout L = make_layout(D, false);
     Problem p;
     memset(&p, 0, sizeof(p));
     p.n = n;
     p.m = m;
+    p.ldz = n;
     p.method = op.o.method;
+    p.nseg = 1;
+    p.M = m;
     cudaStream_t st = op.o.device_ptrs ? (cudaStream_t)op.o.stream : nullptr;
     bool own_stream = false;
     if (!op.o.device_ptrs) {
@@ -443,7 +679,7 @@ int tinv_plan(int64_t n, const double* d, const double* e, int64_t m, const doub
             p.w = w;
         }
         rc = cuda_code(ce);
-        const Ws wsb = bind_layout(ws.p, L, n, m, P);
+        const Ws wsb = bind_layout(ws.p, L, D);
         if (!rc) rc = cuda_code(launch_plan(p, wsb, 0, st));
         if (!rc) {
             const cudaMemcpyKind k = op.o.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -530,7 +766,8 @@ int tinv_solve(int64_t n, const double* d, const double* e, int64_t m, const dou
     if (ldx < n) return -7;
     if (m == 0) return 0;
     const int32_t P = chain_grid(op.o.grid_ctas, n);
-    const Layout L = make_layout(n, m, P, false);
+    const Dims D = single_dims(n, m, P);
+    const Layout L = make_layout(D, false);
     Problem p;
     memset(&p, 0, sizeof(p));
     p.n = n;
@@ -573,7 +810,7 @@ int tinv_solve(int64_t n, const double* d, const double* e, int64_t m, const dou
             p.w = s;
         }
         rc = cuda_code(ce);
-        const Ws wsb = bind_layout(ws.p, L, n, m, P);
+        const Ws wsb = bind_layout(ws.p, L, D);
         if (!rc) rc = cuda_code(launch_norm(p, wsb, st));
         if (!rc)
             rc = cuda_code(launch_lu(n, p.d, p.e, m, p.w, wsb.fl, wsb.fr, wsb.fu1, wsb.fu2, wsb.fpiv,
@@ -606,12 +843,15 @@ int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int
     if (op.o.method != TINV_CWY && op.o.method != TINV_MGS) return -9;
     if (m == 0) return 0;
     int32_t P = chain_grid(op.o.grid_ctas, n);
-    const Layout L = make_layout(n, m, P, true);
+    const Dims D = single_dims(n, m, P);
+    const Layout L = make_layout(D, true);
     Problem p;
     memset(&p, 0, sizeof(p));
     p.n = n;
     p.m = m;
     p.method = op.o.method;
+    p.nseg = 1;
+    p.M = m;
     cudaStream_t st = op.o.device_ptrs ? (cudaStream_t)op.o.stream : nullptr;
     bool own_stream = false;
     if (!op.o.device_ptrs) {
@@ -639,7 +879,7 @@ int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int
             p.ldz = ldq;
         }
         rc = cuda_code(ce);
-        Ws wsb = bind_layout(ws.p, L, n, m, P);
+        Ws wsb = bind_layout(ws.p, L, D);
         // team size for one cluster of m columns: at most n/16 CTAs
         const int32_t g = (int32_t)((n / 16 < (int64_t)P) ? (n / 16) : P);
         if (g >= 2 && op.o.method == TINV_CWY) {
@@ -649,7 +889,7 @@ int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int
         }
         if (op.o.max_team > 0 && wsb.P > op.o.max_team) wsb.P = op.o.max_team;
         if (wsb.P < 1) wsb.P = 1;
-        if (!rc) rc = cuda_code(launch_orth_plan(m, wsb, p.method, st));
+        if (!rc) rc = cuda_code(launch_orth_plan(p, wsb, p.method, st));
         if (!rc) rc = cuda_code(launch_chain(p, wsb, kModeOrth, V_dev, ldv_dev, st));
         const cudaMemcpyKind k = op.o.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         if (!rc && !op.o.device_ptrs) {

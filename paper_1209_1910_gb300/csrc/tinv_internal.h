@@ -18,8 +18,39 @@ constexpr int kErrBounds = 2;    // a debug bounds check failed (TINV_DEBUG buil
 
 enum ChainMode : int32_t { kModeInvit = 0, kModeOrth = 1 };
 
+// One independent tridiagonal problem of a launch (a whole tinv_ex call, or one problem of a
+// batch).  Eigenvalues of all problems are numbered globally, problem by problem: problem s owns
+// global indices [j0, j0 + m).  Its eigenvalue j has LU-factor rows (and, for cluster members,
+// a Y column) of n entries at element offset foff + (j - j0) n of the factor arrays.
+struct Seg {
+    int64_t n;        // order
+    int64_t m;        // number of eigenvalues / vectors
+    int64_t de;       // offset of d[0] and e[0] in the packed d and e arrays
+    int64_t wo;       // offset of w[0] in the packed w array
+    int64_t z;        // offset of Z[0, 0] in the packed Z array
+    int64_t ldz;      // leading dimension of this problem's Z
+    int64_t j0;       // first global eigenvalue index
+    int64_t foff;     // element offset of the factor rows / Y columns of eigenvalue j0
+    int64_t kj0;      // start-vector key index of eigenvalue j0
+    uint64_t seed;    // start-vector key seed
+    double onenrm, ortol, dtpcrt;  // ||T||_1, 1e-3 ||T||_1, sqrt(0.1/n)   (written by the plan)
+    double pad;
+};
+
+// Sizes a workspace is laid out for.
+struct Dims {
+    int64_t nmax;   // largest order of any problem
+    int64_t M;      // total eigenvalues
+    int64_t F;      // total factor elements: sum over problems of n m
+    int64_t TT;     // elements reserved for T: sum over problems of m^2
+    int64_t nseg;   // problems
+    int32_t P;      // persistent grid size
+};
+Dims single_dims(int64_t n, int64_t m, int32_t P);
+
 // Byte offsets of every device array inside one workspace allocation.
 struct Layout {
+    size_t segs, segj, sinfo;
     size_t scal, wp, head, clstart, clsize, cltoff, sched, queue, ctr, bar;
     size_t fl, fu1, fu2, fr, fpiv, u0n, tolv;
     size_t Y, T, partS, partG, partScal, vecS, vecX, vecR, qbuf, vbuf, tpub, gvec;
@@ -37,51 +68,63 @@ enum CtrIdx : int {
     kCtrCount = 8
 };
 
+// Kernel arguments of a launch.  With seg_preset == 0 the problem table has one entry that
+// the plan kernel fills from n, m, ldz, seed and j0; otherwise the table was copied into the
+// workspace by the host before the launch.
 struct Problem {
-    int64_t n, m, ldz;
-    const double* d;  // [n]
-    const double* e;  // [n-1]
-    const double* w;  // [m]
-    double* Z;        // n x m, ldz
-    int32_t* iters;   // [m] or null
+    int64_t n, m, ldz;  // single problem (seg_preset == 0); n = largest order otherwise
+    const double* d;    // packed diagonals
+    const double* e;    // packed off-diagonals
+    const double* w;    // packed eigenvalue approximations
+    double* Z;          // packed eigenvectors
+    int32_t* iters;     // [M] or null
     int32_t method;
+    int32_t seg_preset;
     uint64_t seed;
     int64_t j0;
+    int64_t nseg, M;
 };
 
 // All device pointers derived from one workspace (see Layout).
 struct Ws {
-    double* scal;     // [4]  onenrm, ortol, dtpcrt
-    double* wp;       // [m]
-    int32_t* head;    // [m]
-    int32_t* clstart; // [m]
-    int32_t* clsize;  // [m]
-    int64_t* cltoff;  // [m]
+    Seg* segs;        // [nseg]
+    int32_t* segj;    // [M]  problem of each global eigenvalue
+    int64_t* sinfo;   // [nseg] non-converged vectors per problem
+    double* scal;     // [4]  onenrm, ortol, dtpcrt of a single problem (tinv_plan)
+    double* wp;       // [M]
+    int32_t* head;    // [M]
+    int32_t* clstart; // [M]
+    int32_t* clsize;  // [M]
+    int64_t* cltoff;  // [M]
     int32_t* sched;   // [P*4] team_first, team_size, team_rank, team_cluster
-    int32_t* queue;   // [m]
+    int32_t* queue;   // [M]
     int64_t* ctr;     // [kCtrCount]
     uint32_t* bar;    // [P]
-    double *fl, *fu1, *fu2, *fr;  // [m*n] LU factors, row j = shift j
-    uint8_t* fpiv;    // [m*n]
-    double* u0n;      // [m]   |u_nn| before perturbation
-    double* tolv;     // [m]   tiny-pivot threshold eps max|U| per shift
-    double* Y;        // [n*m]
-    double* T;        // [m*m]
-    double *partS, *partG;  // [P*n]
+    double *fl, *fu1, *fu2, *fr;  // [F] LU factors, a row of n per eigenvalue
+    uint8_t* fpiv;    // [F]
+    double* u0n;      // [M]   |u_nn| before perturbation
+    double* tolv;     // [M]   tiny-pivot threshold eps max|U| per shift
+    double* Y;        // [F]
+    double* T;        // [TT]
+    double *partS, *partG;  // [P*nmax]
     double* partScal;       // [P*kScalTeam]
-    double *vecS, *vecX, *vecR, *qbuf;  // [P*n]
-    double* vbuf;     // [P*n]  solved iterate of each team (rows of all CTAs)
+    double *vecS, *vecX, *vecR, *qbuf;  // [P*nmax]
+    double* vbuf;     // [P*nmax]  solved iterate of each team (rows of all CTAs)
     double* tpub;     // [P*8]  published solve maps of each team (2 + 6 doubles per rank)
-    double* gvec;     // [P*2n] global fallback for the per-CTA vectors (large n)
+    double* gvec;     // [P*2*nmax] global fallback for the per-CTA vectors (large n)
     int32_t P;        // persistent grid size the schedule was made for
     int32_t use_smem; // per-CTA vectors live in shared memory
 };
 
-Layout make_layout(int64_t n, int64_t m, int32_t P, bool need_chain);
-Ws bind_layout(void* base, const Layout& L, int64_t n, int64_t m, int32_t P);
+Layout make_layout(const Dims& D, bool need_chain);
+Ws bind_layout(void* base, const Layout& L, const Dims& D);
 
 // Kernel launchers (tinv_kernels.cu).  All enqueue on `st` and return cudaGetLastError().
 cudaError_t launch_plan(const Problem& p, const Ws& w, int32_t max_team, cudaStream_t st);
+// Norm and tolerances of a single problem only (into w.scal), for the stand-alone solve.
+cudaError_t launch_norm(const Problem& p, const Ws& w, cudaStream_t st);
+// LU of every eigenvalue's shifted matrix (problem table, perturbed shifts wp), solve-ready.
+cudaError_t launch_lu_seg(const Problem& p, const Ws& w, cudaStream_t st);
 // LU of T - shift_j I for all j.  With tolv != null the diagonal is turned into perturbed
 // reciprocals r = 1/u0 (solve-ready) and tolv[j] receives the tiny-pivot threshold; with
 // tolv == null u0 is left as is.
@@ -95,11 +138,11 @@ cudaError_t launch_chain(const Problem& p, const Ws& w, int32_t mode, const doub
 cudaError_t launch_finalize(const Problem& p, const Ws& w, cudaStream_t st);
 cudaError_t launch_solve_rhs(int64_t n, int64_t m, const Ws& w, double* X, int64_t ldx,
                              int32_t scale, cudaStream_t st);
-cudaError_t launch_orth_plan(int64_t m, const Ws& w, int32_t method, cudaStream_t st);
+cudaError_t launch_orth_plan(const Problem& p, const Ws& w, int32_t method, cudaStream_t st);
 cudaError_t launch_finish_info(const Problem& p, const Ws& w, int64_t* info_out, cudaStream_t st);
 
-// Persistent-grid size (co-resident CTAs of the chain kernel) for order n on the current device,
-// and the threads per CTA it runs with (256 with two CTAs per SM, or 512 with one).
+// Persistent-grid size (co-resident CTAs of the chain kernel) on the current device, and the
+// threads per CTA it runs with.
 int32_t chain_grid(int32_t cap, int64_t n);
 int32_t chain_threads(int64_t n);
 size_t chain_smem_bytes(int64_t n, bool use_smem);

@@ -1,8 +1,10 @@
 // tinv_kernels.cu -- sm_103a kernels of libtinv.
 //
-//   k_plan   : ||T||_1, cluster tolerance, DSTEIN shift perturbation, Peters-Wilkinson cluster
-//              heads (Sec. 2.1; Alg. 4 lines 8-9, 17-18), cluster list, T offsets and the
-//              assignment of clusters to CTA teams of the persistent kernel.
+//   k_plan_seg : one CTA per problem: ||T||_1, cluster tolerance, DSTEIN shift perturbation
+//                (Sec. 2.1; Alg. 4).
+//   k_plan_list: Peters-Wilkinson cluster heads over all problems (Alg. 4), cluster
+//                list, T offsets and the assignment of clusters to CTA teams of the persistent
+//                kernel (large clusters) or to its work queue (the rest, largest first).
 //   k_lu     : one thread per shift: LU with scaled partial pivoting of T - s_j I (Eq. 1).
 //   k_first  : one warp per eigenvalue: random start, DSTEIN scaling and the chunked solve; full
 //              sweep loop + normalization for cluster heads and singletons (Alg. 1 / Alg. 4
@@ -60,79 +62,149 @@ struct OpAdd {
     __device__ T operator()(T a, T b) const { return a + b; }
 };
 
-__device__ __forceinline__ bool new_cluster(const double* wp, int64_t j, double ortol)
+// ||T||_1 = max_i (|d_i| + |e_{i-1}|) + |e_i|   (added in this order, as the oracle)
+__device__ double block_onenorm(int64_t n, const double* d, const double* e, double* sredd)
 {
-    return j == 0 || fabs(__dsub_rn(wp[j], wp[j - 1])) > ortol;
-}
-
-__global__ void __launch_bounds__(kPlanThreads) k_plan(Problem p, Ws w, int32_t max_team,
-                                                       int32_t norm_only)
-{
-    __shared__ double sredd[33];
-    __shared__ int32_t sredi[33];
-    __shared__ int64_t sredl[33];
-    __shared__ int s_tight;
-    const int t = threadIdx.x, B = blockDim.x;
-    const int64_t n = p.n, m = p.m;
-
-    // ||T||_1 = max_i (|d_i| + |e_{i-1}|) + |e_i|   (added in this order, as the oracle)
     double loc = 0.0;
-    for (int64_t i = t; i < n; i += B) {
-        double s = fabs(p.d[i]);
-        if (i > 0) s = __dadd_rn(s, fabs(p.e[i - 1]));
-        if (i < n - 1) s = __dadd_rn(s, fabs(p.e[i]));
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        double s = fabs(d[i]);
+        if (i > 0) s = __dadd_rn(s, fabs(e[i - 1]));
+        if (i < n - 1) s = __dadd_rn(s, fabs(e[i]));
         loc = fmax(loc, s);
     }
-    const double onenrm = block_max(loc, sredd);
-    const double ortol = __dmul_rn(1e-3, onenrm);
-    const double dtpcrt = __dsqrt_rn(__ddiv_rn(0.1, (double)n));
-    if (t == 0) {
+    return block_max(loc, sredd);
+}
+
+// Norm and tolerances of a single problem (the stand-alone solve): w.scal and the counters.
+__global__ void __launch_bounds__(kPlanThreads) k_norm(Problem p, Ws w)
+{
+    __shared__ double sredd[33];
+    const double onenrm = block_onenorm(p.n, p.d, p.e, sredd);
+    if (threadIdx.x == 0) {
         w.scal[0] = onenrm;
-        w.scal[1] = ortol;
-        w.scal[2] = dtpcrt;
+        w.scal[1] = __dmul_rn(1e-3, onenrm);
+        w.scal[2] = __dsqrt_rn(__ddiv_rn(0.1, (double)p.n));
         w.scal[3] = 0.0;
         for (int c = 0; c < kCtrCount; ++c) w.ctr[c] = 0;
-        s_tight = 0;
     }
-    for (int b = t; b < w.P; b += B) w.bar[b] = 0u;
-    if (norm_only) return;
-    __syncthreads();
+}
 
-    // Shift perturbation (DSTEIN): if w_j - w'_{j-1} < 10 eps |w_j| then
-    // w'_j = w'_{j-1} + 10 eps |w_j|.  Without any such pair w' = w; otherwise one thread scans.
+// Plan, part 1: one CTA per problem.  ||T||_1, the cluster tolerance, the convergence threshold
+// (Sec. 2.1; Alg. 4), the problem index of each eigenvalue and the DSTEIN shift
+// perturbation: if w_j - w'_{j-1} < 10 eps |w_j| then w'_j = w'_{j-1} + 10 eps |w_j|.
+__global__ void __launch_bounds__(kPlanThreads) k_plan_seg(Problem p, Ws w)
+{
+    __shared__ double sredd[33];
+    __shared__ int s_tight;
+    const int t = threadIdx.x, B = blockDim.x;
+    const int32_t sidx = blockIdx.x;
+    if (!p.seg_preset) {
+        if (t == 0) {
+            Seg g;
+            memset(&g, 0, sizeof(g));
+            g.n = p.n;
+            g.m = p.m;
+            g.ldz = p.ldz;
+            g.kj0 = p.j0;
+            g.seed = p.seed;
+            w.segs[0] = g;
+        }
+        __syncthreads();
+    }
+    const Seg g = w.segs[sidx];
+    const int64_t n = g.n, m = g.m;
+    const double* d = p.d + g.de;
+    const double* e = p.e + g.de;
+    const double* wv = p.w + g.wo;
+    const double onenrm = n > 0 ? block_onenorm(n, d, e, sredd) : 0.0;
+    const double ortol = __dmul_rn(1e-3, onenrm);
+    const double dtpcrt = n > 0 ? __dsqrt_rn(__ddiv_rn(0.1, (double)n)) : 0.0;
+    if (t == 0) {
+        w.segs[sidx].onenrm = onenrm;
+        w.segs[sidx].ortol = ortol;
+        w.segs[sidx].dtpcrt = dtpcrt;
+        w.sinfo[sidx] = 0;
+        s_tight = 0;
+        if (sidx == 0) {
+            w.scal[0] = onenrm;
+            w.scal[1] = ortol;
+            w.scal[2] = dtpcrt;
+            w.scal[3] = 0.0;
+            for (int c = 0; c < kCtrCount; ++c) w.ctr[c] = 0;
+        }
+    }
+    if (sidx == 0)
+        for (int b = t; b < w.P; b += B) w.bar[b] = 0u;
+    for (int64_t jl = t; jl < m; jl += B) w.segj[g.j0 + jl] = sidx;
+    __syncthreads();
+    // without any tight pair w' = w; otherwise one thread scans
     for (int64_t j = 1 + t; j < m; j += B) {
-        const double xj = p.w[j];
+        const double xj = wv[j];
         const double pertol = __dmul_rn(10.0, fabs(__dmul_rn(kEps, xj)));
-        if (__dsub_rn(xj, p.w[j - 1]) < pertol) s_tight = 1;
+        if (__dsub_rn(xj, wv[j - 1]) < pertol) s_tight = 1;
     }
     __syncthreads();
+    double* wp = w.wp + g.j0;
     if (s_tight == 0) {
-        for (int64_t j = t; j < m; j += B) w.wp[j] = p.w[j];
+        for (int64_t j = t; j < m; j += B) wp[j] = wv[j];
     } else if (t == 0) {
         double xjm = 0.0;
         for (int64_t j = 0; j < m; ++j) {
-            double xj = p.w[j];
+            double xj = wv[j];
             if (j > 0) {
                 const double pertol = __dmul_rn(10.0, fabs(__dmul_rn(kEps, xj)));
                 if (__dsub_rn(xj, xjm) < pertol) xj = __dadd_rn(xjm, pertol);
             }
-            w.wp[j] = xj;
+            wp[j] = xj;
             xjm = xj;
         }
     }
-    __syncthreads();
+}
 
-    // Cluster heads (max-scan of head positions) and the list of clusters with >= 2 members:
-    // a start is a head whose successor continues its cluster, an end is a member whose
-    // successor is a head (or the last index); starts and ends pair up in order.
+// Peters-Wilkinson test on consecutive perturbed shifts of one problem (Sec. 2.1): a new cluster
+// starts at the problem's first eigenvalue or after a gap larger than 1e-3 ||T||_1.
+__device__ __forceinline__ bool new_cluster(const Ws& w, int64_t j)
+{
+    const Seg* g = w.segs + w.segj[j];
+    return j == g->j0 || fabs(__dsub_rn(w.wp[j], w.wp[j - 1])) > g->ortol;
+}
+
+// Work of one cluster (flops of its reorthogonalization grow as size^2 n) and the team-size cap.
+__device__ __forceinline__ double cluster_work(const Ws& w, int32_t c)
+{
+    const double sz = (double)w.clsize[c];
+    return sz * sz * (double)w.segs[w.segj[w.clstart[c]]].n;
+}
+
+constexpr int kMaxCand = 1024;  // team candidates: at most P / 2 <= 1024
+
+// Plan, part 2: one CTA over all eigenvalues.  Cluster heads and the list of clusters with >= 2
+// members, T offsets, and the assignment of clusters to CTA teams of the persistent kernel:
+// clusters whose share of the work is worth >= 2 CTAs get a contiguous team; the rest form a
+// queue, largest first, served by single CTAs (also by team CTAs once their cluster is done).
+__global__ void __launch_bounds__(kPlanThreads) k_plan_list(Problem p, Ws w, int32_t max_team)
+{
+    __shared__ double sredd[33];
+    __shared__ int32_t sredi[33];
+    __shared__ int64_t sredl[33];
+    __shared__ int32_t s_cand[kMaxCand];
+    __shared__ uint8_t s_team[kMaxCand];
+    __shared__ int32_t s_hist[64], s_cur[64];
+    __shared__ int32_t s_ncand;
+    const int t = threadIdx.x, B = blockDim.x;
+    const int64_t M = p.M;
+    const int32_t P = w.P;
+
+    // heads (max-scan of head positions); a start is a head whose successor continues its
+    // cluster, an end is a member whose successor is a head (or the last index)
     int32_t carry_head = 0, carry_cnt = 0, carry_end = 0;
-    for (int64_t base = 0; base < m; base += B) {
+    for (int64_t base = 0; base < M; base += B) {
         const int64_t j = base + t;
-        const bool in = j < m;
-        const bool fj = in && new_cluster(w.wp, j, ortol);
-        const bool fj1 = in && (j + 1 < m) && new_cluster(w.wp, j + 1, ortol);
-        const bool is_start = fj && (j + 1 < m) && !fj1;
-        const bool is_end = in && !fj && (j + 1 == m || fj1);
+        const bool in = j < M;
+        const bool fj = in && new_cluster(w, j);
+        const bool fj1 = in && (j + 1 < M) && new_cluster(w, j + 1);
+        const bool is_start = fj && (j + 1 < M) && !fj1;
+        const bool is_end = in && !fj && (j + 1 == M || fj1);
         int32_t tot, tot2, tot3;
         int32_t hd = block_scan_incl<int32_t>(fj ? (int32_t)j : 0, sredi, OpMax(), 0, &tot);
         hd = max(hd, carry_head);
@@ -159,68 +231,99 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(Problem p, Ws w, int32_t 
         carry_off += tot;
         __syncthreads();
     }
+    for (int32_t b = t; b < P; b += B) {
+        w.sched[4 * b + 0] = b;
+        w.sched[4 * b + 1] = 1;
+        w.sched[4 * b + 2] = 0;
+        w.sched[4 * b + 3] = -1;
+    }
+    if (t < 64) s_hist[t] = 0;
     if (t == 0) {
         w.ctr[kCtrNClust] = K;
         w.ctr[kCtrTSize] = carry_off;
+        s_ncand = 0;
     }
+    __syncthreads();
 
-    // Team schedule (one thread): clusters whose share of the work (~ m_c^2) is worth >= 2 CTAs
-    // get a contiguous team of CTAs; the rest form a queue served by single CTAs.  CTAs that
-    // finish their team's cluster join the queue.
+    // team candidates (MGS and single-CTA grids use the queue only)
+    double wl = 0.0;
+    for (int32_t c = t; c < K; c += B) wl += cluster_work(w, c);
+    const double wtot = block_sum(wl, sredd);
+    const bool teams = (p.method == 0) && P >= 2 && K > 0;
+    int32_t carry_c = 0;
+    for (int32_t base = 0; base < K; base += B) {
+        const int32_t c = base + t;
+        bool cand = false;
+        if (teams && c < K) {
+            const double wc = cluster_work(w, c);
+            int64_t gmax = min((int64_t)P, max((int64_t)1, w.segs[w.segj[w.clstart[c]]].n / 16));
+            if (max_team > 0) gmax = min(gmax, (int64_t)max_team);
+            cand = floor((double)P * wc / wtot) >= 2.0 && gmax >= 2;
+        }
+        int32_t tot;
+        const int32_t pos = block_scan_incl<int32_t>(cand ? 1 : 0, sredi, OpAdd(), 0, &tot);
+        if (cand && carry_c + pos - 1 < kMaxCand) s_cand[carry_c + pos - 1] = c;
+        carry_c += tot;
+        __syncthreads();
+    }
+    const int32_t ncand = min(carry_c, kMaxCand);
     if (t == 0) {
-        const int32_t P = w.P;
-        for (int32_t b = 0; b < P; ++b) {
-            w.sched[4 * b + 0] = b;
-            w.sched[4 * b + 1] = 1;
-            w.sched[4 * b + 2] = 0;
-            w.sched[4 * b + 3] = -1;
-        }
-        int32_t nq = 0;
-        if (p.method != 0 || K == 0) {
-            for (int32_t c = 0; c < K; ++c) w.queue[nq++] = c;
-        } else {
-            double wtot = 0.0;
-            for (int32_t c = 0; c < K; ++c) wtot += (double)w.clsize[c] * (double)w.clsize[c];
-            int32_t gmax = (int32_t)min((int64_t)P, max((int64_t)1, n / 16));
+        double wteam = 0.0;
+        for (int32_t i = 0; i < ncand; ++i) wteam += cluster_work(w, s_cand[i]);
+        const double wq = wtot - wteam;
+        int32_t Q = 0;
+        if (wq > 0.0) Q = max(1, (int32_t)llrint(P * wq / wtot));
+        const int32_t Pteam = max(0, P - Q);
+        int32_t next = 0;
+        for (int32_t i = 0; i < ncand; ++i) {
+            const int32_t c = s_cand[i];
+            const double wc = cluster_work(w, c);
+            int32_t gmax = (int32_t)min((int64_t)P, max((int64_t)1, w.segs[w.segj[w.clstart[c]]].n / 16));
             if (max_team > 0) gmax = min(gmax, max_team);
-            double wq = 0.0, wteam = 0.0;
-            for (int32_t c = 0; c < K; ++c) {
-                const double wc = (double)w.clsize[c] * (double)w.clsize[c];
-                if (floor(P * wc / wtot) >= 2.0 && gmax >= 2)
-                    wteam += wc;
-                else
-                    wq += wc;
-            }
-            int32_t Q = 0;
-            if (wq > 0.0) Q = max(1, (int32_t)llrint(P * wq / wtot));
-            const int32_t Pteam = max(0, P - Q);
-            int32_t next = 0;
-            for (int32_t c = 0; c < K; ++c) {
-                const double wc = (double)w.clsize[c] * (double)w.clsize[c];
-                int32_t g = 0;
-                if (floor(P * wc / wtot) >= 2.0 && gmax >= 2 && wteam > 0.0)
-                    g = min(gmax, (int32_t)floor(Pteam * wc / wteam));
-                if (g >= 2 && next + g <= Pteam) {
-                    for (int32_t r = 0; r < g; ++r) {
-                        const int32_t b = next + r;
-                        w.sched[4 * b + 0] = next;
-                        w.sched[4 * b + 1] = g;
-                        w.sched[4 * b + 2] = r;
-                        w.sched[4 * b + 3] = c;
-                    }
-                    next += g;
-                } else {
-                    w.queue[nq++] = c;
+            int32_t g = min(gmax, (int32_t)floor(Pteam * wc / wteam));
+            s_team[i] = 0;
+            if (g >= 2 && next + g <= Pteam) {
+                for (int32_t r = 0; r < g; ++r) {
+                    const int32_t b = next + r;
+                    w.sched[4 * b + 0] = next;
+                    w.sched[4 * b + 1] = g;
+                    w.sched[4 * b + 2] = r;
+                    w.sched[4 * b + 3] = c;
                 }
+                next += g;
+                s_team[i] = 1;
             }
         }
-        w.ctr[kCtrNQueue] = nq;
+        s_ncand = ncand;
+    }
+    __syncthreads();
+
+    // queue: every cluster without a team, in decreasing order of work (buckets of powers of 2)
+    auto on_team = [&](int32_t c) {
+        for (int32_t i = 0; i < s_ncand; ++i)
+            if (s_cand[i] == c) return s_team[i] != 0;
+        return false;
+    };
+    auto bucket = [&](int32_t c) { return 63 - min(63, max(0, ilogb(cluster_work(w, c)))); };
+    for (int32_t c = t; c < K; c += B)
+        if (!on_team(c)) atomicAdd(&s_hist[bucket(c)], 1);
+    __syncthreads();
+    if (t == 0) {
+        int32_t acc = 0;
+        for (int i = 0; i < 64; ++i) {
+            s_cur[i] = acc;
+            acc += s_hist[i];
+        }
+        w.ctr[kCtrNQueue] = acc;
         w.ctr[kCtrQHead] = 0;
     }
+    __syncthreads();
+    for (int32_t c = t; c < K; c += B)
+        if (!on_team(c)) w.queue[atomicAdd(&s_cur[bucket(c)], 1)] = c;
 }
 
-// Plan for stand-alone orthogonalization: one cluster made of all m columns.
-__global__ void k_orth_plan(int64_t m, Ws w, int32_t method)
+// Plan for stand-alone orthogonalization: one problem, one cluster made of all m columns.
+__global__ void k_orth_plan(Problem p, Ws w, int32_t method)
 {
     const int t = threadIdx.x;
     for (int b = t; b < w.P; b += blockDim.x) {
@@ -230,13 +333,20 @@ __global__ void k_orth_plan(int64_t m, Ws w, int32_t method)
         w.sched[4 * b + 2] = 0;
         w.sched[4 * b + 3] = -1;
     }
+    for (int64_t j = t; j < p.m; j += blockDim.x) w.segj[j] = 0;
     if (t == 0) {
+        Seg g;
+        memset(&g, 0, sizeof(g));
+        g.n = p.n;
+        g.m = p.m;
+        g.ldz = p.ldz;
+        w.segs[0] = g;
         for (int c = 0; c < kCtrCount; ++c) w.ctr[c] = 0;
         w.clstart[0] = 0;
-        w.clsize[0] = (int32_t)m;
+        w.clsize[0] = (int32_t)p.m;
         w.cltoff[0] = 0;
         w.ctr[kCtrNClust] = 1;
-        w.ctr[kCtrTSize] = m * m;
+        w.ctr[kCtrTSize] = p.m * p.m;
         w.scal[0] = w.scal[1] = w.scal[2] = w.scal[3] = 0.0;
     }
     __syncthreads();
@@ -289,20 +399,14 @@ __device__ __forceinline__ unsigned long long abs_bits(double x)
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-__global__ void k_lu(int64_t n, const double* __restrict__ d, const double* __restrict__ e,
-                     int64_t m, const double* __restrict__ shift, double* __restrict__ L,
-                     double* __restrict__ U0, double* __restrict__ U1, double* __restrict__ U2,
-                     uint8_t* __restrict__ PV, double* __restrict__ u0n, double* __restrict__ tolv)
+// LU of T - lam I (order n) into one row of each output; |u_nn| and the tiny-pivot threshold
+// eps max|U| (eps if U = 0) go to *u0n and *tolv when those are given.
+__device__ __forceinline__ void lu_row(int64_t n, const double* __restrict__ d,
+                                       const double* __restrict__ e, double lam, double* __restrict__ l,
+                                       double* __restrict__ u0, double* __restrict__ u1,
+                                       double* __restrict__ u2, uint8_t* __restrict__ pv,
+                                       double* u0n, double* tolv)
 {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    const double lam = shift[j];
-    const size_t base = (size_t)j * (size_t)n;
-    double* l = L + base;
-    double* u0 = U0 + base;
-    double* u1 = U1 + base;
-    double* u2 = U2 + base;
-    uint8_t* pv = PV + base;
     double ak = __dsub_rn(d[0], lam);
     double bk = (n > 1) ? e[0] : 0.0;
     unsigned long long umax = 0;  // max |U entry| as the bit pattern of a non-negative double
@@ -344,27 +448,59 @@ __global__ void k_lu(int64_t n, const double* __restrict__ d, const double* __re
     u2[n - 1] = 0.0;
     pv[n - 1] = 0;
     umax = max(umax, abs_bits(ak));
-    if (u0n) u0n[j] = fabs(ak);
+    if (u0n) *u0n = fabs(ak);
     if (tolv) {
-        // tiny-pivot threshold tol = eps * max|U| (eps if U = 0)
         double tol = __dmul_rn(kEps, __longlong_as_double((long long)umax));
         if (tol == 0.0) tol = kEps;
-        tolv[j] = tol;
+        *tolv = tol;
     }
 }
 
-// r = 1/u0 with tiny pivots |u0| < tol replaced by sign(u0) tol (sign(0) = +), in place,
-// for every (shift, row): all m*n entries in parallel.
+// One problem, shift j in row j (stride n) of every output (tinv_lu, tinv_solve).
+__global__ void k_lu(int64_t n, const double* __restrict__ d, const double* __restrict__ e,
+                     int64_t m, const double* __restrict__ shift, double* __restrict__ L,
+                     double* __restrict__ U0, double* __restrict__ U1, double* __restrict__ U2,
+                     uint8_t* __restrict__ PV, double* __restrict__ u0n, double* __restrict__ tolv)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const size_t base = (size_t)j * (size_t)n;
+    lu_row(n, d, e, shift[j], L + base, U0 + base, U1 + base, U2 + base, PV + base,
+           u0n ? u0n + j : nullptr, tolv ? tolv + j : nullptr);
+}
+
+// Problem table: global eigenvalue j of problem s, shift w'_j, rows at the problem's offsets.
+__global__ void k_lu_seg(Problem p, Ws w)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= p.M) return;
+    const Seg* g = w.segs + w.segj[j];
+    const int64_t n = g->n;
+    const size_t base = (size_t)(g->foff + (j - g->j0) * n);
+    lu_row(n, p.d + g->de, p.e + g->de, w.wp[j], w.fl + base, w.fr + base, w.fu1 + base,
+           w.fu2 + base, w.fpiv + base, w.u0n + j, w.tolv + j);
+}
+
+// r = 1/u0 with tiny pivots |u0| < tol replaced by sign(u0) tol (sign(0) = +), in place.
+__device__ __forceinline__ void recip_row(int64_t n, double* __restrict__ row, double tol)
+{
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        double a = row[k];
+        if (fabs(a) < tol) a = (a >= 0.0) ? tol : -tol;
+        row[k] = __drcp_rn(a);
+    }
+}
+
 __global__ void k_recip(int64_t n, int64_t m, double* __restrict__ U0R, const double* __restrict__ tolv)
 {
-    for (int64_t j = blockIdx.x; j < m; j += gridDim.x) {
-        const double tol = tolv[j];
-        double* row = U0R + (size_t)j * (size_t)n;
-        for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
-            double a = row[k];
-            if (fabs(a) < tol) a = (a >= 0.0) ? tol : -tol;
-            row[k] = __drcp_rn(a);
-        }
+    for (int64_t j = blockIdx.x; j < m; j += gridDim.x) recip_row(n, U0R + (size_t)j * (size_t)n, tolv[j]);
+}
+
+__global__ void k_recip_seg(Problem p, Ws w)
+{
+    for (int64_t j = blockIdx.x; j < p.M; j += gridDim.x) {
+        const Seg* g = w.segs + w.segj[j];
+        recip_row(g->n, w.fr + (size_t)(g->foff + (j - g->j0) * g->n), w.tolv[j]);
     }
 }
 
@@ -372,9 +508,8 @@ __global__ void k_recip(int64_t n, int64_t m, double* __restrict__ U0R, const do
 // One warp per eigenvalue: start vector, DSTEIN scaling, chunked solve, convergence test and
 // normalization (cluster heads and singletons); cluster members get their first solve only.
 // ==========================================================================================
-__device__ __forceinline__ Fac fac_of(const Ws& w, int64_t j, int64_t n)
+__device__ __forceinline__ Fac fac_at(const Ws& w, size_t base)
 {
-    const size_t base = (size_t)j * (size_t)n;
     Fac f;
     f.l = w.fl + base;
     f.u1 = w.fu1 + base;
@@ -382,6 +517,27 @@ __device__ __forceinline__ Fac fac_of(const Ws& w, int64_t j, int64_t n)
     f.r = w.fr + base;
     f.piv = w.fpiv + base;
     return f;
+}
+
+// Factor rows of eigenvalue j of a single problem of order n (stand-alone solve).
+__device__ __forceinline__ Fac fac_of(const Ws& w, int64_t j, int64_t n)
+{
+    return fac_at(w, (size_t)j * (size_t)n);
+}
+
+// Global eigenvalue j of the problem table: its problem, local index and factor-row offset.
+struct JRef {
+    const Seg* g;
+    int64_t jl;
+    size_t off;
+};
+__device__ __forceinline__ JRef jref(const Ws& w, int64_t j)
+{
+    JRef r;
+    r.g = w.segs + w.segj[j];
+    r.jl = j - r.g->j0;
+    r.off = (size_t)(r.g->foff + r.jl * r.g->n);
+    return r;
 }
 
 __device__ void warp_scale(int64_t n, double* x, double onenrm, double u0n, int lane)
@@ -395,19 +551,35 @@ __device__ void warp_scale(int64_t n, double* x, double onenrm, double u0n, int 
     __syncwarp();
 }
 
+// Record a vector that did not converge (total and per problem).
+__device__ __forceinline__ void count_nonconverged(const Ws& w, int64_t j)
+{
+    atomicAdd((unsigned long long*)&w.ctr[kCtrInfo], 1ull);
+    atomicAdd((unsigned long long*)&w.sinfo[w.segj[j]], 1ull);
+}
+
 __global__ void __launch_bounds__(kFirstWarps * 32) k_first(Problem p, Ws w)
 {
     __shared__ double sh_all[kFirstWarps][8 * 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * kFirstWarps + warp;
-    if (j >= p.m) return;
+    if (j >= p.M) return;
     double* sh = sh_all[warp];
-    const int64_t n = p.n;
-    double* x = p.Z + j * p.ldz;
-    const Fac f = fac_of(w, j, n);
-    const double onenrm = w.scal[0], dtpcrt = w.scal[2], u0n = w.u0n[j];
+    const JRef jr = jref(w, j);
+    const Seg& g = *jr.g;
+    const int64_t n = g.n;
+    double* x = p.Z + g.z + jr.jl * g.ldz;
+    const Fac f = fac_at(w, jr.off);
+    const double onenrm = g.onenrm, dtpcrt = g.dtpcrt, u0n = w.u0n[j];
     const bool is_head = (w.head[j] == (int32_t)j);
-    const uint64_t key = start_key(p.seed, p.j0 + j, 0);
+    if (n == 1) {  // T = [d_1]: z = [1]
+        if (lane == 0) {
+            x[0] = 1.0;
+            if (p.iters) p.iters[j] = 1;
+        }
+        return;
+    }
+    const uint64_t key = start_key(g.seed, g.kj0 + jr.jl, 0);
     for (int64_t i = lane; i < n; i += 32) x[i] = start_value(key, i);
     __syncwarp();
     const int maxits = is_head ? kMaxIts : 1;
@@ -446,19 +618,20 @@ __global__ void __launch_bounds__(kFirstWarps * 32) k_first(Problem p, Ws w)
     for (int64_t i = lane; i < n; i += 32) x[i] *= s;
     if (lane == 0) {
         if (p.iters) p.iters[j] = conv ? its : -its;
-        if (!conv) atomicAdd((unsigned long long*)&w.ctr[kCtrInfo], 1ull);
+        if (!conv) count_nonconverged(w, j);
     }
 }
 
-// Alg. 4 line 21 for the compact-WY cluster members: z_j = q / ||q||_2 with the first entry of
+// Alg. 4 for the compact-WY cluster members: z_j = q / ||q||_2 with the first entry of
 // largest magnitude made positive.  One warp per column, all columns in parallel.
 __global__ void __launch_bounds__(kFirstWarps * 32) k_finalize(Problem p, Ws w)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * kFirstWarps + warp;
-    if (j >= p.m || w.head[j] == (int32_t)j) return;  // heads are final after k_first
-    double* x = p.Z + j * p.ldz;
-    const int64_t n = p.n;
+    if (j >= p.M || w.head[j] == (int32_t)j) return;  // heads are final after k_first
+    const JRef jr = jref(w, j);
+    double* x = p.Z + jr.g->z + jr.jl * jr.g->ldz;
+    const int64_t n = jr.g->n;
     double ss = 0.0, am = -1.0;
     int64_t ai = 0;
     for (int64_t i = lane; i < n; i += 32) {
@@ -633,29 +806,34 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
 {
     const Problem& p = cx.p;
     const Ws& w = cx.w;
-    const int64_t n = p.n;
     const int t = threadIdx.x;
     const int B = blockDim.x;
     const int G = tm.G, rank = tm.rank, leader = tm.leader;
     const int64_t s0 = w.clstart[c];
     const int64_t mc = w.clsize[c];
+    const JRef jr = jref(w, s0);  // the cluster's problem; members are consecutive
+    const Seg& sg = *jr.g;
+    const int64_t n = sg.n;
+    double* Zc = p.Z + sg.z + jr.jl * sg.ldz;  // column kk of Zc: member kk
+    const int64_t ldz = sg.ldz;
     double* Tc = w.T + w.cltoff[c];
     const int64_t ldt = mc;
-    double* Yc = w.Y + (size_t)s0 * (size_t)n;
-    double* vecS = w.vecS + (size_t)leader * n;
-    double* vecX = w.vecX + (size_t)leader * n;
-    double* vecR = w.vecR + (size_t)leader * n;
-    double* qbuf = w.qbuf + (size_t)leader * n;
-    double* vbuf = w.vbuf + (size_t)leader * n;
+    double* Yc = w.Y + jr.off;  // Y column and factor rows of member kk at + kk n
+    const size_t ns = (size_t)p.n;  // stride of the per-CTA buffers: the largest order
+    double* vecS = w.vecS + (size_t)leader * ns;
+    double* vecX = w.vecX + (size_t)leader * ns;
+    double* vecR = w.vecR + (size_t)leader * ns;
+    double* qbuf = w.qbuf + (size_t)leader * ns;
+    double* vbuf = w.vbuf + (size_t)leader * ns;
     double* pubf = w.tpub + (size_t)leader * 8;  // 2 doubles per rank, then 6 per rank
     double* pubb = pubf + 2 * G;
-    double* myS = w.partS + (size_t)(leader + rank) * n;
-    double* myG = w.partG + (size_t)(leader + rank) * n;
+    double* myS = w.partS + (size_t)(leader + rank) * ns;
+    double* myG = w.partG + (size_t)(leader + rank) * ns;
     double* scal_t = w.partScal + (size_t)leader * kScalTeam;  // rank r at + r*kScalTeam
     double* vsm = cx.vsm;
     double* s1 = cx.s1;
     double* red = cx.red;
-    const double onenrm = w.scal[0], dtpcrt = w.scal[2];
+    const double onenrm = sg.onenrm, dtpcrt = sg.dtpcrt;
     const bool orth = (cx.mode == kModeOrth);
     __shared__ double s_b[8];
 
@@ -664,8 +842,8 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
 
     int64_t kstart = 0;
     if (!orth) {
-        // Alg. 4 lines 10-12: Y_1 = [y_1], T_1 = [t_1] from the final head vector z.
-        const double* z = p.Z + s0 * p.ldz;
+        // Alg. 4: Y_1 = [y_1], T_1 = [t_1] from the final head vector z.
+        const double* z = Zc;
         double ss = 0.0;
         for (int64_t r = ra0 + t; r < ra1; r += B) ss = fma(z[r], z[r], ss);
         ss = block_sum(ss, red);
@@ -703,7 +881,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
         const int64_t k = kk;  // previous reflectors: columns 0..k-1 of Yc
         // stage r = row k of Y_k into vecR (spread over the team)
         for (int64_t l = (int64_t)rank * B + t; l < k; l += (int64_t)G * B) vecR[l] = Yc[k + l * n];
-        const Fac f = orth ? Fac{} : fac_of(w, j, n);
+        const Fac f = orth ? Fac{} : fac_at(w, jr.off + (size_t)kk * (size_t)n);
         const double u0n = orth ? 0.0 : w.u0n[j];
         // balanced bounds of this CTA's share of the T products (FP64 sqrt: one thread, once
         // per member; every CTA of the team computes the same values)
@@ -724,7 +902,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             ++its;
             // ---- the iterate v: rows [ra0, ra1) in shared memory, all rows in vsrc ----
             PROF_MARK(cx.prof, kPhEnd);
-            const double* vsrc = orth ? cx.V + kk * cx.ldv : (its == 1 ? p.Z + j * p.ldz : vbuf);
+            const double* vsrc = orth ? cx.V + kk * cx.ldv : (its == 1 ? Zc + kk * ldz : vbuf);
             if (!orth && its > 1) {
                 PROF_MARK(cx.prof, kPhLoad);
                 TeamRef tr{tm.bar, &tm.target, G, rank, cx.err};
@@ -747,7 +925,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 PROF_MARK(cx.prof, kPhB1);
                 for (int64_t l = t; l < c1; l += B) {
                     double a = 0.0;
-                    a = sum_partials(w.partS + (size_t)leader * n + l, (size_t)n, G);
+                    a = sum_partials(w.partS + (size_t)leader * ns + l, ns, G);
                     s1[l] = a;
                 }
                 __syncthreads();
@@ -807,7 +985,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 }
             } else {
                 for (int64_t l = i0 + (t - 32); l < k; l += B - 32)
-                    s1[l] = sum_partials(w.partG + (size_t)leader * n + l, (size_t)n, G);
+                    s1[l] = sum_partials(w.partG + (size_t)leader * ns + l, ns, G);
             }
             __syncthreads();
             const double cc = s_b[0], tk = s_b[1], ykk = s_b[2];
@@ -865,7 +1043,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             PROF_MARK(cx.prof, kPhB5);
             if (orth) {
                 for (int64_t r = ra0 + t; r < ra1; r += B)
-                    p.Z[r + kk * p.ldz] = qbuf[r];
+                    Zc[r + kk * ldz] = qbuf[r];
                 break;
             }
             // ---- team statistics, convergence test on x = -c q (||x||_inf = |c| max|q|) ----
@@ -886,11 +1064,11 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             const bool success = !broke && fabs(cc) * M >= dtpcrt;
             if (success && ++nrmchk >= kExtra + 1) conv = true;
             if (conv || its == maxits) {
-                // Alg. 4 line 21 (normalization and sign) is applied by k_finalize
-                for (int64_t r = ra0 + t; r < ra1; r += B) p.Z[r + j * p.ldz] = qbuf[r];
+                // Alg. 4 (normalization and sign) is applied by k_finalize
+                for (int64_t r = ra0 + t; r < ra1; r += B) Zc[r + kk * ldz] = qbuf[r];
                 if (rank == 0 && t == 0) {
                     if (p.iters) p.iters[j] = conv ? its : -its;
-                    if (!conv) atomicAdd((unsigned long long*)&w.ctr[kCtrInfo], 1ull);
+                    if (!conv) count_nonconverged(w, j);
                 }
                 break;
             }
@@ -908,18 +1086,22 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
 {
     const Problem& p = cx.p;
     const Ws& w = cx.w;
-    const int64_t n = p.n;
     const int t = threadIdx.x, B = blockDim.x;
     const int64_t s0 = w.clstart[c];
     const int64_t mc = w.clsize[c];
+    const JRef jr = jref(w, s0);  // the cluster's problem; members are consecutive
+    const Seg& sg = *jr.g;
+    const int64_t n = sg.n;
+    double* Zc = p.Z + sg.z + jr.jl * sg.ldz;  // column kk of Zc: member kk
+    const int64_t ldz = sg.ldz;
     double* v = cx.vsm;
     double* red = cx.red;
     const bool orth = (cx.mode == kModeOrth);
-    const double onenrm = w.scal[0], dtpcrt = w.scal[2];
+    const double onenrm = sg.onenrm, dtpcrt = sg.dtpcrt;
     const int64_t kstart = orth ? 0 : 1;
     for (int64_t kk = kstart; kk < mc; ++kk) {
         const int64_t j = s0 + kk;
-        const Fac f = orth ? Fac{} : fac_of(w, j, n);
+        const Fac f = orth ? Fac{} : fac_at(w, jr.off + (size_t)kk * (size_t)n);
         const double u0n = orth ? 0.0 : w.u0n[j];
         int nrmchk = 0, its = 0, attempt = 0;
         bool conv = false;
@@ -930,7 +1112,7 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
                 for (int64_t r = t; r < n; r += B) v[r] = cx.V[r + kk * cx.ldv];
                 __syncthreads();
             } else if (its == 1) {
-                for (int64_t r = t; r < n; r += B) v[r] = p.Z[r + j * p.ldz];
+                for (int64_t r = t; r < n; r += B) v[r] = Zc[r + kk * ldz];
                 __syncthreads();
             } else {
                 double as = 0.0;
@@ -945,9 +1127,9 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
                 if (!team_solve(n, f, v, scl, v, nullptr, 0, n, nullptr, nullptr, tr, red))
                     return false;
             }
-            // Alg. 1 lines 9-11: v <- v - <v, z_i> z_i for the previous members, in order
-            for (int64_t i = s0; i < j; ++i) {
-                const double* zi = p.Z + i * p.ldz;
+            // Alg. 1: v <- v - <v, z_i> z_i for the previous members, in order
+            for (int64_t i = 0; i < kk; ++i) {
+                const double* zi = Zc + i * ldz;
                 double h = 0.0;
                 for (int64_t r = t; r < n; r += B) h = fma(v[r], zi[r], h);
                 h = block_sum(h, red);
@@ -965,7 +1147,7 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
             if (!(as > 0.0) && !orth) {
                 // breakdown: restart from a fresh random vector
                 ++attempt;
-                const uint64_t key = start_key(p.seed, p.j0 + j, attempt);
+                const uint64_t key = start_key(sg.seed, sg.kj0 + jr.jl + kk, attempt);
                 for (int64_t r = t; r < n; r += B) v[r] = start_value(key, r);
                 __syncthreads();
                 ok = false;
@@ -1008,12 +1190,12 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
         }
         double sc = 1.0 / sqrt(ss);
         if (!orth && v[ai] < 0.0) sc = -sc;
-        double* dst = p.Z + (orth ? kk : j) * p.ldz;
+        double* dst = Zc + kk * ldz;
         for (int64_t r = t; r < n; r += B) dst[r] = v[r] * sc;
         __syncthreads();
         if (!orth && t == 0) {
             if (p.iters) p.iters[j] = conv ? its : -its;
-            if (!conv) atomicAdd((unsigned long long*)&w.ctr[kCtrInfo], 1ull);
+            if (!conv) count_nonconverged(w, j);
         }
         if (ld_volatile_i32(cx.err) != 0) return false;
     }
@@ -1118,19 +1300,23 @@ int32_t chain_grid(int32_t cap, int64_t n)
 
 cudaError_t launch_plan(const Problem& p, const Ws& w, int32_t max_team, cudaStream_t st)
 {
-    k_plan<<<1, kPlanThreads, 0, st>>>(p, w, max_team, 0);
+    if (p.nseg <= 0) return cudaSuccess;
+    k_plan_seg<<<(unsigned)p.nseg, kPlanThreads, 0, st>>>(p, w);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_plan_list<<<1, kPlanThreads, 0, st>>>(p, w, max_team);
     return cudaGetLastError();
 }
 
 cudaError_t launch_norm(const Problem& p, const Ws& w, cudaStream_t st)
 {
-    k_plan<<<1, kPlanThreads, 0, st>>>(p, w, 0, 1);
+    k_norm<<<1, kPlanThreads, 0, st>>>(p, w);
     return cudaGetLastError();
 }
 
-cudaError_t launch_orth_plan(int64_t m, const Ws& w, int32_t method, cudaStream_t st)
+cudaError_t launch_orth_plan(const Problem& p, const Ws& w, int32_t method, cudaStream_t st)
 {
-    k_orth_plan<<<1, 256, 0, st>>>(m, w, method);
+    k_orth_plan<<<1, 256, 0, st>>>(p, w, method);
     return cudaGetLastError();
 }
 
@@ -1152,18 +1338,38 @@ cudaError_t launch_lu(int64_t n, const double* d, const double* e, int64_t m, co
     return cudaGetLastError();
 }
 
+static int device_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+cudaError_t launch_lu_seg(const Problem& p, const Ws& w, cudaStream_t st)
+{
+    if (p.M <= 0) return cudaSuccess;
+    const int th = 32;  // one warp per block spreads the sequential factorizations over SMs
+    k_lu_seg<<<(unsigned)((p.M + th - 1) / th), th, 0, st>>>(p, w);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const unsigned rb = (unsigned)min(p.M, (int64_t)device_sms() * 8);
+    k_recip_seg<<<rb, 256, 0, st>>>(p, w);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_first(const Problem& p, const Ws& w, cudaStream_t st)
 {
-    if (p.m <= 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((p.m + kFirstWarps - 1) / kFirstWarps);
+    if (p.M <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((p.M + kFirstWarps - 1) / kFirstWarps);
     k_first<<<blocks, kFirstWarps * 32, 0, st>>>(p, w);
     return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const Problem& p, const Ws& w, cudaStream_t st)
 {
-    if (p.m <= 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((p.m + kFirstWarps - 1) / kFirstWarps);
+    if (p.M <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((p.M + kFirstWarps - 1) / kFirstWarps);
     k_finalize<<<blocks, kFirstWarps * 32, 0, st>>>(p, w);
     return cudaGetLastError();
 }

@@ -12,9 +12,6 @@
 #include "../../include/tinv.h"
 #include "tinv_internal.h"
 
-namespace tinvx {
-cudaError_t launch_norm(const Problem& p, const Ws& w, cudaStream_t st);
-}
 using namespace tinvx;
 
 namespace {
@@ -74,12 +71,13 @@ extern "C" int tinv_solve_noalloc(int64_t n, const double* d, const double* e, i
     if (m == 0) return 0;
     if (m > kNoAllocMaxShifts || m > kNoAllocMaxElems / n) return TINV_ENOTSUP;
     const int32_t P = 1;
-    const Layout L = make_layout(n, m, P, false);
+    const Dims D = single_dims(n, m, P);
+    const Layout L = make_layout(D, false);
     if (L.total > kNoAllocBytes) return TINV_ENOTSUP;
     void* base = nullptr;
     cudaError_t ce = noalloc_scratch(&base);
     if (ce != cudaSuccess) return code_of(ce);
-    const Ws w = bind_layout(base, L, n, m, P);
+    const Ws w = bind_layout(base, L, D);
     Problem p;
     memset(&p, 0, sizeof(p));
     p.n = n;

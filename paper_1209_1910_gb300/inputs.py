@@ -101,16 +101,22 @@ def batch_sizes(count: int = 512, seed: int = 2, lo: int = 64, hi: int = 4096):
     return out
 
 
-def batch(count: int = 512, seed: int = 2, lo: int = 64, hi: int = 4096):
-    """The batched workload: list of (d, e, w); even problems U[-1,1], odd glued W_21^+ (1e-10)."""
+def batch_matrices(count: int = 512, seed: int = 2, lo: int = 64, hi: int = 4096):
+    """The batched workload's matrices: list of (d, e); even problems U[-1,1], odd glued
+    W_21^+ (glue 1e-10)."""
     probs = []
     for p, n in enumerate(batch_sizes(count, seed, lo, hi)):
         if p % 2 == 1:
             d, e = glued_wilkinson(n // 21, 1e-10)
         else:
             d, e = uniform(n, seed=seed * 1000003 + p)
-        probs.append((d, e, eigenvalues(d, e)))
+        probs.append((d, e))
     return probs
+
+
+def batch(count: int = 512, seed: int = 2, lo: int = 64, hi: int = 4096):
+    """The batched workload with eigenvalues: list of (d, e, w)."""
+    return [(d, e, eigenvalues(d, e)) for d, e in batch_matrices(count, seed, lo, hi)]
 
 
 def request_stream(count: int, rate_hz: float, seed: int = 3, lo: int = 128, hi: int = 16384,

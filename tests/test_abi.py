@@ -76,6 +76,58 @@ def test_argument_checks_before_any_device_work(lib):
     assert z1[0] == 1.0
 
 
+def test_batch_argument_checks_before_any_device_work(lib):
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    ns = np.array([3, 2], dtype=np.int64)
+    off_de = np.array([0, 3], dtype=np.int64)
+    off_z = np.array([0, 9], dtype=np.int64)
+    d = np.zeros(5)
+    e = np.ones(5)
+    w = np.array([-1.0, 0.0, 1.0, -1.0, 1.0])
+    Z = np.zeros(13)
+    info = np.zeros(2, dtype=np.int64)
+    assert lib.tinv_batch(-1, None, None, None, None, None, None, None, None, None) == -1
+    assert lib.tinv_batch(0, None, None, None, None, None, None, None, None, None) == 0
+    assert lib.tinv_batch(2, None, P(off_de), P(off_z), P(d), P(e), P(w), P(Z), P(info), None) == -2
+    assert lib.tinv_batch(2, P(ns), None, P(off_z), P(d), P(e), P(w), P(Z), P(info), None) == -3
+    assert lib.tinv_batch(2, P(ns), P(off_de), None, P(d), P(e), P(w), P(Z), P(info), None) == -4
+    neg = np.array([3, -2], dtype=np.int64)
+    assert lib.tinv_batch(2, P(neg), P(off_de), P(off_z), P(d), P(e), P(w), P(Z), P(info), None) == -2
+    assert lib.tinv_batch(2, P(ns), P(off_de), P(off_z), None, P(e), P(w), P(Z), P(info), None) == -5
+    assert lib.tinv_batch(2, P(ns), P(off_de), P(off_z), P(d), None, P(w), P(Z), P(info), None) == -6
+    assert lib.tinv_batch(2, P(ns), P(off_de), P(off_z), P(d), P(e), None, P(Z), P(info), None) == -7
+    assert lib.tinv_batch(2, P(ns), P(off_de), P(off_z), P(d), P(e), P(w), None, P(info), None) == -8
+    o = binding.Opts()
+    lib.tinv_opts_default(ctypes.byref(o))
+    o.method = 3
+    assert lib.tinv_batch(2, P(ns), P(off_de), P(off_z), P(d), P(e), P(w), P(Z), P(info),
+                          ctypes.byref(o)) == -10
+    # values are checked per problem: non-ascending w of problem 1, non-finite d of problem 0
+    wbad = np.array([-1.0, 0.0, 1.0, 1.0, -1.0])
+    assert lib.tinv_batch(2, P(ns), P(off_de), P(off_z), P(d), P(e), P(wbad), P(Z), P(info), None) == -7
+    dbad = np.array([0.0, np.inf, 0.0, 0.0, 0.0])
+    assert lib.tinv_batch(2, P(ns), P(off_de), P(off_z), P(dbad), P(e), P(w), P(Z), P(info), None) == -5
+    # the workspace grows with the sum of n^2
+    small = lib.tinv_batch_workspace_size(2, P(ns), None)
+    big = lib.tinv_batch_workspace_size(2, P(np.array([300, 200], dtype=np.int64)), None)
+    assert 0 < small < big
+
+
+def test_bisect_argument_checks(lib):
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    d, e, w = np.zeros(3), np.ones(2), np.zeros(3)
+    assert lib.tinv_bisect(-1, None, None, None, None) == -1
+    assert lib.tinv_bisect(0, None, None, None, None) == 0
+    assert lib.tinv_bisect(3, None, P(e), P(w), None) == -2
+    assert lib.tinv_bisect(3, P(d), None, P(w), None) == -3
+    assert lib.tinv_bisect(3, P(d), P(e), None, None) == -4
+    assert lib.tinv_bisect(3, P(np.array([0.0, np.nan, 1.0])), P(e), P(w), None) == -2
+    ns = np.array([3], dtype=np.int64)
+    assert lib.tinv_bisect_batch(1, P(ns), None, P(d), P(e), P(w), None) == -3
+    big = np.zeros(70000, dtype=np.int64)
+    assert lib.tinv_bisect_batch(70000, P(big), P(big), P(d), P(e), P(w), None) == -106
+
+
 def test_binding_refuses_missing_library(tmp_path):
     saved = binding._lib
     try:
