@@ -43,6 +43,9 @@ WORKLOADS = {
     "batch512": "512 problems, n log-uniform [64,4096] (seed 2), even U[-1,1] d,e, odd glued "
                 "W21+ (glue 1e-10); all eigenvectors of every problem, one tinv_batch call",
 }
+WORKLOADS["serve"] = ("Poisson request stream (seed 3), n log-uniform [128,4096], 70% U[-1,1] / 30% "
+                      "glued W21+; eigenvalues computed by the server; offered at 0.5x, 0.9x and "
+                      "1.3x the saturated rate")
 # kernels one call enqueues: plan (2), LU (2), first sweep, cluster kernel, CWY finalize, status
 LAUNCHES = {"cwy": 8, "mgs": 7}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (vector and tensor alike), TFLOP/s
@@ -177,6 +180,9 @@ def reference_arm(args):
     if args.workload == "batch512":
         probs = inputs.batch_matrices()
         sample = lambda: cpu_sample_batch(args.method, probs)
+    elif args.workload == "serve":
+        probs = serve_requests()[0]
+        sample = lambda: cpu_sample_batch(args.method, probs, stride=16)
     else:
         d, e, w = inputs.workload(args.workload)
         sample = lambda: cpu_sample(args.workload, args.method, d, e, w)
@@ -394,10 +400,121 @@ def cpu_sample_batch(method, probs, stride=32):
                       "eigenvectors)" % (len(pick), stride, tot))
 
 
+def serve_requests(count=128, hi=4096, seed=3):
+    """The serving workload: (d, e) per request and unit-rate exponential arrival gaps."""
+    g = inputs.rng(seed)
+    reqs = []
+    for r in range(count):
+        n = int(round(math.exp(g.uniform(math.log(128), math.log(hi)))))
+        if g.uniform() < 0.3:
+            d, e = inputs.glued_wilkinson(max(1, round(n / 21)), 1e-10)
+        else:
+            d, e = inputs.uniform(n, seed=seed * 7919 + r)
+        reqs.append((d, e))
+    return reqs, g.exponential(1.0, count)
+
+
+def serve_arm(args, count=128, hi=4096):
+    """Request-queue server under Poisson load: saturated rate (all requests at once), then the
+    same requests offered at 0.5x, 0.9x and 1.3x that rate; p50/p99 latency per level.  Against
+    one-problem-at-a-time calls (tinv through the host API, one after another)."""
+    import torch
+
+    from paper_1209_1910_gb300 import binding, build
+
+    torch.cuda.set_device(0)
+    build.build()
+    binding.load()
+    reqs, gaps = serve_requests(count, hi)
+    M = sum(len(d) for d, _ in reqs)
+    outs = [np.zeros((len(d), len(d)), order="F") for d, _ in reqs]
+
+    def run_level(rate):
+        """Submit every request at its arrival time (rate None: all at once); returns stats."""
+        with binding.Server(method=args.method) as srv:
+            t0 = time.perf_counter()
+            tick = []
+            at = 0.0
+            for (d, e), gap, Z in zip(reqs, gaps, outs):
+                if rate:
+                    at += gap / rate
+                    dt = t0 + at - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                tick.append(srv.submit(d, e, None, out=Z))
+            infos = [srv.wait(t)[1] for t in tick]
+            el = time.perf_counter() - t0
+            st = srv.stats()
+        if any(i != 0 for i in infos):
+            raise RuntimeError("non-converged vectors in served requests")
+        st["wall_s"] = el
+        return st
+
+    run_level(None)  # warm-up (builds the memory pool and pinned staging)
+    sampler = ClockSampler(None)
+    sampler.start()
+    sat = run_level(None)
+    sat_rate = count / sat["wall_s"]
+    levels = []
+    for f in (0.5, 0.9, 1.3):
+        st = run_level(f * sat_rate)
+        levels.append({"load": f, "offered_per_s": f * sat_rate,
+                       "achieved_per_s": count / st["wall_s"], "p50_ms": st["p50_ms"],
+                       "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "waves": st["waves"],
+                       "mean_wave_problems": st["mean_wave_problems"],
+                       "max_inflight_seen": st["max_inflight_seen"]})
+    sampler.stop()
+    # accuracy of a sample of the served results (last level)
+    eps = float(np.finfo(np.float64).eps)
+    worst_r = worst_o = 0.0
+    for q in range(0, count, 16):
+        d, e = reqs[q]
+        Z = outs[q]
+        w = binding.bisect(d, e)
+        n = len(d)
+        R = d[:, None] * Z
+        R[:-1] += e[:, None] * Z[1:]
+        R[1:] += e[:, None] * Z[:-1]
+        R -= Z * w[None, :]
+        nrm = float(np.max(np.abs(d) + np.r_[0, np.abs(e)] + np.r_[np.abs(e), 0]))
+        worst_r = max(worst_r, float(np.abs(R).max()) / (n * eps * nrm))
+        worst_o = max(worst_o, float(np.abs(Z.T @ Z - np.eye(n)).max()) / (n * eps))
+    out = {
+        "metric": "served_problems_per_s", "value": sat_rate, "unit": "problems/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * sat["wall_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["serve"], "method": args.method, "requests": count,
+                   "eigenvectors": M, "parallelism": "single",
+                   "inputs": "host arrays submitted through tinv_submit (copies, bisection and "
+                             "inverse iteration inside the timed region)"},
+        "eigvecs_per_s": M / sat["wall_s"],
+        "saturated": {"p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"], "waves": sat["waves"],
+                      "mean_wave_problems": sat["mean_wave_problems"],
+                      "max_inflight_seen": sat["max_inflight_seen"]},
+        "levels": levels,
+        "check": {"sampled_requests": len(range(0, count, 16)), "worst_residual_ratio": worst_r,
+                  "worst_orth_ratio": worst_o},
+        "clocks": sampler.summary(),
+        "e2e": {"value": sat_rate, "unit": "problems/s",
+                "h2d_bytes_per_step": int(3 * M * 8), "d2h_bytes_per_step": int(sum(len(d) ** 2 for d, _ in reqs) * 8)},
+    }
+    if not args.no_compare:
+        t0 = time.perf_counter()
+        for (d, e), Z in zip(reqs, outs):
+            w = binding.bisect(d, e)
+            binding.tinv(d, e, w, method=args.method, out=Z)
+        el = time.perf_counter() - t0
+        out["compare"] = {"one_at_a_time": {"value": count / el, "unit": "problems/s",
+                                            "eigvecs_per_s": M / el}}
+    print(json.dumps(out), flush=True)
+
+
 def ours_arm(args):
     import torch
     if args.workload == "batch512":
         return batch_arm(args)
+    if args.workload == "serve":
+        return serve_arm(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -427,11 +544,12 @@ def ours_arm(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     head = binding.plan(d, e, w)[1]
     phase = np.zeros(4, dtype=np.float32)
+    counters = torch.zeros(4, dtype=torch.int64, device=dev)
 
     def step(method, with_phase):
         kw = {"phase_ms": phase.ctypes.data} if with_phase else {}
         binding.tinv_device(td, te, tw, Zt, method=method, workspace=ws, iters=iters, info=info,
-                            **kw)
+                            counters=counters.data_ptr(), **kw)
 
     for _ in range(args.warmup):
         step(args.method, False)
@@ -509,7 +627,9 @@ def ours_arm(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "inputs": "resident in HBM", "l2": "flushed by a 512 MiB write between steps"},
         "check": {"nonconverged": nonconv, "residual_ratio": res_ratio, "orth_ratio": orth_ratio,
-                  "sweeps": int(np.abs(it).sum())},
+                  "sweeps": int(np.abs(it).sum()),
+                  "sequential_back_substitutions": {"cluster_kernel": int(counters[0].item()),
+                                                    "first_sweep": int(counters[3].item())}},
         "roofline": roof,
         "gpu_launches": LAUNCHES[args.method] * args.steps,
         "clocks": sampler.summary(),

@@ -65,7 +65,12 @@ typedef struct tinv_opts {
     float* phase_ms;     /* optional HOST [4]: device milliseconds of the plan, LU, first-sweep */
                          /*   and cluster kernels, from CUDA events on the call's stream; the  */
                          /*   call then synchronizes that stream before returning             */
-    int32_t reserved[8];
+    int64_t* counters;   /* optional [4], host or device memory following device_ptrs: [0]   */
+                         /*   cluster-kernel solves whose back substitution was redone         */
+                         /*   sequentially (consistency check failed), [1] clusters with >= 2  */
+                         /*   members, [2] clusters given CTA teams, [3] as [0] for the first   */
+                         /*   sweeps                                                            */
+    int32_t reserved[6];
 } tinv_opts;
 
 /* Fill *o with the defaults: CWY, host pointers, seed 0, j0 0, automatic scheduling. */
@@ -199,10 +204,10 @@ int tinv_solve(int64_t n, const double* d, const double* e, int64_t m, const dou
  *   n, d, e, m, s, X, ldx, scale : as tinv_solve; d, e, s and X are DEVICE pointers of the
  *                                  current device.
  *   stream : cudaStream_t the work is enqueued on; the call returns without synchronizing.
- * Scratch: a fixed 16 MiB array in device memory, part of the library image (every GPU that
+ * Scratch: a fixed 20 MiB array in device memory, part of the library image (every GPU that
  * loads the library holds it until the process exits); it takes m * n <= 262144 and
- * m <= 131072 (for example 512 shifts of order 512).  Larger sizes return TINV_ENOTSUP.  The call performs no cudaMalloc
- * or cudaFree.  The first call on a device looks up the array's device address (with that
+ * m <= 131072 (for example 512 shifts of order 512).  Larger sizes return TINV_ENOTSUP.  The
+ * call performs no cudaMalloc or cudaFree.  The first call on a device looks up the array's device address (with that
  * device current) and caches it; make that first call before any stream capture.  All calls on
  * a device share the array and it keeps the last call's contents (each call writes every entry
  * it reads), so calls whose work overlaps on the GPU race: serialize them, e.g. on one stream.
@@ -220,6 +225,96 @@ int tinv_solve_noalloc(int64_t n, const double* d, const double* e, int64_t m, c
  */
 int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int64_t ldq,
               double* Y, double* T, const tinv_opts* o);
+
+/* ============================================================================================
+ * Serving: a request queue with continuous batching.  The paper has no counterpart; it serves
+ * many independent problems (each the problem of Sec. 2.1) arriving over time through the
+ * batched path.  A worker thread owns the GPU: whenever one of its max_inflight streams is free
+ * it admits the pending requests in arrival order, as far as max_slots and the memory budget
+ * allow, and runs them as one wave (bisection for requests without eigenvalues, then the batched
+ * inverse iteration of tinv_batch); waves on different streams overlap on the device (each
+ * wave's persistent cluster kernel holds its share of the SMs, wave_ctas), so a request that
+ * arrives while others are on the GPU starts as soon as a stream and memory free up.
+ * A problem's result does not depend on the other problems of its wave except through the CTA
+ * team a large cluster gets (rounding only); with max_team = 1 it is bit-identical to a tinv_ex
+ * call with the same seed.
+ * ============================================================================================ */
+typedef struct tinv_server tinv_server; /* opaque */
+
+typedef struct tinv_server_cfg {
+    int32_t max_slots;    /* most problems on the GPU at once (default 4096)                  */
+    int32_t max_inflight; /* most waves in flight at once, one stream each (default 2, <= 8)  */
+    double hbm_fraction;  /* share of the device memory free at creation that the server may  */
+                          /*   use for waves (default 0.5, < 0.95)                             */
+    int32_t method;       /* TINV_CWY (default) or TINV_MGS                                    */
+    int32_t max_team;     /* as tinv_opts.max_team                                             */
+    int32_t max_pending;  /* queued requests beyond which tinv_submit returns TINV_EAGAIN      */
+                          /*   (default 65536)                                                 */
+    int32_t device;       /* CUDA device ordinal                                               */
+    int32_t wave_ctas;    /* SMs (persistent CTAs) of one wave's cluster kernel; 0 = the SM    */
+                          /*   count / max_inflight, so concurrent waves split the GPU         */
+    int32_t reserved[7];
+} tinv_server_cfg;
+
+/* Request states (tinv_poll). */
+#define TINV_REQ_PENDING 0   /* queued, not yet on the GPU              */
+#define TINV_REQ_RUNNING 1   /* part of a wave on the GPU               */
+#define TINV_REQ_DONE 2      /* Z written; tinv_wait returns its info   */
+#define TINV_REQ_CANCELLED 3 /* cancelled; Z not written                */
+#define TINV_REQ_FAILED 4    /* a runtime error; tinv_wait returns it   */
+
+typedef struct tinv_stats {
+    uint64_t submitted, completed, cancelled, failed, rejected;
+    uint64_t waves;             /* waves launched                                         */
+    uint64_t max_inflight_seen; /* most waves that were in flight at the same time         */
+    uint64_t pending;           /* requests queued now                                    */
+    uint64_t inflight_waves;    /* waves in flight now                                    */
+    double mean_wave_problems;  /* problems per wave                                      */
+    double p50_ms, p99_ms, mean_ms; /* submit-to-completion latency of completed requests */
+    double problems_per_s;      /* completed requests / (last completion - first submit)  */
+    double eigvecs_per_s;       /* completed eigenvectors over the same span               */
+    double reserved[8];
+} tinv_stats;
+
+/* Fill *c with the defaults above. */
+void tinv_server_cfg_default(tinv_server_cfg* c);
+
+/* Start a server on cfg->device (NULL cfg = defaults): its streams and worker thread.  Returns
+ * 0, -1 for an invalid configuration, -2 for a NULL out, or TINV_ENODEV / TINV_ECUDA. */
+int tinv_server_create(const tinv_server_cfg* cfg, tinv_server** out);
+
+/* Queue the problem (n, d, e) for all n eigenvectors.  d, e and w are HOST arrays copied before
+ * the call returns; w (ascending) may be NULL, and the eigenvalues are then computed on the GPU
+ * by tinv_bisect's bisection.  Z is a caller-owned HOST n x n buffer (column-major, ld n) that
+ * must stay valid until the request is final; it is written only when the request completes.
+ * seed keys the start vectors as tinv_opts.seed (with j0 = 0).  *ticket receives the request's
+ * id.  Returns 0; -k for an invalid argument k (1-based); TINV_EAGAIN when max_pending requests
+ * are queued (retry later); TINV_ENOTSUP when the problem alone exceeds the memory budget;
+ * TINV_ECANCELED once the server is being destroyed. */
+int tinv_submit(tinv_server* srv, int64_t n, const double* d, const double* e, const double* w,
+                double* Z, uint64_t seed, uint64_t* ticket);
+
+/* Current state (TINV_REQ_*) of a request; -2 if the ticket is unknown (never issued, or
+ * already returned by tinv_wait). */
+int tinv_poll(tinv_server* srv, uint64_t ticket, int32_t* state);
+
+/* Wait until the request is final (timeout_ms < 0: without limit).  Returns 0 with *info = the
+ * number of vectors that did not converge (LAPACK convention), TINV_ECANCELED, the runtime error
+ * of a failed request, or TINV_ETIMEDOUT if the limit passed first (the request stays queued).
+ * A final state releases the ticket. */
+int tinv_wait(tinv_server* srv, uint64_t ticket, int32_t timeout_ms, int64_t* info);
+
+/* Cancel a request: a pending one is removed from the queue at once; a running one finishes on
+ * the GPU but its result is not written.  Returns 0, TINV_ECANCELED if it was already cancelled,
+ * 1 if it had already completed, -2 for an unknown ticket. */
+int tinv_cancel(tinv_server* srv, uint64_t ticket);
+
+/* Counters and latency percentiles so far. */
+int tinv_server_stats(tinv_server* srv, tinv_stats* st);
+
+/* Finish every queued and running request (drain), then stop the worker and free the server.
+ * No other call on srv may be in progress or follow. */
+int tinv_server_destroy(tinv_server* srv);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,9 @@ ERRORS = {-101: "ENOMEM", -102: "ECUDA", -103: "ETIMEDOUT", -104: "EAGAIN", -105
 EXPORTS = ["tinv_opts_default", "tinv_strerror", "tinv_version", "tinv", "tinv_ex",
            "tinv_workspace_size", "tinv_batch", "tinv_batch_workspace_size", "tinv_bisect",
            "tinv_bisect_batch", "tinv_plan",
-           "tinv_lu", "tinv_solve", "tinv_solve_noalloc", "tinv_orth"]
+           "tinv_lu", "tinv_solve", "tinv_solve_noalloc", "tinv_orth",
+           "tinv_server_cfg_default", "tinv_server_create", "tinv_submit", "tinv_poll",
+           "tinv_wait", "tinv_cancel", "tinv_server_stats", "tinv_server_destroy"]
 
 
 class TinvError(RuntimeError):
@@ -43,7 +45,8 @@ class Opts(ctypes.Structure):
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
                 ("iters", ctypes.c_void_p), ("info", ctypes.c_void_p),
                 ("max_team", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
-                ("phase_ms", ctypes.c_void_p), ("reserved", ctypes.c_int32 * 8)]
+                ("phase_ms", ctypes.c_void_p), ("counters", ctypes.c_void_p),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 def load(path: str | None = None) -> ctypes.CDLL:
@@ -74,6 +77,24 @@ def load(path: str | None = None) -> ctypes.CDLL:
             lib.tinv_lu.restype = ctypes.c_int
             lib.tinv_solve.argtypes = [I64, P, P, I64, P, P, I64, I32, ctypes.POINTER(Opts)]
             lib.tinv_solve.restype = ctypes.c_int
+            SP = ctypes.POINTER(ctypes.c_void_p)
+            lib.tinv_server_cfg_default.argtypes = [ctypes.POINTER(ServerCfg)]
+            lib.tinv_server_cfg_default.restype = None
+            lib.tinv_server_create.argtypes = [ctypes.POINTER(ServerCfg), SP]
+            lib.tinv_server_create.restype = ctypes.c_int
+            lib.tinv_submit.argtypes = [P, I64, P, P, P, P, ctypes.c_uint64,
+                                        ctypes.POINTER(ctypes.c_uint64)]
+            lib.tinv_submit.restype = ctypes.c_int
+            lib.tinv_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)]
+            lib.tinv_poll.restype = ctypes.c_int
+            lib.tinv_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+            lib.tinv_wait.restype = ctypes.c_int
+            lib.tinv_cancel.argtypes = [P, ctypes.c_uint64]
+            lib.tinv_cancel.restype = ctypes.c_int
+            lib.tinv_server_stats.argtypes = [P, ctypes.POINTER(Stats)]
+            lib.tinv_server_stats.restype = ctypes.c_int
+            lib.tinv_server_destroy.argtypes = [P]
+            lib.tinv_server_destroy.restype = ctypes.c_int
             lib.tinv_bisect.argtypes = [I64, P, P, P, ctypes.POINTER(Opts)]
             lib.tinv_bisect.restype = ctypes.c_int
             lib.tinv_bisect_batch.argtypes = [I64, P, P, P, P, P, ctypes.POINTER(Opts)]
@@ -293,3 +314,87 @@ def bisect_batch_device(ns, off_de, d, e, w, **kw):
     o = _opts(device=True, stream=_stream_of(d), **kw)
     return _check(load().tinv_bisect_batch(len(ns), _ptr(ns), _ptr(off_de), _ptr(d), _ptr(e),
                                            _ptr(w), ctypes.byref(o)), "tinv_bisect_batch")
+
+
+# ------------------------------------------------------------------------------------------
+# serving: request queue with continuous batching
+# ------------------------------------------------------------------------------------------
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("hbm_fraction", ctypes.c_double), ("method", ctypes.c_int32),
+                ("max_team", ctypes.c_int32), ("max_pending", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("wave_ctas", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in
+                ("submitted", "completed", "cancelled", "failed", "rejected", "waves",
+                 "max_inflight_seen", "pending", "inflight_waves")] + \
+               [(k, ctypes.c_double) for k in
+                ("mean_wave_problems", "p50_ms", "p99_ms", "mean_ms", "problems_per_s",
+                 "eigvecs_per_s")] + [("reserved", ctypes.c_double * 8)]
+
+
+REQ_STATES = {0: "pending", 1: "running", 2: "done", 3: "cancelled", 4: "failed"}
+
+
+class Server:
+    """Request-queue server (tinv_server_*): submit problems at any time, wait for results."""
+
+    def __init__(self, method="cwy", **cfg):
+        lib = load()
+        c = ServerCfg()
+        lib.tinv_server_cfg_default(ctypes.byref(c))
+        c.method = METHODS[method] if isinstance(method, str) else int(method)
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        h = ctypes.c_void_p()
+        _check(lib.tinv_server_create(ctypes.byref(c), ctypes.byref(h)), "tinv_server_create")
+        self._h = h
+        self._bufs = {}  # ticket -> (Z, inputs kept alive until final)
+
+    def submit(self, d, e, w=None, seed=0, out=None):
+        d, e = _f64(d), _f64(e)
+        w = None if w is None else _f64(w)
+        n = len(d)
+        Z = np.zeros((n, n), order="F") if out is None else out
+        t = ctypes.c_uint64()
+        rc = load().tinv_submit(self._h, n, _ptr(d), _ptr(e), _ptr(w), _ptr(Z), seed, ctypes.byref(t))
+        _check(rc, "tinv_submit")
+        self._bufs[t.value] = Z
+        return t.value
+
+    def poll(self, ticket):
+        s = ctypes.c_int32()
+        _check(load().tinv_poll(self._h, ticket, ctypes.byref(s)), "tinv_poll")
+        return REQ_STATES[s.value]
+
+    def wait(self, ticket, timeout_ms=-1):
+        """Returns (Z, info); raises TinvError for a cancelled or failed request or a timeout."""
+        info = ctypes.c_int64()
+        rc = load().tinv_wait(self._h, ticket, timeout_ms, ctypes.byref(info))
+        if rc == -103:  # timed out: the request stays queued
+            raise TinvError(rc, "tinv_wait")
+        Z = self._bufs.pop(ticket, None)
+        _check(rc, "tinv_wait")
+        return Z, info.value
+
+    def cancel(self, ticket):
+        return load().tinv_cancel(self._h, ticket)
+
+    def stats(self):
+        st = Stats()
+        _check(load().tinv_server_stats(self._h, ctypes.byref(st)), "tinv_server_stats")
+        return {k: getattr(st, k) for k, _ in Stats._fields_ if k != "reserved"}
+
+    def close(self):
+        if self._h:
+            load().tinv_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libtinv.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["tinv_kernels.cu", "tinv_api.cu", "tinv_noalloc.cu", "tinv_bisect.cu"]
+SOURCES = ["tinv_kernels.cu", "tinv_api.cu", "tinv_noalloc.cu", "tinv_bisect.cu",
+           "tinv_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

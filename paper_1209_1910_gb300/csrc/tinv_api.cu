@@ -32,7 +32,7 @@ Dims single_dims(int64_t n, int64_t m, int32_t P)
     return D;
 }
 
-Layout make_layout(const Dims& D, bool need_chain)
+Layout make_layout(const Dims& D, bool need_chain, bool need_rhs)
 {
     Layout L;
     memset(&L, 0, sizeof(L));
@@ -63,6 +63,7 @@ Layout make_layout(const Dims& D, bool need_chain)
     L.fpiv = take(ff);
     L.u0n = take(mm * sizeof(double));
     L.tolv = take(mm * sizeof(double));
+    if (need_rhs) L.rhs = take(ff * sizeof(double));
     if (need_chain) {
         L.Y = take(ff * sizeof(double));
         L.T = take((size_t)D.TT * sizeof(double));
@@ -106,6 +107,7 @@ Ws bind_layout(void* base, const Layout& L, const Dims& D)
     w.fpiv = (uint8_t*)(b + L.fpiv);
     w.u0n = (double*)(b + L.u0n);
     w.tolv = (double*)(b + L.tolv);
+    w.rhs = L.rhs ? (double*)(b + L.rhs) : nullptr;
     if (L.Y) {
         w.Y = (double*)(b + L.Y);
         w.T = (double*)(b + L.T);
@@ -184,6 +186,23 @@ __global__ void k_finish(const int64_t* ctr, int64_t* info)
     *info = err ? (int64_t)TINV_ETIMEDOUT : ctr[kCtrInfo];
 }
 
+// tinv_opts.counters from the counter block.
+__global__ void k_counters(const int64_t* ctr, int64_t* out)
+{
+    out[0] = ctr[kCtrFallback];
+    out[1] = ctr[kCtrNClust];
+    out[2] = ctr[kCtrNClust] - ctr[kCtrNQueue];
+    out[3] = ctr[kCtrFallbackFirst];
+}
+
+void host_counters(const int64_t* ctr, int64_t* out)
+{
+    out[0] = ctr[kCtrFallback];
+    out[1] = ctr[kCtrNClust];
+    out[2] = ctr[kCtrNClust] - ctr[kCtrNQueue];
+    out[3] = ctr[kCtrFallbackFirst];
+}
+
 // Per-problem results of a batch: the non-converged count, or the timeout code for all.
 __global__ void k_finish_batch(const int64_t* ctr, const int64_t* sinfo, int64_t nprob, int64_t* info)
 {
@@ -241,7 +260,8 @@ int enqueue_tinv(const Problem& p, void* ws, const Dims& D, int32_t max_team, cu
 // Sizes and problem table of a batch (host arrays n, off_de, off_z), with the argument checks
 // that need no array contents.  Returns 0 or the error code.
 int batch_tables(int64_t nprob, const int64_t* n, const int64_t* off_de, const int64_t* off_z,
-                 const tinv_opts& o, int32_t P, Dims* D, std::vector<Seg>* segs)
+                 const uint64_t* seeds, const tinv_opts& o, int32_t P, Dims* D,
+                 std::vector<Seg>* segs)
 {
     Dims d;
     memset(&d, 0, sizeof(d));
@@ -263,7 +283,7 @@ int batch_tables(int64_t nprob, const int64_t* n, const int64_t* off_de, const i
         g.j0 = d.M;
         g.foff = d.F;
         g.kj0 = o.j0;
-        g.seed = o.seed;
+        g.seed = seeds ? seeds[q] : o.seed;
         d.nmax = nq > d.nmax ? nq : d.nmax;
         d.M += nq;
         d.F += nq * nq;
@@ -276,6 +296,80 @@ int batch_tables(int64_t nprob, const int64_t* n, const int64_t* off_de, const i
 }
 
 }  // namespace
+
+namespace tinvx {
+
+int batch_enqueue_device(int64_t nprob, const int64_t* n, const int64_t* off_de,
+                         const int64_t* off_z, const uint64_t* seeds, const double* d,
+                         const double* e, const double* w, double* Z, int64_t* info,
+                         const tinv_opts& o)
+{
+    int64_t nmax = 1;
+    for (int64_t q = 0; q < nprob; ++q) nmax = n[q] > nmax ? n[q] : nmax;
+    const int32_t P = chain_grid(o.grid_ctas, nmax);
+    Dims D;
+    std::vector<Seg> segs;
+    int rc = batch_tables(nprob, n, off_de, off_z, seeds, o, P, &D, &segs);
+    if (rc != 0) return rc;
+    if (D.M == 0) return 0;
+    Problem p;
+    memset(&p, 0, sizeof(p));
+    p.n = D.nmax;
+    p.method = o.method;
+    p.seg_preset = 1;
+    p.nseg = nprob;
+    p.M = D.M;
+    p.d = d;
+    p.e = e;
+    p.w = w;
+    p.Z = Z;
+    p.iters = o.iters;
+    const Layout L = make_layout(D, true);
+    cudaStream_t st = (cudaStream_t)o.stream;
+    DevBuf own;
+    void* ws = o.workspace;
+    if (ws) {
+        if (o.workspace_bytes < L.total) return TINV_EWORKSPACE;
+    } else {
+        cudaError_t ce = own.alloc(L.total, st, true);
+        if (ce != cudaSuccess) return TINV_ENOMEM;
+        ws = own.p;
+    }
+    const Ws wsb = bind_layout(ws, L, D);
+    cudaError_t ce = cudaMemcpyAsync(wsb.segs, segs.data(), segs.size() * sizeof(Seg),
+                                     cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) return cuda_code(ce);
+    rc = enqueue_tinv(p, ws, D, o.max_team, st, o.phase_ms);
+    if (rc != 0) return rc;
+    if (info) {
+        k_finish_batch<<<(unsigned)((nprob + 255) / 256), 256, 0, st>>>(wsb.ctr, wsb.sinfo, nprob, info);
+        if (cudaGetLastError() != cudaSuccess) return TINV_ECUDA;
+    }
+    if (o.info) {
+        k_finish<<<1, 1, 0, st>>>(wsb.ctr, o.info);
+        if (cudaGetLastError() != cudaSuccess) return TINV_ECUDA;
+    }
+    if (o.counters) {
+        k_counters<<<1, 1, 0, st>>>(wsb.ctr, o.counters);
+        if (cudaGetLastError() != cudaSuccess) return TINV_ECUDA;
+    }
+    return 0;
+}
+
+size_t batch_workspace_bytes(int64_t nprob, const int64_t* n, const tinv_opts& o)
+{
+    int64_t nmax = 1;
+    for (int64_t q = 0; q < nprob; ++q) nmax = n[q] > nmax ? n[q] : nmax;
+    std::vector<int64_t> zeros((size_t)(nprob > 0 ? nprob : 1), 0);
+    Dims D;
+    std::vector<Seg> segs;
+    if (batch_tables(nprob, n, zeros.data(), zeros.data(), nullptr, o, chain_grid(o.grid_ctas, nmax),
+                     &D, &segs) != 0)
+        return 0;
+    return make_layout(D, true).total;
+}
+
+}  // namespace tinvx
 
 extern "C" {
 
@@ -372,9 +466,13 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
         }
         int rc = enqueue_tinv(p, ws, D, op.o.max_team, st, op.o.phase_ms);
         if (rc != 0) return rc;
+        const Ws wsb = bind_layout(ws, make_layout(D, true), D);
         if (op.o.info) {
-            const Ws wsb = bind_layout(ws, make_layout(D, true), D);
             k_finish<<<1, 1, 0, st>>>(wsb.ctr, op.o.info);
+            if (cudaGetLastError() != cudaSuccess) return TINV_ECUDA;
+        }
+        if (op.o.counters) {
+            k_counters<<<1, 1, 0, st>>>(wsb.ctr, op.o.counters);
             if (cudaGetLastError() != cudaSuccess) return TINV_ECUDA;
         }
         return 0;
@@ -432,6 +530,7 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
             rc = cuda_code(ce);
         }
         if (!rc) {
+            if (op.o.counters) host_counters(ctr, op.o.counters);
             if (ctr[kCtrErr]) {
                 rc = TINV_ETIMEDOUT;
             } else {
@@ -467,8 +566,8 @@ size_t tinv_batch_workspace_size(int64_t nprob, const int64_t* n, const tinv_opt
     std::vector<int64_t> zeros((size_t)(nprob > 0 ? nprob : 1), 0);
     Dims D;
     std::vector<Seg> segs;
-    if (batch_tables(nprob, n, zeros.data(), zeros.data(), op.o, chain_grid(op.o.grid_ctas, nmax),
-                     &D, &segs) != 0)
+    if (batch_tables(nprob, n, zeros.data(), zeros.data(), nullptr, op.o,
+                     chain_grid(op.o.grid_ctas, nmax), &D, &segs) != 0)
         return 0;
     return make_layout(D, true).total;
 }
@@ -497,10 +596,12 @@ int tinv_batch(int64_t nprob, const int64_t* n, const int64_t* off_de, const int
     if (e_len > 0 && !e) return -6;
     if (de_len > 0 && !w) return -7;
     if (z_len > 0 && !Z) return -8;
+    if (op.o.device_ptrs)
+        return batch_enqueue_device(nprob, n, off_de, off_z, nullptr, d, e, w, Z, info, op.o);
     const int32_t P = chain_grid(op.o.grid_ctas, nmax);
     Dims D;
     std::vector<Seg> segs;
-    int rc = batch_tables(nprob, n, off_de, off_z, op.o, P, &D, &segs);
+    int rc = batch_tables(nprob, n, off_de, off_z, nullptr, op.o, P, &D, &segs);
     if (rc != 0) return rc;
     if (D.M == 0) return 0;
 
@@ -512,39 +613,6 @@ int tinv_batch(int64_t nprob, const int64_t* n, const int64_t* off_de, const int
     p.nseg = nprob;
     p.M = D.M;
     const Layout L = make_layout(D, true);
-
-    if (op.o.device_ptrs) {
-        cudaStream_t st = (cudaStream_t)op.o.stream;
-        p.d = d;
-        p.e = e;
-        p.w = w;
-        p.Z = Z;
-        p.iters = op.o.iters;
-        DevBuf own;
-        void* ws = op.o.workspace;
-        if (ws) {
-            if (op.o.workspace_bytes < L.total) return TINV_EWORKSPACE;
-        } else {
-            cudaError_t ce = own.alloc(L.total, st, true);
-            if (ce != cudaSuccess) return TINV_ENOMEM;
-            ws = own.p;
-        }
-        const Ws wsb = bind_layout(ws, L, D);
-        cudaError_t ce = cudaMemcpyAsync(wsb.segs, segs.data(), segs.size() * sizeof(Seg),
-                                         cudaMemcpyHostToDevice, st);
-        if (ce != cudaSuccess) return cuda_code(ce);
-        rc = enqueue_tinv(p, ws, D, op.o.max_team, st, op.o.phase_ms);
-        if (rc != 0) return rc;
-        if (info) {
-            k_finish_batch<<<(unsigned)((nprob + 255) / 256), 256, 0, st>>>(wsb.ctr, wsb.sinfo, nprob, info);
-            if (cudaGetLastError() != cudaSuccess) return TINV_ECUDA;
-        }
-        if (op.o.info) {
-            k_finish<<<1, 1, 0, st>>>(wsb.ctr, op.o.info);
-            if (cudaGetLastError() != cudaSuccess) return TINV_ECUDA;
-        }
-        return 0;
-    }
 
     // ---- host pointers: validate values, copy in, run, copy out ----
     for (int64_t q = 0; q < nprob; ++q) {
@@ -606,6 +674,7 @@ int tinv_batch(int64_t nprob, const int64_t* n, const int64_t* off_de, const int
             rc = cuda_code(ce);
         }
         if (!rc) {
+            if (op.o.counters) host_counters(ctr, op.o.counters);
             if (ctr[kCtrErr]) {
                 rc = TINV_ETIMEDOUT;
                 if (info)
@@ -767,7 +836,7 @@ int tinv_solve(int64_t n, const double* d, const double* e, int64_t m, const dou
     if (m == 0) return 0;
     const int32_t P = chain_grid(op.o.grid_ctas, n);
     const Dims D = single_dims(n, m, P);
-    const Layout L = make_layout(D, false);
+    const Layout L = make_layout(D, false, true);
     Problem p;
     memset(&p, 0, sizeof(p));
     p.n = n;

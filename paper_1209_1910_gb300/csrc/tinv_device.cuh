@@ -132,6 +132,11 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p)
     return *(volatile const int*)p;
 }
 
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p)
+{
+    return *(volatile const unsigned long long*)p;
+}
+
 __device__ __forceinline__ void red_release_add_u32(uint32_t* p, uint32_t v)
 {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -174,25 +179,37 @@ __device__ __noinline__ bool team_sync(uint32_t* ctr, uint32_t& target, int G, i
 //
 // The P participating threads each own a contiguous chunk of L = ceil(n/P) rows.  Both
 // substitutions are linear recurrences with fixed coefficients, so each chunk first computes
-// its affine map (carry in -> carry out) in parallel, then one thread propagates the actual
-// boundary values across the P chunks in order (values, not composed maps, so nothing grows
-// beyond the true solution), then every chunk re-runs its rows from its true boundary value.
+// its affine map (carry in -> carry out) in parallel, then one thread propagates the boundary
+// values across the P chunks in order, then every chunk re-runs its rows from its boundary
+// value.  The forward maps have multipliers |l| <= 1.  The back-substitution maps grow by
+// 1/|u0| at every small pivot, and near-singular shifts of clustered spectra can put several
+// small pivots into one chunk; the boundary value folded from such a map then carries an error
+// far above the rounding of the true solution.  Every chunk therefore re-checks the rows next to
+// its lower boundary against the values its neighbour computed (row_consistent); if any row
+// fails, the solve is redone sequentially, so the result is always backward stable.
 //
 // Forward (P, L): carry c_k is the value at row k after the eliminations above it.
 //   no interchange at k: y_k = c_k,      c_{k+1} = b_{k+1} - l_k c_k
 //   interchange at k   : y_k = b_{k+1},  c_{k+1} = c_k - l_k b_{k+1}
-// Back (U): x_k = (y_k - u1_k x_{k+1} - u2_k x_{k+2}) * r_k with r_k = 1/u0_k (perturbed).
+// Back (U): x_k = a_k x_{k+1} + b_k x_{k+2} + r_k y_k with r_k = 1/u0_k (perturbed),
+//   a_k = -u1_k r_k and b_k = -u2_k r_k (the factors are stored in this form).
 //
 // `sh` holds >= 8P doubles visible to the group; `t` is the thread's rank in the group (ranks
 // >= P idle but must still call, because `sync` may be a CTA barrier).
 // ------------------------------------------------------------------------------------------
 struct Fac {
-    const double* __restrict__ l;
-    const double* __restrict__ u1;
-    const double* __restrict__ u2;
-    const double* __restrict__ r;
-    const uint8_t* __restrict__ piv;
+    const double* __restrict__ l;    // multipliers of L
+    const double* __restrict__ a;    // -u1 / u0 (perturbed u0)
+    const double* __restrict__ b;    // -u2 / u0
+    const double* __restrict__ r;    // 1 / u0
+    const uint8_t* __restrict__ piv; // row interchanges
 };
+
+// One row of the back substitution: x_k from x_{k+1}, x_{k+2} and the forward result y_k.
+__device__ __forceinline__ double back_row(double a, double b, double r, double y, double x1, double x2)
+{
+    return fma(a, x1, fma(b, x2, y * r));
+}
 
 struct WarpSync {
     __device__ __forceinline__ void operator()() const { __syncwarp(); }
@@ -201,8 +218,110 @@ struct CtaSync {
     __device__ __forceinline__ void operator()() const { __syncthreads(); }
 };
 
+// Sequential back substitution by the calling thread alone of rows [0, top), from the forward
+// results y and the already final x[top], x[top + 1] (rows at or past n count as 0).  The
+// forward elimination is stable in parallel (its multipliers are at most 1 in magnitude).  The
+// parallel solves fall back to it when their consistency check fails, from the lowest failing
+// chunk boundary: the rows below it passed every check, so they are already backward stable.
+__device__ __noinline__ void seq_back(int64_t n, const Fac& f, const double* y, double* x, int64_t top)
+{
+    double cur = top < n ? x[top] : 0.0, nxt = top + 1 < n ? x[top + 1] : 0.0;
+    int64_t k = top - 1;
+    for (; k >= 3; k -= 4) {
+        double a[4], b[4], z[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            a[i] = f.a[k - i];
+            b[i] = f.b[k - i];
+            z[i] = y[k - i] * f.r[k - i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const double v = fma(a[i], cur, fma(b[i], nxt, z[i]));
+            x[k - i] = v;
+            nxt = cur;
+            cur = v;
+        }
+    }
+    for (; k >= 0; --k) {
+        const double v = back_row(f.a[k], f.b[k], f.r[k], y[k], cur, nxt);
+        x[k] = v;
+        nxt = cur;
+        cur = v;
+    }
+}
+
+// The same by a whole CTA: warps 1.. stream the coefficients (a, b, r y) of the next block of
+// rows into shared memory while thread 0 runs the current block's recurrence from shared memory,
+// so the single thread pays only its two FMAs per row.  `sh` holds >= 6 kStageRows doubles.
+// Called by every thread of the CTA; y and x may be global or shared (not the same array).
+constexpr int kStageRows = 320;
+__device__ __noinline__ void staged_seq_back(int64_t n, const Fac& f, const double* y, double* x,
+                                             double* sh, int64_t top0)
+{
+    const int t = threadIdx.x, B = blockDim.x;
+    auto stage = [&](int64_t lo, int64_t hi, int buf, int t0, int nt) {
+        double* sa = sh + buf * 3 * kStageRows;
+        for (int64_t k = lo + (t - t0); k < hi; k += nt) {
+            const int64_t i = k - lo;
+            sa[i] = f.a[k];
+            sa[kStageRows + i] = f.b[k];
+            sa[2 * kStageRows + i] = y[k] * f.r[k];
+        }
+    };
+    int64_t top = top0;
+    int64_t lo = top > kStageRows ? top - kStageRows : 0;
+    stage(lo, top, 0, 0, B);
+    double cur = 0.0, nxt = 0.0;
+    if (t == 0) {
+        cur = top < n ? x[top] : 0.0;
+        nxt = top + 1 < n ? x[top + 1] : 0.0;
+    }
+    __syncthreads();
+    for (int blk = 0;; ++blk) {
+        const int64_t nlo = lo > kStageRows ? lo - kStageRows : 0;
+        if (t >= 32 && lo > 0) stage(nlo, lo, (blk + 1) & 1, 32, B - 32);
+        if (t == 0) {
+            const double* sa = sh + (blk & 1) * 3 * kStageRows;
+            for (int64_t k = top - 1; k >= lo; --k) {
+                const int64_t i = k - lo;
+                const double v = fma(sa[i], cur, fma(sa[kStageRows + i], nxt, sa[2 * kStageRows + i]));
+                x[k] = v;
+                nxt = cur;
+                cur = v;
+            }
+        }
+        __syncthreads();
+        if (lo == 0) break;
+        top = lo;
+        lo = nlo;
+    }
+}
+
+// Backward-stability test of one row of the back substitution: x_k recomputed from the stored
+// neighbours x_{k+1}, x_{k+2} (and the row's right-hand side y) agrees with the stored x_k to a
+// few roundings of the row's terms.  Rows inside a chunk pass by construction; a row next to a
+// chunk boundary fails when the boundary values its chunk assumed (from the folded chunk maps,
+// which lose accuracy when the maps grow across several tiny pivots) are not the values the
+// neighbouring chunk computed.  A NaN or infinity fails.
+#ifndef TINV_SOLVE_TOL
+#define TINV_SOLVE_TOL 1024.0
+#endif
+constexpr double kSolveTol = TINV_SOLVE_TOL;  // accepted backward error of a row, in eps
+
+__device__ __forceinline__ bool row_consistent(double a, double b, double r, double y, double x1,
+                                               double x2, double xk)
+{
+    const double v = back_row(a, b, r, y, x1, x2);
+    const double scale = fabs(y * r) + fabs(a * x1) + fabs(b * x2);
+    return fabs(v - xk) <= kSolveTol * kEps * scale;
+}
+
+// x (n rows) solved in place by P chunks; `ysave` (n doubles) receives the forward results for
+// the sequential fallback.  Returns true when the fallback ran.
 template <class Sync>
-__device__ void chunk_solve(int64_t n, const Fac& f, double* x, double* sh, int t, int P, Sync sync)
+__device__ bool chunk_solve(int64_t n, const Fac& f, double* x, double* ysave, double* sh, int t,
+                            int P, Sync sync)
 {
     const int64_t L = (n + P - 1) / P;
     const int64_t lo = (int64_t)t * L;
@@ -269,10 +388,10 @@ __device__ void chunk_solve(int64_t n, const Fac& f, double* x, double* sh, int 
     double p0 = 0.0, p1 = 0.0, h10 = 1.0, h11 = 0.0, h20 = 0.0, h21 = 1.0;
     if (act) {
         for (int64_t k = hi - 1; k >= lo; --k) {
-            const double rk = f.r[k], a = f.u1[k], b = f.u2[k], y = x[k];
-            const double vp = fma(-b, p1, fma(-a, p0, y)) * rk;
-            const double v1 = fma(-b, h11, -a * h10) * rk;
-            const double v2 = fma(-b, h21, -a * h20) * rk;
+            const double a = f.a[k], b = f.b[k], y = x[k];
+            const double vp = back_row(a, b, f.r[k], y, p0, p1);
+            const double v1 = fma(a, h10, b * h11);
+            const double v2 = fma(a, h20, b * h21);
             p1 = p0;
             p0 = vp;
             h11 = h10;
@@ -304,16 +423,38 @@ __device__ void chunk_solve(int64_t n, const Fac& f, double* x, double* sh, int 
     }
     sync();
     // ---- back: phase 3 ----
+    double ysv0 = 0.0, ysv1 = 0.0;  // forward results of rows hi-1, hi-2
     if (act) {
         double cur = ent[2 * t], nxt = ent[2 * t + 1];
+        ysv0 = x[hi - 1];
+        if (hi - 2 >= lo) ysv1 = x[hi - 2];
         for (int64_t k = hi - 1; k >= lo; --k) {
-            const double v = fma(-f.u2[k], nxt, fma(-f.u1[k], cur, x[k])) * f.r[k];
+            const double y = x[k];
+            ysave[k] = y;
+            const double v = back_row(f.a[k], f.b[k], f.r[k], y, cur, nxt);
             x[k] = v;
             nxt = cur;
             cur = v;
         }
     }
     sync();
+    // ---- rows next to the chunk boundaries against the neighbours' values ----
+    bool bad = false;
+    if (act && hi < n) {
+        const double x1 = x[hi], x2 = (hi + 1 < n) ? x[hi + 1] : 0.0;
+        bad = !row_consistent(f.a[hi - 1], f.b[hi - 1], f.r[hi - 1], ysv0, x1, x2, x[hi - 1]);
+        if (hi - 2 >= lo)
+            bad = bad || !row_consistent(f.a[hi - 2], f.b[hi - 2], f.r[hi - 2], ysv1, x[hi - 1], x1,
+                                         x[hi - 2]);
+    }
+    const bool fallback = __any_sync(0xffffffffu, bad);
+    if (fallback) {
+        // restart below the lowest failing boundary (the largest failing hi)
+        const int top = __reduce_max_sync(0xffffffffu, bad ? (int)hi : 0);
+        if (t == 0) seq_back(n, f, ysave, x, top);
+        sync();
+    }
+    return fallback;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -328,6 +469,8 @@ __device__ void chunk_solve(int64_t n, const Fac& f, double* x, double* sh, int 
 // (back) as actual values, then re-runs its rows from the true boundary values.
 //   bsrc  : right-hand side (global, or shared when G == 1); the solve reads bsrc[k] * fac for
 //           its rows and the first row of the next CTA.
+//   ysave : n doubles (global when G > 1, not vsm) receiving the forward results of the own rows,
+//           which the sequential fallback reads for all rows.
 //   vsm   : row-indexed scratch of the CTA (n slots); on return vsm[r0..r1) = x.
 //   vout  : if not null, also receives x[r0..r1) (global, for other CTAs of the team).
 //   pubf, pubb : team buffers of 2 and 6 doubles per rank for the published maps.
@@ -338,6 +481,9 @@ struct TeamRef {
     uint32_t* target;
     int G, rank;
     int* err;
+    unsigned long long* flag;  // team word for the consistency verdict (G > 1)
+    unsigned long long stamp;  // increasing per solve of the team
+    unsigned long long* nfall; // counter of sequential fallbacks (may be null)
 };
 
 __device__ __forceinline__ void compose2(double& m00, double& m01, double& m10, double& m11,
@@ -356,9 +502,10 @@ __device__ __forceinline__ void compose2(double& m00, double& m01, double& m10, 
     f1 = b1;
 }
 
-__device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* bsrc, double fac, double* vsm,
-                           double* vout, int64_t r0, int64_t r1, double* pubf, double* pubb,
-                           TeamRef tr, double* sh)
+__device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* bsrc, double fac,
+                                        double* vsm, double* vout, double* ysave, int64_t r0,
+                                        int64_t r1, double* pubf, double* pubb, TeamRef tr,
+                                        double* sh)
 {
     constexpr int NW = 4, PT = 32 * NW;
     const int t = threadIdx.x, B = blockDim.x, lane = t & 31, wid = t >> 5;
@@ -471,10 +618,10 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
     if (act) {
         double p0 = 0.0, p1 = 0.0, h10 = 1.0, h11 = 0.0, h20 = 0.0, h21 = 1.0;
         for (int64_t k = hi - 1; k >= lo; --k) {
-            const double rk = f.r[k], a = f.u1[k], b = f.u2[k], y = vsm[k];
-            const double vp = fma(-b, p1, fma(-a, p0, y)) * rk;
-            const double v1 = fma(-b, h11, -a * h10) * rk;
-            const double v2 = fma(-b, h21, -a * h20) * rk;
+            const double a = f.a[k], b = f.b[k], y = vsm[k];
+            const double vp = back_row(a, b, f.r[k], y, p0, p1);
+            const double v1 = fma(a, h10, b * h11);
+            const double v2 = fma(a, h20, b * h21);
             p1 = p0;
             p0 = vp;
             h11 = h10;
@@ -573,12 +720,17 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
         }
     }
     __syncthreads();
+    double ysv0 = 0.0, ysv1 = 0.0;  // forward results of rows hi-1, hi-2
     if (act) {
         const double w0 = sh[64 + 2 * wid], w1 = sh[64 + 2 * wid + 1];
         double cur = fma(e00, w0, fma(e01, w1, g0));
         double nxt = fma(e10, w0, fma(e11, w1, g1));
+        ysv0 = vsm[hi - 1];
+        if (hi - 2 >= lo) ysv1 = vsm[hi - 2];
         for (int64_t k = hi - 1; k >= lo; --k) {
-            const double v = fma(-f.u2[k], nxt, fma(-f.u1[k], cur, vsm[k])) * f.r[k];
+            const double y = vsm[k];
+            ysave[k] = y;
+            const double v = back_row(f.a[k], f.b[k], f.r[k], y, cur, nxt);
             vsm[k] = v;
             if (vout) vout[k] = v;
             nxt = cur;
@@ -586,6 +738,50 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
         }
     }
     __syncthreads();
+
+    // ---------------- consistency at the chunk boundaries ----------------
+    // The rows below a CTA's last chunk belong to the next CTA: read them once all are written.
+    if (tr.G > 1 && !team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+    bool bad = false;
+    if (act && hi < n) {
+        const double x1 = (hi < r1) ? vsm[hi] : __ldcg(&vout[hi]);
+        const double x2 = (hi + 1 >= n) ? 0.0 : ((hi + 1 < r1) ? vsm[hi + 1] : __ldcg(&vout[hi + 1]));
+        bad = !row_consistent(f.a[hi - 1], f.b[hi - 1], f.r[hi - 1], ysv0, x1, x2, vsm[hi - 1]);
+        if (hi - 2 >= lo)
+            bad = bad || !row_consistent(f.a[hi - 2], f.b[hi - 2], f.r[hi - 2], ysv1, vsm[hi - 1],
+                                         x1, vsm[hi - 2]);
+    }
+    // verdict word: the solve's stamp above the largest failing boundary row (the restart point)
+    __shared__ unsigned long long s_top;
+    if (t == 0) s_top = 0ull;
+    __syncthreads();
+    if (bad) atomicMax(&s_top, (unsigned long long)hi);
+    bool fallback = __syncthreads_or(bad) != 0;
+    int64_t top = (int64_t)s_top;
+    if (tr.G > 1) {
+        if (fallback && t == 0) atomicMax(tr.flag, (tr.stamp << 32) | s_top);
+        if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+        const unsigned long long v = ld_volatile_u64(tr.flag);
+        fallback = (v >> 32) == tr.stamp;
+        top = (int64_t)(v & 0xffffffffull);
+    }
+    if (fallback) {
+        // the back substitution again, sequentially, by the first CTA of the team, for the rows
+        // above the restart point (ysave holds the forward results of all rows)
+        if (tr.rank == 0) {
+            staged_seq_back(n, f, ysave, tr.G > 1 ? vout : vsm, sh, top);
+            if (t == 0 && tr.nfall) atomicAdd(tr.nfall, 1ull);
+        }
+        if (tr.G > 1) {
+            if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+            for (int64_t k = r0 + t; k < r1; k += B) vsm[k] = __ldcg(&vout[k]);
+        } else {
+            __syncthreads();
+            if (vout)
+                for (int64_t k = r0 + t; k < r1; k += B) vout[k] = vsm[k];
+        }
+        __syncthreads();
+    }
     return true;
 }
 

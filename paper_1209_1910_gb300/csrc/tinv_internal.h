@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/tinv.h"
+
 namespace tinvx {
 
 constexpr int kFirstWarps = 8;      // warps per CTA of the warp-per-eigenvalue solve kernel
@@ -52,7 +54,7 @@ Dims single_dims(int64_t n, int64_t m, int32_t P);
 struct Layout {
     size_t segs, segj, sinfo;
     size_t scal, wp, head, clstart, clsize, cltoff, sched, queue, ctr, bar;
-    size_t fl, fu1, fu2, fr, fpiv, u0n, tolv;
+    size_t fl, fu1, fu2, fr, fpiv, u0n, tolv, rhs;
     size_t Y, T, partS, partG, partScal, vecS, vecX, vecR, qbuf, vbuf, tpub, gvec;
     size_t total;
 };
@@ -65,6 +67,8 @@ enum CtrIdx : int {
     kCtrErr = 3,     // error word
     kCtrInfo = 4,    // non-converged vectors
     kCtrTSize = 5,   // entries of T used
+    kCtrFallback = 6,       // cluster-kernel solves whose back substitution was redone sequentially
+    kCtrFallbackFirst = 7,  // the same in the first-sweep kernel
     kCtrCount = 8
 };
 
@@ -104,6 +108,8 @@ struct Ws {
     uint8_t* fpiv;    // [F]
     double* u0n;      // [M]   |u_nn| before perturbation
     double* tolv;     // [M]   tiny-pivot threshold eps max|U| per shift
+    double* rhs;      // [F]   right-hand sides kept for the sequential fallback (stand-alone
+                      //       solve; the cluster path keeps them in Y)
     double* Y;        // [F]
     double* T;        // [TT]
     double *partS, *partG;  // [P*nmax]
@@ -116,7 +122,8 @@ struct Ws {
     int32_t use_smem; // per-CTA vectors live in shared memory
 };
 
-Layout make_layout(const Dims& D, bool need_chain);
+// need_chain: the cluster kernel's arrays; need_rhs: a copy of the right-hand sides (tinv_solve).
+Layout make_layout(const Dims& D, bool need_chain, bool need_rhs = false);
 Ws bind_layout(void* base, const Layout& L, const Dims& D);
 
 // Kernel launchers (tinv_kernels.cu).  All enqueue on `st` and return cudaGetLastError().
@@ -125,9 +132,9 @@ cudaError_t launch_plan(const Problem& p, const Ws& w, int32_t max_team, cudaStr
 cudaError_t launch_norm(const Problem& p, const Ws& w, cudaStream_t st);
 // LU of every eigenvalue's shifted matrix (problem table, perturbed shifts wp), solve-ready.
 cudaError_t launch_lu_seg(const Problem& p, const Ws& w, cudaStream_t st);
-// LU of T - shift_j I for all j.  With tolv != null the diagonal is turned into perturbed
-// reciprocals r = 1/u0 (solve-ready) and tolv[j] receives the tiny-pivot threshold; with
-// tolv == null u0 is left as is.
+// LU of T - shift_j I for all j.  With tolv != null the factors are made solve-ready in place
+// (u0 -> r = 1/u0 with tiny pivots perturbed, u1 -> -u1 r, u2 -> -u2 r) and tolv[j] receives
+// the tiny-pivot threshold; with tolv == null the factors are left as computed.
 cudaError_t launch_lu(int64_t n, const double* d, const double* e, int64_t m, const double* shift,
                       double* l, double* u0_or_r, double* u1, double* u2, uint8_t* piv,
                       double* u0n, double* tolv, cudaStream_t st);
@@ -147,5 +154,19 @@ int32_t chain_grid(int32_t cap, int64_t n);
 int32_t chain_threads(int64_t n);
 size_t chain_smem_bytes(int64_t n, bool use_smem);
 bool chain_use_smem(int64_t n);
+
+// Batched path on device arrays (tinv_api.cu): the device-pointer form of tinv_batch, with an
+// optional per-problem seed array (host; null = o.seed for every problem).  Enqueues on
+// o.stream; allocates its workspace stream-ordered unless o.workspace is given.
+int batch_enqueue_device(int64_t nprob, const int64_t* n, const int64_t* off_de,
+                         const int64_t* off_z, const uint64_t* seeds, const double* d,
+                         const double* e, const double* w, double* Z, int64_t* info,
+                         const tinv_opts& o);
+size_t batch_workspace_bytes(int64_t nprob, const int64_t* n, const tinv_opts& o);
+
+// Sturm bisection of nprob problems (tinv_bisect.cu); ns/offs are DEVICE arrays, or null for
+// one problem of order n1 at offset 0.
+cudaError_t launch_bisect(int64_t nprob, const int64_t* ns, const int64_t* offs, int64_t n1,
+                          int64_t nmax, const double* d, const double* e, double* w, cudaStream_t st);
 
 }  // namespace tinvx

@@ -133,8 +133,12 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_seg(Problem p, Ws w)
             for (int c = 0; c < kCtrCount; ++c) w.ctr[c] = 0;
         }
     }
-    if (sidx == 0)
+    if (sidx == 0) {
         for (int b = t; b < w.P; b += B) w.bar[b] = 0u;
+        if (w.partScal)  // the teams' consistency-verdict words (slot 15 of each block)
+            for (int b = t; b < w.P; b += B)
+                ((unsigned long long*)w.partScal)[(size_t)b * kScalTeam + 15] = 0ull;
+    }
     for (int64_t jl = t; jl < m; jl += B) w.segj[g.j0 + jl] = sidx;
     __syncthreads();
     // without any tight pair w' = w; otherwise one thread scans
@@ -481,26 +485,36 @@ __global__ void k_lu_seg(Problem p, Ws w)
            w.fu2 + base, w.fpiv + base, w.u0n + j, w.tolv + j);
 }
 
-// r = 1/u0 with tiny pivots |u0| < tol replaced by sign(u0) tol (sign(0) = +), in place.
-__device__ __forceinline__ void recip_row(int64_t n, double* __restrict__ row, double tol)
+// Solve-ready back-substitution factors, in place: r = 1/u0 with tiny pivots |u0| < tol
+// replaced by sign(u0) tol (sign(0) = +), a = -u1 r, b = -u2 r.
+__device__ __forceinline__ void recip_row(int64_t n, double* __restrict__ u0, double* __restrict__ u1,
+                                          double* __restrict__ u2, double tol)
 {
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
-        double a = row[k];
+        double a = u0[k];
         if (fabs(a) < tol) a = (a >= 0.0) ? tol : -tol;
-        row[k] = __drcp_rn(a);
+        const double r = __drcp_rn(a);
+        u0[k] = r;
+        u1[k] = -u1[k] * r;
+        u2[k] = -u2[k] * r;
     }
 }
 
-__global__ void k_recip(int64_t n, int64_t m, double* __restrict__ U0R, const double* __restrict__ tolv)
+__global__ void k_recip(int64_t n, int64_t m, double* __restrict__ U0R, double* __restrict__ U1,
+                        double* __restrict__ U2, const double* __restrict__ tolv)
 {
-    for (int64_t j = blockIdx.x; j < m; j += gridDim.x) recip_row(n, U0R + (size_t)j * (size_t)n, tolv[j]);
+    for (int64_t j = blockIdx.x; j < m; j += gridDim.x) {
+        const size_t o = (size_t)j * (size_t)n;
+        recip_row(n, U0R + o, U1 + o, U2 + o, tolv[j]);
+    }
 }
 
 __global__ void k_recip_seg(Problem p, Ws w)
 {
     for (int64_t j = blockIdx.x; j < p.M; j += gridDim.x) {
         const Seg* g = w.segs + w.segj[j];
-        recip_row(g->n, w.fr + (size_t)(g->foff + (j - g->j0) * g->n), w.tolv[j]);
+        const size_t o = (size_t)(g->foff + (j - g->j0) * g->n);
+        recip_row(g->n, w.fr + o, w.fu1 + o, w.fu2 + o, w.tolv[j]);
     }
 }
 
@@ -512,8 +526,8 @@ __device__ __forceinline__ Fac fac_at(const Ws& w, size_t base)
 {
     Fac f;
     f.l = w.fl + base;
-    f.u1 = w.fu1 + base;
-    f.u2 = w.fu2 + base;
+    f.a = w.fu1 + base;  // -u1/u0 after k_recip
+    f.b = w.fu2 + base;  // -u2/u0
     f.r = w.fr + base;
     f.piv = w.fpiv + base;
     return f;
@@ -585,10 +599,12 @@ __global__ void __launch_bounds__(kFirstWarps * 32) k_first(Problem p, Ws w)
     const int maxits = is_head ? kMaxIts : 1;
     int nrmchk = 0, its = 0;
     bool conv = false;
+    double* ysave = w.Y + jr.off;  // free until the cluster kernel writes this Y column
     while (its < maxits) {
         ++its;
         warp_scale(n, x, onenrm, u0n, lane);
-        chunk_solve(n, f, x, sh, lane, 32, WarpSync());
+        if (chunk_solve(n, f, x, ysave, sh, lane, 32, WarpSync()) && lane == 0)
+            atomicAdd((unsigned long long*)&w.ctr[kCtrFallbackFirst], 1ull);
         if (!is_head) break;
         double mx = 0.0;
         for (int64_t i = lane; i < n; i += 32) mx = fmax(mx, fabs(x[i]));
@@ -660,7 +676,8 @@ __global__ void __launch_bounds__(kFirstWarps * 32) k_solve_rhs(int64_t n, int64
     if (j >= m) return;
     double* x = X + j * ldx;
     if (scale) warp_scale(n, x, w.scal[0], w.u0n[j], lane);
-    chunk_solve(n, fac_of(w, j, n), x, sh_all[warp], lane, 32, WarpSync());
+    chunk_solve(n, fac_of(w, j, n), x, w.rhs + (size_t)j * (size_t)n, sh_all[warp], lane, 32,
+                WarpSync());
 }
 
 // ==========================================================================================
@@ -708,6 +725,7 @@ struct ChainCtx {
     double* s1;    // [n] staging vector (shared or global)
     double* red;   // [2048] reduction / solve scratch (shared)
     int* err;
+    unsigned long long nsolve;  // solves so far (the team's stamps: equal in all its CTAs)
     Prof prof;
 };
 
@@ -905,8 +923,10 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             const double* vsrc = orth ? cx.V + kk * cx.ldv : (its == 1 ? Zc + kk * ldz : vbuf);
             if (!orth && its > 1) {
                 PROF_MARK(cx.prof, kPhLoad);
-                TeamRef tr{tm.bar, &tm.target, G, rank, cx.err};
-                if (!team_solve(n, f, qbuf, fac_next, vsm, vbuf, ra0, ra1, pubf, pubb, tr, red))
+                TeamRef tr{tm.bar, &tm.target, G, rank, cx.err,
+                           (unsigned long long*)(scal_t + 15), ++cx.nsolve,
+                           (unsigned long long*)&w.ctr[kCtrFallback]};
+                if (!team_solve(n, f, qbuf, fac_next, vsm, vbuf, vecS, ra0, ra1, pubf, pubb, tr, red))
                     return false;
                 PROF_MARK(cx.prof, kPhSolve);
             } else {
@@ -1123,8 +1143,9 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
                 __syncthreads();
                 const double scl = s_scl;
                 uint32_t tgt = 0;
-                TeamRef tr{nullptr, &tgt, 1, 0, cx.err};
-                if (!team_solve(n, f, v, scl, v, nullptr, 0, n, nullptr, nullptr, tr, red))
+                TeamRef tr{nullptr, &tgt, 1, 0, cx.err, nullptr, 0ull,
+                           (unsigned long long*)&w.ctr[kCtrFallback]};
+                if (!team_solve(n, f, v, scl, v, nullptr, cx.s1, 0, n, nullptr, nullptr, tr, red))
                     return false;
             }
             // Alg. 1: v <- v - <v, z_i> z_i for the previous members, in order
@@ -1224,6 +1245,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t
         cx.s1 = cx.vsm + n;
     }
     cx.err = (int*)&w.ctr[kCtrErr];
+    cx.nsolve = 0;
     __shared__ int s_c;
 #ifdef TINV_PHASE_PROFILE
     for (int i = 0; i < kPhN; ++i) cx.prof.c[i] = 0;
@@ -1334,7 +1356,7 @@ cudaError_t launch_lu(int64_t n, const double* d, const double* e, int64_t m, co
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const unsigned rb = (unsigned)min(m, (int64_t)(sms > 0 ? sms : 1) * 8);
-    k_recip<<<rb, 256, 0, st>>>(n, m, u0_or_r, tolv);
+    k_recip<<<rb, 256, 0, st>>>(n, m, u0_or_r, u1, u2, tolv);
     return cudaGetLastError();
 }
 

@@ -18,9 +18,9 @@ namespace {
 
 constexpr int64_t kNoAllocMaxElems = 262144;  // largest m * n accepted (e.g. 512 x 512)
 constexpr int64_t kNoAllocMaxShifts = 131072; // largest m accepted
-// 16 MiB holds the scratch layout of every (n, m) within both limits (largest: n = 2,
-// m = 131072, about 14.3 MiB)
-constexpr size_t kNoAllocBytes = 16u << 20;
+// 20 MiB holds the scratch layout of every (n, m) within both limits (largest: n = 2,
+// m = 131072, about 16.8 MiB, of which the kept right-hand sides are 2 MiB)
+constexpr size_t kNoAllocBytes = 20u << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -72,7 +72,7 @@ extern "C" int tinv_solve_noalloc(int64_t n, const double* d, const double* e, i
     if (m > kNoAllocMaxShifts || m > kNoAllocMaxElems / n) return TINV_ENOTSUP;
     const int32_t P = 1;
     const Dims D = single_dims(n, m, P);
-    const Layout L = make_layout(D, false);
+    const Layout L = make_layout(D, false, true);
     if (L.total > kNoAllocBytes) return TINV_ENOTSUP;
     void* base = nullptr;
     cudaError_t ce = noalloc_scratch(&base);

@@ -128,6 +128,28 @@ def test_bisect_argument_checks(lib):
     assert lib.tinv_bisect_batch(70000, P(big), P(big), P(d), P(e), P(w), None) == -106
 
 
+def test_server_config_and_null_checks(lib):
+    c = binding.ServerCfg()
+    lib.tinv_server_cfg_default(ctypes.byref(c))
+    assert (c.max_slots, c.max_inflight, c.hbm_fraction, c.method, c.max_pending) == \
+        (4096, 2, 0.5, binding.TINV_CWY, 65536)
+    assert ctypes.sizeof(binding.ServerCfg) == 64 and ctypes.sizeof(binding.Stats) == 184
+    t = ctypes.c_uint64()
+    d = np.zeros(3)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    assert lib.tinv_submit(None, 3, P(d), P(d), None, P(d), 0, ctypes.byref(t)) == -1
+    assert lib.tinv_poll(None, 1, None) == -1
+    assert lib.tinv_wait(None, 1, 0, None) == -1
+    assert lib.tinv_cancel(None, 1) == -1
+    assert lib.tinv_server_destroy(None) == -1
+    h = ctypes.c_void_p()
+    assert lib.tinv_server_create(None, None) == -2
+    bad = binding.ServerCfg()
+    lib.tinv_server_cfg_default(ctypes.byref(bad))
+    bad.hbm_fraction = 0.99
+    assert lib.tinv_server_create(ctypes.byref(bad), ctypes.byref(h)) == -1
+
+
 def test_binding_refuses_missing_library(tmp_path):
     saved = binding._lib
     try:

@@ -226,6 +226,27 @@ def test_tinv_glued4200_full_size(gpu, orc, method):
         assert sin_angle(Zo, Z[:, s:t]) <= 1e-10
 
 
+def test_tinv_glued3108_near_singular_solves(gpu, orc):
+    # 148 copies of W_21^+: the shifts of the 296-member clusters leave one small pivot per
+    # block in U, and for late members the chunked back substitution folds maps that grew
+    # across two of them (a boundary error of ~1e-5 relative).  The solves' consistency check
+    # must catch that and redo those solves sequentially.
+    d, e = inputs.glued_wilkinson(148, 1e-10)
+    w = orc.bisect(d, e)
+    head = orc.plan(d, e, w)[1]
+    Zs = {}
+    for name, kw in (("cwy", {}), ("cwy1", {"max_team": 1}), ("mgs", {"method": "mgs"})):
+        Z, info, *_ = gpu.tinv(d, e, w, return_info=True, **kw)
+        assert info == 0
+        assert residual_ratio(d, e, w, Z) <= 100 and orth_ratio(Z) <= 100, name
+        Zs[name] = Z
+    assert _within_cluster_orth(Zs["cwy"], head) <= 10
+    s, t = 1924, 2220
+    Zo, oinfo, *_ = orc.tinv(d, e, w[s:t], "cwy", j0=s)
+    assert oinfo == 0
+    assert sin_angle(Zo, Zs["cwy"][:, s:t]) <= 1e-10
+
+
 def test_tinv_toeplitz4200_closed_form(gpu):
     n = 4200
     d, e = inputs.toeplitz(n, 2.0, 1.0)
