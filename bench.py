@@ -49,6 +49,9 @@ WORKLOADS["serve"] = ("Poisson request stream (seed 3), n log-uniform [128,4096]
 # kernels one call enqueues: plan (2), LU (2), first sweep, cluster kernel, CWY finalize, status
 LAUNCHES = {"cwy": 8, "mgs": 7}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (vector and tensor alike), TFLOP/s
+# DRAM bytes (read + write) of one cluster-kernel launch, from ncu on the current kernels
+# (profiles/launches_glued4200_cwy.md); None where no capture exists
+TRAFFIC_BYTES = {("glued4200", "cwy"): 25.71e9}
 
 
 def parse():
@@ -612,7 +615,8 @@ def ours_arm(args):
     kern_ms = float(statistics.mean(chain_ms))
     achieved = flops / (kern_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_chain",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": TRAFFIC_BYTES.get((args.workload, args.method)), "kernel": "k_chain",
             "kernel_ms": kern_ms, "flops_per_launch": flops,
             "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (derived in the design notes)",
             "phase_ms": {"plan": float(phase[0]), "lu": float(phase[1]),
