@@ -180,7 +180,8 @@ __device__ __forceinline__ double cluster_work(const Ws& w, int32_t c)
     return sz * sz * (double)w.segs[w.segj[w.clstart[c]]].n;
 }
 
-constexpr int kMaxCand = 1024;  // team candidates: at most P / 2 <= 1024
+constexpr int kMaxCand = 1024;   // team candidates: at most P / 2 <= 1024
+constexpr int kSliceTeam = 32;  // teams at least this large reduce s and g by slices
 
 // Plan, part 2: one CTA over all eigenvalues.  Cluster heads and the list of clusters with >= 2
 // members, T offsets, and the assignment of clusters to CTA teams of the persistent kernel:
@@ -857,6 +858,10 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
 
     // rows of passes A and C and of the head step
     const int64_t ra0 = part_lo(0, n, rank, G), ra1 = part_lo(0, n, rank + 1, G);
+    // Large teams add the team partials of s and g by slices (one CTA per slice, one more
+    // barrier) instead of every CTA adding all G partials of every column it needs; the
+    // additions are the same, in the same order, so the results do not change.
+    const bool sliced = G >= kSliceTeam;
 
     int64_t kstart = 0;
     if (!orth) {
@@ -943,10 +948,17 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 PROF_MARK(cx.prof, kPhB1);
                 // ---- s' = T_k^T s, columns [c0, c1) of this CTA ----
                 PROF_MARK(cx.prof, kPhB1);
-                for (int64_t l = t; l < c1; l += B) {
-                    double a = 0.0;
-                    a = sum_partials(w.partS + (size_t)leader * ns + l, ns, G);
-                    s1[l] = a;
+                if (sliced) {
+                    // each CTA adds the G partials of its slice of columns into vecX (free
+                    // until the T column step); then every CTA reads the columns it needs
+                    const int64_t l0 = part_lo(0, k, rank, G), l1 = part_lo(0, k, rank + 1, G);
+                    for (int64_t l = l0 + t; l < l1; l += B)
+                        vecX[l] = sum_partials(w.partS + (size_t)leader * ns + l, ns, G);
+                    if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+                    for (int64_t l = t; l < c1; l += B) s1[l] = __ldcg(&vecX[l]);
+                } else {
+                    for (int64_t l = t; l < c1; l += B)
+                        s1[l] = sum_partials(w.partS + (size_t)leader * ns + l, ns, G);
                 }
                 __syncthreads();
                 PROF_MARK(cx.prof, kPhT1a);
@@ -1003,9 +1015,18 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                     s_b[2] = ue - cc;                    // y_kk
                     s_b[3] = broke ? 1.0 : 0.0;
                 }
+            } else if (sliced) {
+                // the slice of g of this CTA into vecS (free after pass B)
+                const int64_t l0 = part_lo(0, k, rank, G), l1 = part_lo(0, k, rank + 1, G);
+                for (int64_t l = l0 + (t - 32); l < l1; l += B - 32)
+                    vecS[l] = sum_partials(w.partG + (size_t)leader * ns + l, ns, G);
             } else {
                 for (int64_t l = i0 + (t - 32); l < k; l += B - 32)
                     s1[l] = sum_partials(w.partG + (size_t)leader * ns + l, ns, G);
+            }
+            if (sliced) {
+                if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+                for (int64_t l = i0 + t; l < k; l += B) s1[l] = __ldcg(&vecS[l]);
             }
             __syncthreads();
             const double cc = s_b[0], tk = s_b[1], ykk = s_b[2];
