@@ -943,6 +943,11 @@ __device__ __noinline__ void cta_coldots(const double* __restrict__ A, int64_t l
     const int cl = lane >> 2, ph = lane & 3;
     const int64_t nc = c1 - c0;
     if (nc <= 0) return;
+    // the rows the columns [c0, c1) can touch (the row segments below are laid over them)
+    if (KIND == kLower)
+        rlo = max(rlo, c0);
+    else
+        rhi = min(rhi, c1);
     if (nc <= nW) {
         // few columns: one warp per column, lanes along its rows, one shuffle reduction
         if (wid < nc) {

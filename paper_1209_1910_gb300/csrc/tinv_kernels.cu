@@ -735,6 +735,23 @@ __device__ __forceinline__ int64_t part_lo(int64_t a, int64_t b, int r, int G)
     return a + ((b - a) * r) / G;
 }
 
+// Split the n rows of a lower trapezoid with K columns (row rho holds min(rho+1, K) of them)
+// into G ranges of equal work: the rows of passes A and C.
+__device__ __forceinline__ int64_t trap_row_lo(int64_t n, int64_t K, int r, int G)
+{
+    if (r <= 0) return 0;
+    if (r >= G) return n;
+    const double Kd = (double)K, tri = 0.5 * Kd * (Kd + 1.0);
+    const double total = tri + (double)(n - K) * Kd;
+    const double tgt = total * (double)r / (double)G;
+    int64_t rho;
+    if (tgt <= tri)
+        rho = (int64_t)llrint(0.5 * (sqrt(8.0 * tgt + 1.0) - 1.0));
+    else
+        rho = K + (int64_t)llrint((tgt - tri) / Kd);
+    return min(n, max((int64_t)0, rho));
+}
+
 // Split [0, k) so that column i of an upper-triangular matrix (work i+1) is balanced.
 __device__ __forceinline__ int64_t tri_col_lo(int64_t k, int r, int G)
 {
@@ -908,15 +925,19 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
         const double u0n = orth ? 0.0 : w.u0n[j];
         // balanced bounds of this CTA's share of the T products (FP64 sqrt: one thread, once
         // per member; every CTA of the team computes the same values)
-        __shared__ int64_t s_tb[4];
+        __shared__ int64_t s_tb[6];
         if (t == 0) {
             s_tb[0] = tri_col_lo(k, rank, G);
             s_tb[1] = tri_col_lo(k, rank + 1, G);
             s_tb[2] = tri_row_lo(k, rank, G);
             s_tb[3] = tri_row_lo(k, rank + 1, G);
+            // rows of passes A and C, balanced for the trapezoid of Y_{k+1}
+            s_tb[4] = trap_row_lo(n, k + 1, rank, G);
+            s_tb[5] = trap_row_lo(n, k + 1, rank + 1, G);
         }
         __syncthreads();
         const int64_t c0 = s_tb[0], c1 = s_tb[1], i0 = s_tb[2], i1 = s_tb[3];
+        const int64_t rc0 = s_tb[4], rc1 = s_tb[5];
         int nrmchk = 0, its = 0;
         bool conv = false;
         double fac_next = 0.0;
@@ -934,14 +955,17 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 if (!team_solve(n, f, qbuf, fac_next, vsm, vbuf, vecS, ra0, ra1, pubf, pubb, tr, red))
                     return false;
                 PROF_MARK(cx.prof, kPhSolve);
-            } else {
-                for (int64_t r = ra0 + t; r < ra1; r += B) vsm[r] = __ldcg(&vsrc[r]);
+            }
+            // pass A's rows of v (all rows of vsrc are complete: the solve ends with a team
+            // barrier, the first sweep's iterate was written before this kernel)
+            if (orth || its == 1 || rc0 != ra0 || rc1 != ra1) {
+                for (int64_t r = rc0 + t; r < rc1; r += B) vsm[r] = __ldcg(&vsrc[r]);
                 __syncthreads();
             }
             PROF_MARK(cx.prof, kPhLoad);
             if (k > 0) {
                 // ---- pass A: s = Y_k^T v = L_k^T v_check + Yhat_k^T v_hat (team partials) ----
-                cta_coldots<kLower>(Yc, n, 0, k, ra0, ra1, vsm, red,
+                cta_coldots<kLower>(Yc, n, 0, k, rc0, rc1, vsm, red,
                                     [&](int64_t i, double s) { myS[i] = s; });
                 PROF_MARK(cx.prof, kPhA);
                 if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
@@ -1064,7 +1088,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             for (int64_t l = t; l <= k; l += B) s1[l] = __ldcg(&vecX[l]);
             __syncthreads();
             PROF_MARK(cx.prof, kPhCa);
-            cta_rowdots<kLowerCol, 1>(Yc, n, ra0, ra1, k + 1, s1, nullptr, red,
+            cta_rowdots<kLowerCol, 1>(Yc, n, rc0, rc1, k + 1, s1, nullptr, red,
                                       [&](int64_t rho, double a, double) {
                                           const double q = (rho == k) ? a - 1.0 : a;
                                           qbuf[rho] = q;
@@ -1074,7 +1098,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             // 2-norm and the sign convention are applied once, by k_finalize
             PROF_MARK(cx.prof, kPhCb);
             double as, am;
-            cta_sum_max<false>(vsm + ra0, ra1 - ra0, red, as, am);
+            cta_sum_max<false>(vsm + rc0, rc1 - rc0, red, as, am);
             if (t == 0) {
                 scal_t[rank * kScalTeam + 2] = as;
                 scal_t[rank * kScalTeam + 3] = am;
