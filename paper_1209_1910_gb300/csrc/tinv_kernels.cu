@@ -735,12 +735,15 @@ __device__ __forceinline__ int64_t part_lo(int64_t a, int64_t b, int r, int G)
     return a + ((b - a) * r) / G;
 }
 
-// Split the n rows of a lower trapezoid with K columns (row rho holds min(rho+1, K) of them)
-// into G ranges of equal work: the rows of passes A and C.
+// Rows of passes A and C for rank r of G: the n rows of a lower trapezoid with K columns (row
+// rho holds min(rho+1, K) of them).  While the triangle is a small part (4K <= n) equal rows
+// are used (short rows run less efficiently, so their smaller work does not make them cheaper);
+// beyond that, ranges of equal work.
 __device__ __forceinline__ int64_t trap_row_lo(int64_t n, int64_t K, int r, int G)
 {
     if (r <= 0) return 0;
     if (r >= G) return n;
+    if (4 * K <= n) return (n * r) / G;
     const double Kd = (double)K, tri = 0.5 * Kd * (Kd + 1.0);
     const double total = tri + (double)(n - K) * Kd;
     const double tgt = total * (double)r / (double)G;
