@@ -11,7 +11,8 @@ One JSON line is printed by rank 0.  `value` is the device-timed throughput with
 resident in HBM (CUDA events around each step on the launching stream, L2 flushed by a
 512 MiB write between steps); `e2e` is the same metric through the host-pointer C ABI call
 (pinned host buffers, host<->device copies inside the timed region).  With N > 1 (torchrun)
-every rank solves its own copy of the workload (replicas; no collective on the data path).
+every rank solves its own copy of a single-problem workload (replicas), and the batch workload
+is split into per-rank problem shards; there is no collective on the data path.
 """
 from __future__ import annotations
 
@@ -219,12 +220,23 @@ def batch_arm(args):
     import torch
 
     from paper_1209_1910_gb300 import binding, build
+    from paper_1209_1910_gb300.replicas import env_rank, lpt_shards, problem_cost, reduce_max, reduce_sum
 
-    dev = torch.device("cuda", 0)
+    rank, world, local = env_rank()
+    dist = None
+    dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=dev)
     build.build()
     binding.load()
-    probs = inputs.batch_matrices()
+    probs_all = inputs.batch_matrices()
+    # several GPUs: each rank solves its own shard of the problems (no data-path collective)
+    shard = lpt_shards([problem_cost(len(p[0])) for p in probs_all], world)[rank]
+    probs = [probs_all[q] for q in shard]
     ns, off_de, off_z = binding.pack_offsets([len(p[0]) for p in probs])
     M, nprob = int(ns.sum()), len(ns)
     D = np.zeros(M)
@@ -256,6 +268,8 @@ def batch_arm(args):
     st = torch.cuda.current_stream(dev)
     sampler = ClockSampler(None)
     step_ms, chain_ms = [], []
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
     for _ in range(args.steps):
@@ -269,9 +283,16 @@ def batch_arm(args):
         step_ms.append(a.elapsed_time(b))
         chain_ms.append(float(phase[3]))
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     sampler.stop()
     total_ms = float(sum(step_ms))
-    value = M * args.steps / (total_ms * 1e-3)
+    M_all, nprob_all = M, nprob
+    if dist:
+        total_ms = reduce_max(total_ms, dist, dev)
+        M_all = int(reduce_sum(M, dist, dev))
+        nprob_all = int(reduce_sum(nprob, dist, dev))
+    value = M_all * args.steps / (total_ms * 1e-3)
 
     # checks: status of every problem; residual and orthogonality ratios of a sample
     nonconv = int(info.sum().item())
@@ -303,15 +324,16 @@ def batch_arm(args):
     kern_ms = float(statistics.mean(chain_ms))
     achieved = flops / (kern_ms * 1e-3) / 1e12
     out = {
-        "metric": "eigvecs_per_s", "value": value, "unit": "eigvec/s", "n_gpus": 1,
+        "metric": "eigvecs_per_s", "value": value, "unit": "eigvec/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS["batch512"], "method": args.method,
-                   "problems": nprob, "eigenvectors": M, "parallelism": "single",
+                   "problems": nprob_all, "eigenvectors": M_all,
+                   "parallelism": "problem shards (LPT)" if world > 1 else "single",
                    "inputs": "resident in HBM (eigenvalues by GPU bisection, untimed)",
                    "l2": "flushed by a 512 MiB write between steps"},
-        "problems_per_s": nprob * args.steps / (total_ms * 1e-3),
+        "problems_per_s": nprob_all * args.steps / (total_ms * 1e-3),
         "check": {"nonconverged": nonconv, "sampled_problems": len(sample),
                   "worst_residual_ratio": worst_r, "worst_orth_ratio": worst_o,
                   "sweeps": int(np.abs(it).sum())},
@@ -326,7 +348,7 @@ def batch_arm(args):
     }
 
     # the same problems one call at a time (each call a full launch sequence), same stream
-    if not args.no_compare:
+    if not args.no_compare and world == 1:
         def one_at_a_time():
             for q in range(nprob):
                 n, a0, z0 = int(ns[q]), int(off_de[q]), int(off_z[q])
@@ -346,7 +368,7 @@ def batch_arm(args):
                                             "problems_per_s": nprob / (t1 * 1e-3)}}
 
     # end to end through the host-pointer C ABI (pinned buffers, copies inside the timed region)
-    if not args.no_e2e:
+    if not args.no_e2e and world == 1:
         import ctypes
 
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -376,11 +398,15 @@ def batch_arm(args):
                       "d2h_bytes_per_step": int((ns * ns).sum()) * 8 + nprob * 8 + 64}
         del hz
 
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         v, desc = cpu_sample_batch(args.method, probs)
         out["cpu_baseline"] = {"value": v, "unit": "eigvec/s", "cores": 1, "kind": "oracle",
                                "sample": desc}
-    print(json.dumps(out), flush=True)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def cpu_sample_batch(method, probs, stride=32):
