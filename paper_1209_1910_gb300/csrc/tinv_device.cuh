@@ -308,20 +308,24 @@ __device__ __noinline__ void staged_seq_back(int64_t n, const Fac& f, const doub
 #define TINV_SOLVE_TOL 1024.0
 #endif
 constexpr double kSolveTol = TINV_SOLVE_TOL;  // accepted backward error of a row, in eps
+// For a solve whose result only starts the next sweep (not a possible final vector) any error
+// that leaves a usable start vector is harmless; this bound still rejects garbage.
+constexpr double kSolveTolLoose = 1099511627776.0;  // 2^40 eps
 
 __device__ __forceinline__ bool row_consistent(double a, double b, double r, double y, double x1,
-                                               double x2, double xk)
+                                               double x2, double xk, double tol)
 {
     const double v = back_row(a, b, r, y, x1, x2);
     const double scale = fabs(y * r) + fabs(a * x1) + fabs(b * x2);
-    return fabs(v - xk) <= kSolveTol * kEps * scale;
+    return fabs(v - xk) <= tol * kEps * scale;
 }
 
 // x (n rows) solved in place by P chunks; `ysave` (n doubles) receives the forward results for
-// the sequential fallback.  Returns true when the fallback ran.
+// the sequential fallback; `tol` is the accepted backward error of a row, in eps.  Returns true
+// when the fallback ran.
 template <class Sync>
 __device__ bool chunk_solve(int64_t n, const Fac& f, double* x, double* ysave, double* sh, int t,
-                            int P, Sync sync)
+                            int P, Sync sync, double tol = kSolveTol)
 {
     const int64_t L = (n + P - 1) / P;
     const int64_t lo = (int64_t)t * L;
@@ -442,10 +446,10 @@ __device__ bool chunk_solve(int64_t n, const Fac& f, double* x, double* ysave, d
     bool bad = false;
     if (act && hi < n) {
         const double x1 = x[hi], x2 = (hi + 1 < n) ? x[hi + 1] : 0.0;
-        bad = !row_consistent(f.a[hi - 1], f.b[hi - 1], f.r[hi - 1], ysv0, x1, x2, x[hi - 1]);
+        bad = !row_consistent(f.a[hi - 1], f.b[hi - 1], f.r[hi - 1], ysv0, x1, x2, x[hi - 1], tol);
         if (hi - 2 >= lo)
             bad = bad || !row_consistent(f.a[hi - 2], f.b[hi - 2], f.r[hi - 2], ysv1, x[hi - 1], x1,
-                                         x[hi - 2]);
+                                         x[hi - 2], tol);
     }
     const bool fallback = __any_sync(0xffffffffu, bad);
     if (fallback) {
@@ -484,6 +488,7 @@ struct TeamRef {
     unsigned long long* flag;  // team word for the consistency verdict (G > 1)
     unsigned long long stamp;  // increasing per solve of the team
     unsigned long long* nfall; // counter of sequential fallbacks (may be null)
+    double tol;                // accepted backward error of a row, in eps
 };
 
 __device__ __forceinline__ void compose2(double& m00, double& m01, double& m10, double& m11,
@@ -746,10 +751,10 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
     if (act && hi < n) {
         const double x1 = (hi < r1) ? vsm[hi] : __ldcg(&vout[hi]);
         const double x2 = (hi + 1 >= n) ? 0.0 : ((hi + 1 < r1) ? vsm[hi + 1] : __ldcg(&vout[hi + 1]));
-        bad = !row_consistent(f.a[hi - 1], f.b[hi - 1], f.r[hi - 1], ysv0, x1, x2, vsm[hi - 1]);
+        bad = !row_consistent(f.a[hi - 1], f.b[hi - 1], f.r[hi - 1], ysv0, x1, x2, vsm[hi - 1], tr.tol);
         if (hi - 2 >= lo)
             bad = bad || !row_consistent(f.a[hi - 2], f.b[hi - 2], f.r[hi - 2], ysv1, vsm[hi - 1],
-                                         x1, vsm[hi - 2]);
+                                         x1, vsm[hi - 2], tr.tol);
     }
     // verdict word: the solve's stamp above the largest failing boundary row (the restart point)
     __shared__ unsigned long long s_top;

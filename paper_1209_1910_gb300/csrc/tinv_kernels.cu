@@ -604,7 +604,11 @@ __global__ void __launch_bounds__(kFirstWarps * 32) k_first(Problem p, Ws w)
     while (its < maxits) {
         ++its;
         warp_scale(n, x, onenrm, u0n, lane);
-        if (chunk_solve(n, f, x, ysave, sh, lane, 32, WarpSync()) && lane == 0)
+        // a member's first sweep only starts the cluster kernel's sweeps; a head's sweep can
+        // be its last once it has kExtra successes or reaches the sweep limit
+        const bool may_end = is_head && (nrmchk >= kExtra || its == maxits);
+        if (chunk_solve(n, f, x, ysave, sh, lane, 32, WarpSync(), may_end ? kSolveTol : kSolveTolLoose) &&
+            lane == 0)
             atomicAdd((unsigned long long*)&w.ctr[kCtrFallbackFirst], 1ull);
         if (!is_head) break;
         double mx = 0.0;
@@ -952,9 +956,13 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
             const double* vsrc = orth ? cx.V + kk * cx.ldv : (its == 1 ? Zc + kk * ldz : vbuf);
             if (!orth && its > 1) {
                 PROF_MARK(cx.prof, kPhLoad);
+                // the solve of a sweep that cannot be the member's last only starts the next
+                // sweep: a loose check suffices
+                const bool may_end = nrmchk >= kExtra || its == maxits;
                 TeamRef tr{tm.bar, &tm.target, G, rank, cx.err,
                            (unsigned long long*)(scal_t + 15), ++cx.nsolve,
-                           (unsigned long long*)&w.ctr[kCtrFallback]};
+                           (unsigned long long*)&w.ctr[kCtrFallback],
+                           may_end ? kSolveTol : kSolveTolLoose};
                 if (!team_solve(n, f, qbuf, fac_next, vsm, vbuf, vecS, ra0, ra1, pubf, pubb, tr, red))
                     return false;
                 PROF_MARK(cx.prof, kPhSolve);
@@ -1191,8 +1199,10 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
                 __syncthreads();
                 const double scl = s_scl;
                 uint32_t tgt = 0;
+                const bool may_end = nrmchk >= kExtra || its == maxits;
                 TeamRef tr{nullptr, &tgt, 1, 0, cx.err, nullptr, 0ull,
-                           (unsigned long long*)&w.ctr[kCtrFallback]};
+                           (unsigned long long*)&w.ctr[kCtrFallback],
+                           may_end ? kSolveTol : kSolveTolLoose};
                 if (!team_solve(n, f, v, scl, v, nullptr, cx.s1, 0, n, nullptr, nullptr, tr, red))
                     return false;
             }
