@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_list(Problem p, Ws w, int
     __shared__ int64_t sredl[33];
     __shared__ int32_t s_cand[kMaxCand];
     __shared__ uint8_t s_team[kMaxCand];
+    __shared__ int32_t s_gsz[kMaxCand];
     __shared__ int32_t s_hist[64], s_cur[64];
     __shared__ int32_t s_ncand;
     const int t = threadIdx.x, B = blockDim.x;
@@ -279,13 +280,40 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_list(Problem p, Ws w, int
         int32_t Q = 0;
         if (wq > 0.0) Q = max(1, (int32_t)llrint(P * wq / wtot));
         const int32_t Pteam = max(0, P - Q);
+        // team sizes: floor of each candidate's share; the CTAs left over go one each to the
+        // teams with the largest fractional shares (ties to the earlier cluster)
+        int32_t used = 0;
+        for (int32_t i = 0; i < ncand; ++i) {
+            const int32_t c = s_cand[i];
+            int32_t gmax = (int32_t)min((int64_t)P, max((int64_t)1, w.segs[w.segj[w.clstart[c]]].n / 16));
+            if (max_team > 0) gmax = min(gmax, max_team);
+            const double share = Pteam * cluster_work(w, c) / wteam;
+            const int32_t g = min(gmax, (int32_t)floor(share));
+            s_gsz[i] = g;
+            if (g >= 2) used += g;
+        }
+        for (int32_t left = Pteam - used; left > 0; --left) {
+            int32_t best = -1;
+            double bf = -1.0;
+            for (int32_t i = 0; i < ncand; ++i) {
+                const int32_t c = s_cand[i];
+                int32_t gmax = (int32_t)min((int64_t)P, max((int64_t)1, w.segs[w.segj[w.clstart[c]]].n / 16));
+                if (max_team > 0) gmax = min(gmax, max_team);
+                if (s_gsz[i] < 2 || s_gsz[i] >= gmax) continue;
+                const double share = Pteam * cluster_work(w, c) / wteam;
+                const double fr = share - (double)s_gsz[i];
+                if (fr > bf) {
+                    bf = fr;
+                    best = i;
+                }
+            }
+            if (best < 0) break;
+            ++s_gsz[best];
+        }
         int32_t next = 0;
         for (int32_t i = 0; i < ncand; ++i) {
             const int32_t c = s_cand[i];
-            const double wc = cluster_work(w, c);
-            int32_t gmax = (int32_t)min((int64_t)P, max((int64_t)1, w.segs[w.segj[w.clstart[c]]].n / 16));
-            if (max_team > 0) gmax = min(gmax, max_team);
-            int32_t g = min(gmax, (int32_t)floor(Pteam * wc / wteam));
+            const int32_t g = s_gsz[i];
             s_team[i] = 0;
             if (g >= 2 && next + g <= Pteam) {
                 for (int32_t r = 0; r < g; ++r) {
