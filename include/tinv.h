@@ -70,7 +70,12 @@ typedef struct tinv_opts {
                          /*   sequentially (consistency check failed), [1] clusters with >= 2  */
                          /*   members, [2] clusters given CTA teams, [3] as [0] for the first   */
                          /*   sweeps                                                            */
-    int32_t reserved[6];
+    int32_t table_ready; /* tinv_batch with device pointers and o->workspace: 1 = the workspace */
+                         /*   already holds this batch's problem table (an earlier call with    */
+                         /*   the same n, off_de, off_z, seed and j0 wrote it); the call then   */
+                         /*   makes no host-to-device copy and no allocation, so it can be      */
+                         /*   captured into a CUDA graph and replayed (phase_ms must be NULL)   */
+    int32_t reserved[5];
 } tinv_opts;
 
 /* Fill *o with the defaults: CWY, host pointers, seed 0, j0 0, automatic scheduling. */

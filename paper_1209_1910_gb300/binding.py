@@ -46,7 +46,7 @@ class Opts(ctypes.Structure):
                 ("iters", ctypes.c_void_p), ("info", ctypes.c_void_p),
                 ("max_team", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
                 ("phase_ms", ctypes.c_void_p), ("counters", ctypes.c_void_p),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("table_ready", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 def load(path: str | None = None) -> ctypes.CDLL:

@@ -336,9 +336,11 @@ int batch_enqueue_device(int64_t nprob, const int64_t* n, const int64_t* off_de,
         ws = own.p;
     }
     const Ws wsb = bind_layout(ws, L, D);
-    cudaError_t ce = cudaMemcpyAsync(wsb.segs, segs.data(), segs.size() * sizeof(Seg),
-                                     cudaMemcpyHostToDevice, st);
-    if (ce != cudaSuccess) return cuda_code(ce);
+    if (!(o.table_ready && o.workspace)) {
+        cudaError_t ce = cudaMemcpyAsync(wsb.segs, segs.data(), segs.size() * sizeof(Seg),
+                                         cudaMemcpyHostToDevice, st);
+        if (ce != cudaSuccess) return cuda_code(ce);
+    }
     rc = enqueue_tinv(p, ws, D, o.max_team, st, o.phase_ms);
     if (rc != 0) return rc;
     if (info) {
