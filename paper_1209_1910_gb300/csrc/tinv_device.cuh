@@ -467,10 +467,12 @@ __device__ bool chunk_solve(int64_t n, const Fac& f, double* x, double* ysave, d
 // The team's G CTAs each own rows [r0, r1) (>= 2 rows each).  Inside a CTA the first 128
 // threads own contiguous chunks; every chunk computes the affine map of both substitutions
 // over its rows (as in chunk_solve).  Maps are combined by an inclusive Kogge-Stone scan inside
-// each warp (at most 32 chunks, so composed maps stay small), then by one thread over the 4
-// warps into the CTA's map, which is published to the team.  After one team barrier per
-// direction every CTA folds the published maps of the CTAs before it (forward) or after it
-// (back) as actual values, then re-runs its rows from the true boundary values.
+// each warp, then by one thread over the 4 warps into the CTA's map, which is published to the
+// team.  After one team barrier per direction every CTA folds the published maps of the CTAs
+// before it (forward) or after it (back) as actual values.  In the forward direction the warps'
+// composed maps then give every chunk its carry; in the back direction (whose maps grow at small
+// pivots) the first lane of each warp folds the warp's own chunk maps as values instead.  Every
+// chunk then re-runs its rows from its boundary values, and the result is checked.
 //   bsrc  : right-hand side (global, or shared when G == 1); the solve reads bsrc[k] * fac for
 //           its rows and the first row of the next CTA.
 //   ysave : n doubles (global when G > 1, not vsm) receiving the forward results of the own rows,
@@ -478,7 +480,7 @@ __device__ bool chunk_solve(int64_t n, const Fac& f, double* x, double* ysave, d
 //   vsm   : row-indexed scratch of the CTA (n slots); on return vsm[r0..r1) = x.
 //   vout  : if not null, also receives x[r0..r1) (global, for other CTAs of the team).
 //   pubf, pubb : team buffers of 2 and 6 doubles per rank for the published maps.
-//   sh    : >= 128 + 6 G doubles of shared scratch.
+//   sh    : 2048 doubles of shared scratch (128 + 6 G + 6 * 128 are used; G <= 192).
 // ------------------------------------------------------------------------------------------
 struct TeamRef {
     uint32_t* bar;
@@ -641,8 +643,20 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
         f0 = p0;
         f1 = p1;
     }
+    // The chunks' own maps, kept for the value fold below that gives every chunk its boundary
+    // values (applying composed maps to values loses accuracy when they span several small
+    // pivots; the compositions are used only between warps and between CTAs).
+    double* cm = sh + 128 + 6 * tr.G;  // [6 * PT]; sh holds 2048 doubles, so G <= 192
+    if (part) {
+        double* o = cm + 6 * t;
+        o[0] = m00;
+        o[1] = m01;
+        o[2] = m10;
+        o[3] = m11;
+        o[4] = f0;
+        o[5] = f1;
+    }
     // inclusive suffix scan within the warp: S_p = m_p o m_{p+1} o ... o m_31
-    double e00 = 1.0, e01 = 0.0, e10 = 0.0, e11 = 1.0, g0 = 0.0, g1 = 0.0;  // exclusive
     if (part) {
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -653,20 +667,6 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
             const double q0 = __shfl_down_sync(0xffffffffu, f0, d);
             const double q1 = __shfl_down_sync(0xffffffffu, f1, d);
             if (lane + d < 32) compose2(m00, m01, m10, m11, f0, f1, n00, n01, n10, n11, q0, q1);
-        }
-        e00 = __shfl_down_sync(0xffffffffu, m00, 1);
-        e01 = __shfl_down_sync(0xffffffffu, m01, 1);
-        e10 = __shfl_down_sync(0xffffffffu, m10, 1);
-        e11 = __shfl_down_sync(0xffffffffu, m11, 1);
-        g0 = __shfl_down_sync(0xffffffffu, f0, 1);
-        g1 = __shfl_down_sync(0xffffffffu, f1, 1);
-        if (lane == 31) {
-            e00 = 1.0;
-            e01 = 0.0;
-            e10 = 0.0;
-            e11 = 1.0;
-            g0 = 0.0;
-            g1 = 0.0;
         }
         if (lane == 0) {
             double* o = sh + 32 + 6 * wid;
@@ -725,11 +725,25 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
         }
     }
     __syncthreads();
+    // each warp's first lane folds the warp's chunk maps as values, from the warp's boundary
+    // values upwards; chunk p receives (x_hi, x_hi+1) in its slots 0 and 1
+    if (part && lane == 0) {
+        double s0 = sh[64 + 2 * wid], s1 = sh[64 + 2 * wid + 1];
+        for (int l = 31; l >= 0; --l) {
+            double* o = cm + 6 * (32 * wid + l);
+            const double q00 = o[0], q01 = o[1], q10 = o[2], q11 = o[3], q0 = o[4], q1 = o[5];
+            o[0] = s0;
+            o[1] = s1;
+            const double n0 = fma(q00, s0, fma(q01, s1, q0));
+            const double n1 = fma(q10, s0, fma(q11, s1, q1));
+            s0 = n0;
+            s1 = n1;
+        }
+    }
+    __syncwarp();
     double ysv0 = 0.0, ysv1 = 0.0;  // forward results of rows hi-1, hi-2
     if (act) {
-        const double w0 = sh[64 + 2 * wid], w1 = sh[64 + 2 * wid + 1];
-        double cur = fma(e00, w0, fma(e01, w1, g0));
-        double nxt = fma(e10, w0, fma(e11, w1, g1));
+        double cur = cm[6 * t], nxt = cm[6 * t + 1];
         ysv0 = vsm[hi - 1];
         if (hi - 2 >= lo) ysv1 = vsm[hi - 2];
         for (int64_t k = hi - 1; k >= lo; --k) {
@@ -763,6 +777,14 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
     if (bad) atomicMax(&s_top, (unsigned long long)hi);
     bool fallback = __syncthreads_or(bad) != 0;
     int64_t top = (int64_t)s_top;
+#ifdef TINV_PHASE_PROFILE
+    if (bad) {
+        // boundary kind: 0 inside a warp, 1 between warps of the CTA, 2 between CTAs
+        const int kind = (hi >= r1) ? 2 : (((t + 1) & 31) == 0 ? 1 : 0);
+        printf("BADBOUND rank=%d G=%d t=%d hi=%lld kind=%d tol=%g\n", tr.rank, tr.G, t, (long long)hi,
+               kind, tr.tol);
+    }
+#endif
     if (tr.G > 1) {
         if (fallback && t == 0) atomicMax(tr.flag, (tr.stamp << 32) | s_top);
         if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
@@ -776,6 +798,9 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
         if (tr.rank == 0) {
             staged_seq_back(n, f, ysave, tr.G > 1 ? vout : vsm, sh, top);
             if (t == 0 && tr.nfall) atomicAdd(tr.nfall, 1ull);
+#ifdef TINV_PHASE_PROFILE
+            if (t == 0) printf("FALLBACK G=%d top=%lld n=%lld\n", tr.G, (long long)top, (long long)n);
+#endif
         }
         if (tr.G > 1) {
             if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
