@@ -52,7 +52,7 @@ LAUNCHES = {"cwy": 8, "mgs": 7}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (vector and tensor alike), TFLOP/s
 # DRAM bytes (read + write) of one cluster-kernel launch, from ncu on the current kernels
 # (profiles/launches_glued4200_cwy.md); None where no capture exists
-TRAFFIC_BYTES = {("glued4200", "cwy"): 37.84e9}
+TRAFFIC_BYTES = {("glued4200", "cwy"): 31.54e9}
 
 
 def parse():
