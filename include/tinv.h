@@ -171,6 +171,41 @@ int tinv_bisect_batch(int64_t nprob, const int64_t* n, const int64_t* off_de, co
                       const double* e, double* w, const tinv_opts* o);
 
 /*
+ * tinv_split -- the unreduced blocks of T.  The paper takes its eigenvalues from LAPACK's
+ * bisection (Sec. 5.1), which hands DSTEIN the blocks of T (IBLOCK/ISPLIT); the rule here: row i
+ * ends a block iff |e_i| <= eps ||T||_1, with eps = 2^-52 and ||T||_1 = max_i(|d_i| + |e_{i-1}|
+ * + |e_i|) (dropping such an entry changes T by at most eps ||T||_1 in norm).
+ *   isplit : [n] receives, for each block b < *nblock, one past its last row (ascending; the last
+ *            entry is n).  nblock : receives the number of blocks (0 for n = 0).
+ * d, e and isplit follow o->device_ptrs for d, e only: isplit and nblock are always host memory
+ * (the call synchronizes o->stream).  Returns 0, -k for invalid argument k, or a runtime error.
+ */
+int tinv_split(int64_t n, const double* d, const double* e, int64_t* isplit, int64_t* nblock,
+               const tinv_opts* o);
+
+/*
+ * tinv_eig -- all eigenvalues and eigenvectors of T, with T split first (tinv_split): each block
+ * is an independent problem whose eigenvalues come from bisection (tinv_bisect) and whose
+ * eigenvectors come from inverse iteration with the chosen reorthogonalization (tinv_batch over
+ * the blocks; method, seed and j0 apply to every block as in tinv_batch).  The block results are
+ * merged into ascending order by a stable sort over the blocks' eigenvalues taken in block order
+ * (equal values keep the lower block first).
+ *   w      : [n] receives the eigenvalues, ascending.
+ *   Z      : n x n, column-major, leading dimension ldz >= n: column j receives the unit
+ *            eigenvector of w[j] (sign as in tinv), exactly zero outside its block.
+ *   iblock : optional [n]: the block (0-based) of each eigenvalue.
+ *   isplit, nblock : optional, as tinv_split (always host memory).
+ *   o      : method, seed, j0, max_team, grid_ctas apply; o->iters, if given, receives the sweep
+ *            counts in the order of w; workspace, counters and phase_ms are not used.
+ * d, e, w, Z, iblock and o->iters are host or device memory following o->device_ptrs.  The call
+ * synchronizes o->stream (the block table and the merge order are formed on the host).
+ * Returns 0, -k for invalid argument k (n = 1, d = 2, e = 3, w = 4, Z = 5, ldz = 6, method = 10),
+ * the total number of non-converged vectors (> 0), or a runtime error code.
+ */
+int tinv_eig(int64_t n, const double* d, const double* e, double* w, double* Z, int64_t ldz,
+             int64_t* iblock, int64_t* isplit, int64_t* nblock, const tinv_opts* o);
+
+/*
  * tinv_plan -- step a1/a2 alone (Sec. 2.1; Alg. 4): ||T||_1, the cluster
  * tolerance, the convergence threshold and the cluster head of every eigenvalue.
  *   wp    : [m] perturbed shifts w' (coincident approximations are separated by 10 eps |w|).

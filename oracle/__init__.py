@@ -61,6 +61,8 @@ def _load():
             lib.orc_start_value.argtypes = [ctypes.c_uint64, I64, ctypes.c_int, I64]
             lib.orc_onenorm.restype = D
             lib.orc_onenorm.argtypes = [I64, P, P]
+            lib.orc_split.restype = I64
+            lib.orc_split.argtypes = [I64, P, P, P]
             lib.orc_sturm_count.restype = I64
             lib.orc_sturm_count.argtypes = [I64, P, P, D, D]
             lib.orc_bisect.restype = None
@@ -107,6 +109,16 @@ def start_vector(seed: int, j: int, n: int, attempt: int = 0) -> np.ndarray:
 def onenorm(d, e) -> float:
     d, e = _f64(d), _f64(e)
     return float(_load().orc_onenorm(len(d), _p(d), _p(e)))
+
+
+def split(d, e) -> np.ndarray:
+    """One past the last row of each unreduced block (row i ends a block iff
+    |e_i| <= eps ||T||_1)."""
+    d, e = _f64(d), _f64(e)
+    n = len(d)
+    isplit = np.zeros(max(n, 1), dtype=np.int64)
+    nb = int(_load().orc_split(n, _p(d), _p(e), _p(isplit)))
+    return isplit[:nb].copy()
 
 
 def sturm_count(d, e, x: float, pivmin: float) -> int:
@@ -183,6 +195,39 @@ def tinv(d, e, w, method: str = "cwy", seed: int = 0, j0: int = 0):
                             ctypes.c_uint64(seed), _p(ifail), _p(iters), ctypes.byref(st))
     return Z, int(info), ifail[:info], iters[:m], {
         "sweeps": st.sweeps, "breakdowns": st.breakdowns, "orth_flops": st.orth_flops}
+
+
+def eig_split(d, e, method: str = "cwy", seed: int = 0, j0: int = 0):
+    """All eigenpairs of T split into unreduced blocks: each block's eigenvalues by bisection
+    and its eigenvectors by `tinv` (the same method, seed and j0 for every block), merged into
+    ascending order by a stable sort over the blocks' values in block order (ties keep the
+    lower block first).  Returns (w, Z, iblock, isplit, info); Z is n x n with each column zero
+    outside its block."""
+    d, e = _f64(d), _f64(e)
+    n = len(d)
+    isplit = split(d, e)
+    vals, blk, cols = [], [], []
+    info = 0
+    b0 = 0
+    for b, b1 in enumerate(isplit):
+        db, eb = d[b0:b1], e[b0:b1 - 1]
+        wb = bisect(db, eb)
+        Zb, ib, _, _, _ = tinv(db, eb, wb, method=method, seed=seed, j0=j0)
+        info += ib
+        for l in range(b1 - b0):
+            col = np.zeros(n)
+            col[b0:b1] = Zb[:, l]
+            vals.append(wb[l])
+            blk.append(b)
+            cols.append(col)
+        b0 = b1
+    order = np.argsort(np.asarray(vals), kind="stable")
+    w = np.asarray(vals)[order] if n else np.zeros(0)
+    Z = np.zeros((n, n), order="F")
+    for j, src in enumerate(order):
+        Z[:, j] = cols[src]
+    iblock = np.asarray(blk, dtype=np.int64)[order] if n else np.zeros(0, dtype=np.int64)
+    return w, Z, iblock, isplit, info
 
 
 def jacobi(A):

@@ -97,6 +97,25 @@ double orc_onenorm(int64_t n, const double* d, const double* e)
     return nrm;
 }
 
+/* Unreduced blocks.  The paper takes its eigenvalues and their blocks from DSTEBZ and is silent
+ * on the splitting rule; the reading taken here: the entry e_i is negligible, and row i ends a
+ * block, iff |e_i| <= eps ||T||_1.  Dropping it changes T by at most eps ||T||_1 in norm, within
+ * the residual bound the method already has.  isplit[b] = one past the last row of block b. */
+int64_t orc_split(int64_t n, const double* d, const double* e, int64_t* isplit)
+{
+    if (n <= 0) return 0;
+    double tol = EPS * orc_onenorm(n, d, e);
+    int64_t nb = 0;
+    for (int64_t i = 0; i < n - 1; ++i) {
+        if (fabs(e[i]) <= tol) {
+            isplit[nb] = i + 1;
+            nb = nb + 1;
+        }
+    }
+    isplit[nb] = n;
+    return nb + 1;
+}
+
 int64_t orc_sturm_count(int64_t n, const double* d, const double* e, double x, double pivmin)
 {
     int64_t cnt = 0;

@@ -38,6 +38,9 @@ double orc_start_value(uint64_t seed, int64_t j, int attempt, int64_t i);
 /* ||T||_1 = max_i (|d_i| + |e_{i-1}| + |e_i|) (the norm in the Peters-Wilkinson test). */
 double orc_onenorm(int64_t n, const double* d, const double* e);
 
+/* Split points: row i ends a block iff |e_i| <= eps ||T||_1; isplit[b] = one past the last row
+ * of block b (isplit holds n entries).  Returns the number of blocks (0 for n = 0).     */
+int64_t orc_split(int64_t n, const double* d, const double* e, int64_t* isplit);
 /* Sturm count: number of eigenvalues of T strictly below x.                            */
 int64_t orc_sturm_count(int64_t n, const double* d, const double* e, double x, double pivmin);
 /* All n eigenvalues of T by Sturm-count bisection, ascending (the paper's DSTEBZ step). */

@@ -26,7 +26,7 @@ ERRORS = {-101: "ENOMEM", -102: "ECUDA", -103: "ETIMEDOUT", -104: "EAGAIN", -105
 # every function include/tinv.h declares
 EXPORTS = ["tinv_opts_default", "tinv_strerror", "tinv_version", "tinv", "tinv_ex",
            "tinv_workspace_size", "tinv_batch", "tinv_batch_workspace_size", "tinv_bisect",
-           "tinv_bisect_batch", "tinv_plan",
+           "tinv_bisect_batch", "tinv_split", "tinv_eig", "tinv_plan",
            "tinv_lu", "tinv_solve", "tinv_solve_noalloc", "tinv_orth",
            "tinv_server_cfg_default", "tinv_server_create", "tinv_submit", "tinv_poll",
            "tinv_wait", "tinv_cancel", "tinv_server_stats", "tinv_server_destroy"]
@@ -107,6 +107,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
             lib.tinv_solve_noalloc.restype = ctypes.c_int
             lib.tinv_orth.argtypes = [I64, I64, P, I64, P, I64, P, P, ctypes.POINTER(Opts)]
             lib.tinv_orth.restype = ctypes.c_int
+            lib.tinv_split.argtypes = [I64, P, P, P, P, ctypes.POINTER(Opts)]
+            lib.tinv_split.restype = ctypes.c_int
+            lib.tinv_eig.argtypes = [I64, P, P, P, P, I64, P, P, P, ctypes.POINTER(Opts)]
+            lib.tinv_eig.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -314,6 +318,48 @@ def bisect_batch_device(ns, off_de, d, e, w, **kw):
     o = _opts(device=True, stream=_stream_of(d), **kw)
     return _check(load().tinv_bisect_batch(len(ns), _ptr(ns), _ptr(off_de), _ptr(d), _ptr(e),
                                            _ptr(w), ctypes.byref(o)), "tinv_bisect_batch")
+
+
+def split(d, e, **kw):
+    """Unreduced blocks of T (host arrays): one past the last row of each block."""
+    d, e = _f64(d), _f64(e)
+    n = len(d)
+    isplit = np.zeros(max(n, 1), dtype=np.int64)
+    nb = ctypes.c_int64(0)
+    _check(load().tinv_split(n, _ptr(d), _ptr(e), _ptr(isplit), ctypes.byref(nb),
+                             ctypes.byref(_opts(**kw))), "tinv_split")
+    return isplit[:nb.value].copy()
+
+
+def eig(d, e, method="cwy", seed=0, j0=0, ldz=None, iters=None, **kw):
+    """All eigenpairs of T split into unreduced blocks (host arrays).  Returns
+    (w, Z, iblock, isplit, info): Z is n x n (column j the eigenvector of w[j])."""
+    d, e = _f64(d), _f64(e)
+    n = len(d)
+    ldz = n if ldz is None else ldz
+    w = np.zeros(max(n, 1))
+    Zb = np.zeros((max(n, 1), max(ldz, 1)))  # row j = column j of the column-major result
+    iblock = np.zeros(max(n, 1), dtype=np.int64)
+    isplit = np.zeros(max(n, 1), dtype=np.int64)
+    nb = ctypes.c_int64(0)
+    o = _opts(method, seed, j0, iters=_ptr(iters), **kw)
+    info = _check(load().tinv_eig(n, _ptr(d), _ptr(e), _ptr(w), _ptr(Zb), ldz, _ptr(iblock),
+                                  _ptr(isplit), ctypes.byref(nb), ctypes.byref(o)), "tinv_eig")
+    Z = np.asfortranarray(Zb[:n, :n].T) if n else np.zeros((0, 0))
+    return w[:n], Z, iblock[:n], isplit[:nb.value].copy(), info
+
+
+def eig_device(d, e, w, Z, iblock=None, method="cwy", seed=0, j0=0, iters=None, **kw):
+    """tinv_eig on torch CUDA tensors (float64 d[n], e[n-1], w[n], Z[n, n] whose rows are the
+    eigenvectors, int64 iblock[n]).  Synchronizes the tensors' stream.  Returns
+    (info, isplit)."""
+    n = d.numel()
+    isplit = np.zeros(max(n, 1), dtype=np.int64)
+    nb = ctypes.c_int64(0)
+    o = _opts(method, seed, j0, device=True, stream=_stream_of(d), iters=_ptr(iters), **kw)
+    info = _check(load().tinv_eig(n, _ptr(d), _ptr(e), _ptr(w), _ptr(Z), n, _ptr(iblock),
+                                  _ptr(isplit), ctypes.byref(nb), ctypes.byref(o)), "tinv_eig")
+    return info, isplit[:nb.value].copy()
 
 
 # ------------------------------------------------------------------------------------------

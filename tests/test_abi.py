@@ -128,6 +128,35 @@ def test_bisect_argument_checks(lib):
     assert lib.tinv_bisect_batch(70000, P(big), P(big), P(d), P(e), P(w), None) == -106
 
 
+def test_split_and_eig_argument_checks(lib):
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    d, e, w = np.zeros(3), np.ones(2), np.zeros(3)
+    Z = np.zeros(9)
+    isplit = np.zeros(3, dtype=np.int64)
+    nb = ctypes.c_int64(-7)
+    assert lib.tinv_split(-1, None, None, None, ctypes.byref(nb), None) == -1
+    assert lib.tinv_split(0, None, None, None, ctypes.byref(nb), None) == 0 and nb.value == 0
+    assert lib.tinv_split(3, None, P(e), P(isplit), ctypes.byref(nb), None) == -2
+    assert lib.tinv_split(3, P(d), None, P(isplit), ctypes.byref(nb), None) == -3
+    assert lib.tinv_split(3, P(d), P(e), None, ctypes.byref(nb), None) == -4
+    assert lib.tinv_split(3, P(d), P(e), P(isplit), None, None) == -5
+    assert lib.tinv_split(3, P(d), P(np.array([1.0, np.inf])), P(isplit), ctypes.byref(nb), None) == -3
+    assert lib.tinv_eig(-1, None, None, None, None, 0, None, None, None, None) == -1
+    assert lib.tinv_eig(0, None, None, None, None, 0, None, None, ctypes.byref(nb), None) == 0
+    assert nb.value == 0
+    assert lib.tinv_eig(3, None, P(e), P(w), P(Z), 3, None, None, None, None) == -2
+    assert lib.tinv_eig(3, P(d), None, P(w), P(Z), 3, None, None, None, None) == -3
+    assert lib.tinv_eig(3, P(d), P(e), None, P(Z), 3, None, None, None, None) == -4
+    assert lib.tinv_eig(3, P(d), P(e), P(w), None, 3, None, None, None, None) == -5
+    assert lib.tinv_eig(3, P(d), P(e), P(w), P(Z), 2, None, None, None, None) == -6
+    assert lib.tinv_eig(3, P(np.array([0.0, np.nan, 1.0])), P(e), P(w), P(Z), 3, None, None,
+                        None, None) == -2
+    o = binding.Opts()
+    lib.tinv_opts_default(ctypes.byref(o))
+    o.method = 7
+    assert lib.tinv_eig(3, P(d), P(e), P(w), P(Z), 3, None, None, None, ctypes.byref(o)) == -10
+
+
 def test_server_config_and_null_checks(lib):
     c = binding.ServerCfg()
     lib.tinv_server_cfg_default(ctypes.byref(c))
