@@ -206,6 +206,30 @@ int tinv_eig(int64_t n, const double* d, const double* e, double* w, double* Z, 
              int64_t* iblock, int64_t* isplit, int64_t* nblock, const tinv_opts* o);
 
 /*
+ * tinv_bdsvd -- singular triplets of an upper bidiagonal B (diagonal a[n], superdiagonal b[n-1])
+ * by this inverse iteration applied to B's Golub-Kahan form (singular vectors of a bidiagonal
+ * matrix are named as a further use of the method in Sec. 6): T_GK of order 2n has zero diagonal
+ * and off-diagonal (a_1, b_1, a_2, b_2, ..., a_n); its eigenvalues are +-sigma_i and the
+ * eigenvector of +sigma is (v_1, u_1, ..., v_n, u_n)/sqrt(2).  The n largest eigenvalues of T_GK
+ * come from bisection (tinv_bisect), their eigenvectors from tinv_ex with the chosen method, and
+ * each vector's even and odd entries, scaled to unit length separately (a half that is all zero
+ * stays zero), give v_j and u_j.
+ *   s     : [n] receives the singular values, ascending.
+ *   U, V  : n x n, column-major, leading dimensions ldu, ldv >= n: B v_j = s_j u_j and
+ *           B^T u_j = s_j v_j.  Rows n .. ld-1 of each column are not written.
+ *   o     : method, seed, j0 (keys of the start vectors of T_GK's eigenvectors, as tinv_ex),
+ *           max_team and grid_ctas apply; o->iters, if given, receives the n sweep counts;
+ *           workspace, counters and phase_ms are not used.
+ * A zero singular value (a singular B) has a two-dimensional eigenspace in T_GK whose vectors
+ * need not split into a v and a u of equal weight; its columns are then not reliable.
+ * a, b, s, U, V and o->iters follow o->device_ptrs; the call synchronizes o->stream.
+ * Returns 0, -k for invalid argument k (n = 1, a = 2, b = 3, s = 4, U = 5, ldu = 6, V = 7,
+ * ldv = 8, method = 9), the number of non-converged vectors (> 0), or a runtime error code.
+ */
+int tinv_bdsvd(int64_t n, const double* a, const double* b, double* s, double* U, int64_t ldu,
+               double* V, int64_t ldv, const tinv_opts* o);
+
+/*
  * tinv_plan -- step a1/a2 alone (Sec. 2.1; Alg. 4): ||T||_1, the cluster
  * tolerance, the convergence threshold and the cluster head of every eigenvalue.
  *   wp    : [m] perturbed shifts w' (coincident approximations are separated by 10 eps |w|).

@@ -230,6 +230,45 @@ def eig_split(d, e, method: str = "cwy", seed: int = 0, j0: int = 0):
     return w, Z, iblock, isplit, info
 
 
+def golub_kahan(a, b):
+    """The Golub-Kahan form of the upper bidiagonal B (diagonal a[n], superdiagonal b[n-1]):
+    the symmetric tridiagonal T_GK of order 2n with zero diagonal and off-diagonal
+    (a_1, b_1, a_2, b_2, ..., a_n).  Its eigenvalues are +-sigma_i; for +sigma the eigenvector
+    is (v_1, u_1, v_2, u_2, ..., v_n, u_n) / sqrt(2) with B v = sigma u, B^T u = sigma v."""
+    a, b = _f64(a), _f64(b)
+    n = len(a)
+    e2 = np.zeros(max(2 * n - 1, 0))
+    e2[0::2] = a
+    e2[1::2] = b
+    return np.zeros(2 * n), e2
+
+
+def bdsvd(a, b, method: str = "cwy", seed: int = 0, j0: int = 0):
+    """Singular triplets of the upper bidiagonal B by inverse iteration on T_GK (the paper's
+    Sec. 6 names singular vectors of a bidiagonal matrix as a further use of the method):
+    s = the n largest eigenvalues of T_GK by bisection (ascending), z_j the eigenvector of s_j
+    from `tinv` with the given method, seed and j0; v_j = the even entries of z_j and u_j = the
+    odd ones, each scaled to unit 2-norm (left as zeros if they are all zero).  Returns
+    (s, U, V, info)."""
+    n = len(a)
+    d2, e2 = golub_kahan(a, b)
+    if n == 0:
+        return np.zeros(0), np.zeros((0, 0)), np.zeros((0, 0)), 0
+    w2 = bisect(d2, e2)
+    s = w2[n:].copy()
+    Z, info, _, _, _ = tinv(d2, e2, s, method=method, seed=seed, j0=j0)
+    V = np.array(Z[0::2, :], order="F")
+    U = np.array(Z[1::2, :], order="F")
+    for j in range(n):
+        nv = np.sqrt(np.sum(V[:, j] * V[:, j]))
+        nu = np.sqrt(np.sum(U[:, j] * U[:, j]))
+        if nv > 0:
+            V[:, j] = V[:, j] / nv
+        if nu > 0:
+            U[:, j] = U[:, j] / nu
+    return s, U, V, info
+
+
 def jacobi(A):
     """Cyclic Jacobi: returns (ascending eigenvalues, eigenvectors as columns)."""
     A = np.asfortranarray(A, dtype=np.float64).copy(order="F")

@@ -26,7 +26,8 @@ ERRORS = {-101: "ENOMEM", -102: "ECUDA", -103: "ETIMEDOUT", -104: "EAGAIN", -105
 # every function include/tinv.h declares
 EXPORTS = ["tinv_opts_default", "tinv_strerror", "tinv_version", "tinv", "tinv_ex",
            "tinv_workspace_size", "tinv_batch", "tinv_batch_workspace_size", "tinv_bisect",
-           "tinv_bisect_batch", "tinv_split", "tinv_eig", "tinv_plan",
+           "tinv_bisect_batch", "tinv_split", "tinv_eig", "tinv_bdsvd",
+           "tinv_plan",
            "tinv_lu", "tinv_solve", "tinv_solve_noalloc", "tinv_orth",
            "tinv_server_cfg_default", "tinv_server_create", "tinv_submit", "tinv_poll",
            "tinv_wait", "tinv_cancel", "tinv_server_stats", "tinv_server_destroy"]
@@ -111,6 +112,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             lib.tinv_split.restype = ctypes.c_int
             lib.tinv_eig.argtypes = [I64, P, P, P, P, I64, P, P, P, ctypes.POINTER(Opts)]
             lib.tinv_eig.restype = ctypes.c_int
+            lib.tinv_bdsvd.argtypes = [I64, P, P, P, P, I64, P, I64, ctypes.POINTER(Opts)]
+            lib.tinv_bdsvd.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -360,6 +363,31 @@ def eig_device(d, e, w, Z, iblock=None, method="cwy", seed=0, j0=0, iters=None, 
     info = _check(load().tinv_eig(n, _ptr(d), _ptr(e), _ptr(w), _ptr(Z), n, _ptr(iblock),
                                   _ptr(isplit), ctypes.byref(nb), ctypes.byref(o)), "tinv_eig")
     return info, isplit[:nb.value].copy()
+
+
+def bdsvd(a, b, method="cwy", seed=0, j0=0, iters=None, **kw):
+    """Singular triplets of the upper bidiagonal B (host arrays: diagonal a[n], superdiagonal
+    b[n-1]).  Returns (s, U, V, info) with s ascending and B V = U diag(s)."""
+    a, b = _f64(a), _f64(b)
+    n = len(a)
+    s = np.zeros(max(n, 1))
+    Ub = np.zeros((max(n, 1), max(n, 1)))  # row j = column j
+    Vb = np.zeros((max(n, 1), max(n, 1)))
+    o = _opts(method, seed, j0, iters=_ptr(iters), **kw)
+    info = _check(load().tinv_bdsvd(n, _ptr(a), _ptr(b), _ptr(s), _ptr(Ub), n, _ptr(Vb), n,
+                                    ctypes.byref(o)), "tinv_bdsvd")
+    if n == 0:
+        return np.zeros(0), np.zeros((0, 0)), np.zeros((0, 0)), info
+    return s[:n], np.asfortranarray(Ub.T), np.asfortranarray(Vb.T), info
+
+
+def bdsvd_device(a, b, s, U, V, method="cwy", seed=0, j0=0, **kw):
+    """tinv_bdsvd on torch CUDA tensors (float64 a[n], b[n-1], s[n], U[n, n] and V[n, n] whose
+    rows are the singular vectors).  Synchronizes the tensors' stream.  Returns info."""
+    n = a.numel()
+    o = _opts(method, seed, j0, device=True, stream=_stream_of(a), **kw)
+    return _check(load().tinv_bdsvd(n, _ptr(a), _ptr(b), _ptr(s), _ptr(U), n, _ptr(V), n,
+                                    ctypes.byref(o)), "tinv_bdsvd")
 
 
 # ------------------------------------------------------------------------------------------

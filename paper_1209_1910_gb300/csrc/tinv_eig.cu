@@ -375,7 +375,8 @@ extern "C" int tinv_eig(int64_t n, const double* d, const double* e, double* w, 
             if (ce == cudaSuccess && !dev) {
                 ce = cudaMemcpyAsync(w, pw, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st);
                 if (ce == cudaSuccess)
-                    ce = cudaMemcpyAsync(Z, pz, (size_t)(n * ldz) * sizeof(double), cudaMemcpyDeviceToHost, st);
+                    ce = cudaMemcpy2DAsync(Z, (size_t)ldz * sizeof(double), pz, (size_t)ldz * sizeof(double),
+                                           (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDeviceToHost, st);
                 if (ce == cudaSuccess && iblock)
                     ce = cudaMemcpyAsync(iblock, pib, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
                 if (ce == cudaSuccess && op.iters)

@@ -157,6 +157,27 @@ def test_split_and_eig_argument_checks(lib):
     assert lib.tinv_eig(3, P(d), P(e), P(w), P(Z), 3, None, None, None, ctypes.byref(o)) == -10
 
 
+def test_bdsvd_argument_checks(lib):
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    a, b, s = np.ones(3), np.ones(2), np.zeros(3)
+    U, V = np.zeros(9), np.zeros(9)
+    assert lib.tinv_bdsvd(-1, None, None, None, None, 0, None, 0, None) == -1
+    assert lib.tinv_bdsvd(0, None, None, None, None, 0, None, 0, None) == 0
+    assert lib.tinv_bdsvd(3, None, P(b), P(s), P(U), 3, P(V), 3, None) == -2
+    assert lib.tinv_bdsvd(3, P(a), None, P(s), P(U), 3, P(V), 3, None) == -3
+    assert lib.tinv_bdsvd(3, P(a), P(b), None, P(U), 3, P(V), 3, None) == -4
+    assert lib.tinv_bdsvd(3, P(a), P(b), P(s), None, 3, P(V), 3, None) == -5
+    assert lib.tinv_bdsvd(3, P(a), P(b), P(s), P(U), 2, P(V), 3, None) == -6
+    assert lib.tinv_bdsvd(3, P(a), P(b), P(s), P(U), 3, None, 3, None) == -7
+    assert lib.tinv_bdsvd(3, P(a), P(b), P(s), P(U), 3, P(V), 2, None) == -8
+    assert lib.tinv_bdsvd(3, P(np.array([1.0, np.nan, 1.0])), P(b), P(s), P(U), 3, P(V), 3,
+                          None) == -2
+    o = binding.Opts()
+    lib.tinv_opts_default(ctypes.byref(o))
+    o.method = 5
+    assert lib.tinv_bdsvd(3, P(a), P(b), P(s), P(U), 3, P(V), 3, ctypes.byref(o)) == -9
+
+
 def test_server_config_and_null_checks(lib):
     c = binding.ServerCfg()
     lib.tinv_server_cfg_default(ctypes.byref(c))
