@@ -44,11 +44,19 @@ WORKLOADS = {
     "batch512": "512 problems, n log-uniform [64,4096] (seed 2), even U[-1,1] d,e, odd glued "
                 "W21+ (glue 1e-10); all eigenvectors of every problem, one tinv_batch call",
 }
+WORKLOADS["split4200"] = ("glued Wilkinson 200 x W21+ with exactly zero glue, n=4200: all eigenpairs "
+                          "from (d, e) by tinv_eig (200 unreduced blocks of 21)")
+WORKLOADS["bidiag2000"] = ("upper bidiagonal n=2000 (seed 1), a = +-U[1,2), b = U[-1/2,1/2): all "
+                           "singular triplets by tinv_bdsvd (Golub-Kahan form of order 4000, 76 "
+                           "clusters, the largest 583)")
 WORKLOADS["serve"] = ("Poisson request stream (seed 3), n log-uniform [128,4096], 70% U[-1,1] / 30% "
                       "glued W21+; eigenvalues computed by the server; offered at 0.5x, 0.9x and "
                       "1.3x the saturated rate")
 # kernels one call enqueues: plan (2), LU (2), first sweep, cluster kernel, CWY finalize, status
 LAUNCHES = {"cwy": 8, "mgs": 7}
+# the drivers add: split marks, bisection, scatter (tinv_eig); Golub-Kahan form, bisection,
+# half split (tinv_bdsvd)
+DRIVER_EXTRA_LAUNCHES = {"split4200": 3, "bidiag2000": 3}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (vector and tensor alike), TFLOP/s
 # DRAM bytes (read + write) of one cluster-kernel launch, from ncu on the current kernels
 # (profiles/launches_glued4200_cwy.md); None where no capture exists
@@ -187,6 +195,8 @@ def reference_arm(args):
     elif args.workload == "serve":
         probs = serve_requests()[0]
         sample = lambda: cpu_sample_batch(args.method, probs, stride=16)
+    elif args.workload in DRIVER_EXTRA_LAUNCHES:
+        sample = lambda: cpu_sample_driver(args.workload, args.method)
     else:
         d, e, w = inputs.workload(args.workload)
         sample = lambda: cpu_sample(args.workload, args.method, d, e, w)
@@ -201,17 +211,63 @@ def reference_arm(args):
     el = time.perf_counter() - t0
     value = float(statistics.mean(vals))
     out = {
-        "impl": "reference", "metric": "eigvecs_per_s", "value": value, "unit": "eigvec/s",
+        "impl": "reference", "metric": driver_metric(args.workload)[0], "value": value,
+        "unit": driver_metric(args.workload)[1],
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "method": args.method},
-        "cpu_baseline": {"value": value, "unit": "eigvec/s", "cores": 1, "kind": "oracle",
-                         "sample": desc},
-        "e2e": {"value": value, "unit": "eigvec/s", "h2d_bytes_per_step": 0,
+        "cpu_baseline": {"value": value, "unit": driver_metric(args.workload)[1], "cores": 1,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": driver_metric(args.workload)[1], "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
+
+
+def driver_metric(workload: str):
+    if workload == "bidiag2000":
+        return "singular_triplets_per_s", "triplet/s"
+    return "eigvecs_per_s", "eigvec/s"
+
+
+def driver_inputs(workload: str):
+    if workload == "split4200":
+        return inputs.glued_wilkinson(200, 0.0)
+    return inputs.bidiagonal(2000, seed=1)
+
+
+def cpu_sample_driver(workload: str, method: str):
+    """Bounded oracle sample for the driver workloads: the whole split driver on the zero-glue
+    matrix (200 blocks of order 21), or, for the bidiagonal workload, bisection of its
+    Golub-Kahan form plus inverse iteration for the first clusters of at most 200 members, in
+    order, up to ~600 triplets (the half split is O(n) per triplet)."""
+    import oracle
+
+    oracle.build()
+    a, b = driver_inputs(workload)
+    if workload == "split4200":
+        t0 = time.perf_counter()
+        oracle.eig_split(a, b, method=method)
+        return len(a) / (time.perf_counter() - t0), "oracle split driver on the whole matrix"
+    n = len(a)
+    t0 = time.perf_counter()
+    d2, e2 = oracle.golub_kahan(a, b)
+    s = oracle.bisect(d2, e2)[n:]
+    head = oracle.plan(d2, e2, s)[1]
+    starts = np.flatnonzero(head == np.arange(len(head)))
+    ends = np.r_[starts[1:], len(head)]
+    tot = 0
+    for c0, c1 in zip(starts, ends):
+        if tot >= 600:
+            break
+        if c1 - c0 > 200:
+            continue
+        oracle.tinv(d2, e2, s[c0:c1], method, j0=int(c0))
+        tot += c1 - c0
+    dt = time.perf_counter() - t0
+    return tot / dt, ("oracle: bisection of the order-%d Golub-Kahan form, then %d triplets "
+                      "(the first whole clusters of <= 200 members)" % (2 * n, tot))
 
 
 def batch_arm(args):
@@ -565,12 +621,164 @@ def serve_arm(args, count=128, hi=4096):
     print(json.dumps(out), flush=True)
 
 
+def driver_arm(args):
+    """tinv_eig (split4200) or tinv_bdsvd (bidiag2000) on device arrays, one call per step; the
+    calls synchronize their stream (block table, merge order), so a step is the whole call."""
+    import torch
+
+    from paper_1209_1910_gb300 import binding, build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return  # one problem: replicas would repeat it, rank 0 reports
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    build.build()
+    binding.load()
+    a, b = driver_inputs(args.workload)
+    n = len(a)
+    ta, tb = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (a, b))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    phase = np.zeros(4, dtype=np.float32)
+    iters = torch.zeros(n, dtype=torch.int32, device=dev)
+    if args.workload == "split4200":
+        tw = torch.zeros(n, dtype=torch.float64, device=dev)
+        tZ = torch.zeros((n, n), dtype=torch.float64, device=dev)
+        tib = torch.zeros(n, dtype=torch.int64, device=dev)
+
+        def step(with_phase):
+            kw = {"phase_ms": phase.ctypes.data} if with_phase else {}
+            return binding.eig_device(ta, tb, tw, tZ, tib, method=args.method, iters=iters,
+                                      **kw)[0]
+    else:
+        ts = torch.zeros(n, dtype=torch.float64, device=dev)
+        tU = torch.zeros((n, n), dtype=torch.float64, device=dev)
+        tV = torch.zeros((n, n), dtype=torch.float64, device=dev)
+
+        def step(with_phase):
+            kw = {"phase_ms": phase.ctypes.data} if with_phase else {}
+            return binding.bdsvd_device(ta, tb, ts, tU, tV, method=args.method,
+                                        iters=iters.data_ptr(), **kw)
+
+    for _ in range(args.warmup):
+        if step(False) != 0:
+            raise RuntimeError("warm-up run reported non-converged vectors")
+    torch.cuda.synchronize()
+    sampler = ClockSampler(None)
+    st = torch.cuda.current_stream(dev)
+    step_ms, chain_ms = [], []
+    sampler.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        info = step(True)
+        e1.record(st)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        chain_ms.append(float(phase[3]))
+    torch.cuda.synchronize()
+    sampler.stop()
+    total_ms = float(sum(step_ms))
+    value = n * args.steps / (total_ms * 1e-3)
+    eps = float(np.finfo(np.float64).eps)
+    it = iters.cpu().numpy()
+    if args.workload == "split4200":
+        Z = tZ.T
+        R = ta[:, None] * Z
+        R[:-1] += tb[:, None] * Z[1:]
+        R[1:] += tb[:, None] * Z[:-1]
+        R -= Z * tw[None, :]
+        nrm = float(np.max(np.abs(a) + np.r_[0, np.abs(b)] + np.r_[np.abs(b), 0]))
+        res = float(R.abs().max()) / (n * eps * nrm)
+        G = tZ @ tZ.T
+        G.diagonal().sub_(1.0)
+        check = {"nonconverged": int(info), "residual_ratio": res,
+                 "orth_ratio": float(G.abs().max()) / (n * eps)}
+        # algorithmic CWY flops per block (each block is its own problem with its own plan)
+        w_h, iblk = tw.cpu().numpy(), tib.cpu().numpy()
+        blocks = np.r_[0, binding.split(a, b)]
+        flops = 0.0
+        for bi in range(len(blocks) - 1):
+            s0, s1 = int(blocks[bi]), int(blocks[bi + 1])
+            cols = np.flatnonzero(iblk == bi)
+            hb = binding.plan(a[s0:s1], b[s0:s1 - 1], w_h[cols])[1]
+            flops += algorithmic_flops(s1 - s0, hb, it[cols], args.method)
+        del R, G
+    else:
+        Bv = ta[:, None] * tV.T
+        Bv[:-1] += tb[:, None] * tV.T[1:]
+        Rv = Bv - tU.T * ts[None, :]
+        nrm = float(np.max(np.abs(a) + np.r_[0, np.abs(b)]))
+        res = float(Rv.abs().max()) / (n * eps * nrm)
+        GU = tU @ tU.T
+        GU.diagonal().sub_(1.0)
+        GV = tV @ tV.T
+        GV.diagonal().sub_(1.0)
+        check = {"nonconverged": int(info), "residual_ratio": res,
+                 "orth_ratio_u": float(GU.abs().max()) / (n * eps),
+                 "orth_ratio_v": float(GV.abs().max()) / (n * eps)}
+        d2 = np.zeros(2 * n)
+        e2 = np.zeros(2 * n - 1)
+        e2[0::2], e2[1::2] = a, b
+        s_h = ts.cpu().numpy()
+        hb = binding.plan(d2, e2, s_h)[1]
+        flops = algorithmic_flops(2 * n, hb, it, args.method)
+        del Bv, Rv, GU, GV
+    kern_ms = float(statistics.mean(chain_ms))
+    achieved = flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else 0.0
+    metric, unit = driver_metric(args.workload)
+    out = {
+        "metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "method": args.method,
+                   "parallelism": "single", "inputs": "resident in HBM",
+                   "l2": "flushed by a 512 MiB write between steps"},
+        "check": check,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_chain", "kernel_ms": kern_ms, "flops_per_launch": flops,
+                     "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (derived in the design notes)",
+                     "phase_ms": {"plan": float(phase[0]), "lu": float(phase[1]),
+                                  "first": float(phase[2]), "chain": float(phase[3])}},
+        "gpu_launches": (LAUNCHES[args.method] + DRIVER_EXTRA_LAUNCHES[args.workload]) * args.steps,
+        "clocks": sampler.summary(),
+    }
+    if not args.no_e2e:
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+        ha, hb2 = pin(a), pin(b)
+        call = (lambda: binding.eig(ha, hb2, method=args.method)) if args.workload == "split4200" \
+            else (lambda: binding.bdsvd(ha, hb2, method=args.method))
+        call()
+        el = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            call()
+            el += time.perf_counter() - t0
+        nout = 1 if args.workload == "split4200" else 2
+        out["e2e"] = {"value": n * args.steps / el, "unit": unit,
+                      "h2d_bytes_per_step": (2 * n - 1) * 8,
+                      "d2h_bytes_per_step": nout * n * n * 8 + n * 8 + 8}
+    if not args.no_cpu_baseline:
+        v, desc = cpu_sample_driver(args.workload, args.method)
+        out["cpu_baseline"] = {"value": v, "unit": unit, "cores": 1, "kind": "oracle",
+                               "sample": desc}
+    print(json.dumps(out), flush=True)
+
+
 def ours_arm(args):
     import torch
     if args.workload == "batch512":
         return batch_arm(args)
     if args.workload == "serve":
         return serve_arm(args)
+    if args.workload in DRIVER_EXTRA_LAUNCHES:
+        return driver_arm(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -196,7 +196,8 @@ int tinv_split(int64_t n, const double* d, const double* e, int64_t* isplit, int
  *   iblock : optional [n]: the block (0-based) of each eigenvalue.
  *   isplit, nblock : optional, as tinv_split (always host memory).
  *   o      : method, seed, j0, max_team, grid_ctas apply; o->iters, if given, receives the sweep
- *            counts in the order of w; workspace, counters and phase_ms are not used.
+ *            counts in the order of w; o->phase_ms, if given, receives the device times of the
+ *            inverse-iteration launches as for tinv_batch; workspace and counters are not used.
  * d, e, w, Z, iblock and o->iters are host or device memory following o->device_ptrs.  The call
  * synchronizes o->stream (the block table and the merge order are formed on the host).
  * Returns 0, -k for invalid argument k (n = 1, d = 2, e = 3, w = 4, Z = 5, ldz = 6, method = 10),
@@ -219,7 +220,8 @@ int tinv_eig(int64_t n, const double* d, const double* e, double* w, double* Z, 
  *           B^T u_j = s_j v_j.  Rows n .. ld-1 of each column are not written.
  *   o     : method, seed, j0 (keys of the start vectors of T_GK's eigenvectors, as tinv_ex),
  *           max_team and grid_ctas apply; o->iters, if given, receives the n sweep counts;
- *           workspace, counters and phase_ms are not used.
+ *           o->phase_ms, if given, receives the device times of the inverse-iteration launches
+ *           as for tinv_ex; workspace and counters are not used.
  * A zero singular value (a singular B) has a two-dimensional eigenspace in T_GK whose vectors
  * need not split into a v and a u of equal weight; its columns are then not reliable.
  * a, b, s, U, V and o->iters follow o->device_ptrs; the call synchronizes o->stream.

@@ -187,7 +187,6 @@ extern "C" int tinv_bdsvd(int64_t n, const double* a, const double* b, double* s
             to.stream = (void*)st;
             to.info = (int64_t*)binfo.p;
             to.iters = op.iters ? (dev ? op.iters : (int32_t*)bit.p) : nullptr;
-            to.phase_ms = nullptr;
             to.counters = nullptr;
             to.workspace = nullptr;
             to.workspace_bytes = 0;

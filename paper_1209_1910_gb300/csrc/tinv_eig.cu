@@ -329,7 +329,6 @@ extern "C" int tinv_eig(int64_t n, const double* d, const double* e, double* w, 
             bo.workspace_bytes = 0;
             bo.iters = (int32_t*)bitp.p;
             bo.info = nullptr;
-            bo.phase_ms = nullptr;
             bo.counters = nullptr;
             bo.table_ready = 0;
             rc = batch_enqueue_device(nb, size.data(), start.data(), offz.data(), nullptr, pd, pe,

@@ -39,6 +39,15 @@ def glued_wilkinson(g: int, delta: float = 1e-10):
     return d, e
 
 
+def bidiagonal(n: int, seed: int = 1):
+    """Upper bidiagonal B for the singular-vector workload: diagonal a_i = +-U[1, 2) (random
+    sign), superdiagonal b_i ~ U[-1/2, 1/2) (|b_i / a_{i+1}| <= 1/2 keeps B well conditioned)."""
+    g = rng(seed)
+    a = g.uniform(1.0, 2.0, n) * g.choice([-1.0, 1.0], n)
+    b = g.uniform(-0.5, 0.5, max(n - 1, 0))
+    return a, b
+
+
 def toeplitz(n: int, a: float, b: float):
     """Tridiagonal Toeplitz matrix: diagonal a, off-diagonal b (Type 2 has a = b = 1)."""
     return np.full(n, float(a)), np.full(max(n - 1, 0), float(b))
