@@ -93,15 +93,132 @@ __global__ void __launch_bounds__(kBisectThreads) k_bisect(const int64_t* __rest
     W[off + k] = __dmul_rn(0.5, __dadd_rn(lo, hi));
 }
 
+// The same bisection with L = 2^S lanes per eigenvalue, for launches with too few eigenvalues to
+// fill the GPU.  The next S halvings of the bracket can only visit the 2^S - 1 midpoints of a
+// binary tree (node j's children bisect its two halves); lane j < L - 1 computes node j's
+// midpoint by the same rounding formula along its path from the current bracket and the Sturm
+// count there, all lanes in parallel.  The group then takes the S steps exactly as k_bisect
+// does (same termination tests in the same order, the count of the node it reaches), so the
+// result is bit-identical to k_bisect's; only the counts of nodes off the path are wasted.
+template <int L>
+__global__ void __launch_bounds__(kBisectThreads) k_bisect_tree(const int64_t* __restrict__ ns,
+                                                               const int64_t* __restrict__ offs,
+                                                               int64_t n1, const double* __restrict__ D,
+                                                               const double* __restrict__ E,
+                                                               double* __restrict__ W)
+{
+    constexpr int S = (L == 4) ? 2 : (L == 8) ? 3 : (L == 16) ? 4 : 5;
+    const int64_t q = blockIdx.y;
+    const int64_t n = ns ? ns[q] : n1;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = gt / L;  // the whole group of L lanes shares k
+    const int g = (int)(gt % L);
+    if (k >= n) return;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
+    const int64_t off = offs ? offs[q] : 0;
+    const double* d = D + off;
+    const double* e = E + off;
+    double glo = INFINITY, ghi = -INFINITY, emax2 = 0.0, onenrm = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double r = 0.0;
+        if (i > 0) r = __dadd_rn(r, fabs(e[i - 1]));
+        if (i < n - 1) {
+            r = __dadd_rn(r, fabs(e[i]));
+            emax2 = dmax_(emax2, __dmul_rn(e[i], e[i]));
+        }
+        glo = dmin_(glo, __dsub_rn(d[i], r));
+        ghi = dmax_(ghi, __dadd_rn(d[i], r));
+        double sabs = fabs(d[i]);
+        if (i > 0) sabs = __dadd_rn(sabs, fabs(e[i - 1]));
+        if (i < n - 1) sabs = __dadd_rn(sabs, fabs(e[i]));
+        onenrm = dmax_(onenrm, sabs);
+    }
+    const double pivmin = __dmul_rn(DBL_MIN, dmax_(1.0, emax2));
+    const double bnd = dmax_(fabs(glo), fabs(ghi));
+    const double widen = __dadd_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, kEpsB), bnd), (double)n),
+                                   __dmul_rn(2.0, pivmin));
+    double lo = __dsub_rn(glo, widen), hi = __dadd_rn(ghi, widen);
+    const double tol_abs = __dmul_rn(kEpsB, onenrm);
+    int it = 0;
+    for (;;) {
+        // node g of the tree: follow the bits of g + 1 below its leading one (0 = left half)
+        int64_t cnt = 0;
+        if (g < L - 1) {
+            const unsigned path = (unsigned)g + 1u;
+            const int depth = 31 - __clz(path);
+            double blo = lo, bhi = hi;
+            for (int dd = depth - 1; dd >= 0; --dd) {
+                const double m = __dmul_rn(0.5, __dadd_rn(blo, bhi));
+                if ((path >> dd) & 1u)
+                    blo = m;
+                else
+                    bhi = m;
+            }
+            cnt = sturm_count(n, d, e, __dmul_rn(0.5, __dadd_rn(blo, bhi)), pivmin);
+        }
+        // the S steps of the sequential bisection, with the counts of the nodes on its path
+        bool done = false;
+        int j = 0;
+        for (int lev = 0; lev < S; ++lev) {
+            if (it >= kMaxBisect) {
+                done = true;
+                break;
+            }
+            const double tol = dmax_(__dmul_rn(__dmul_rn(2.0, kEpsB), dmax_(fabs(lo), fabs(hi))), tol_abs);
+            if (__dsub_rn(hi, lo) <= tol) {
+                done = true;
+                break;
+            }
+            const double mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
+            if (mid <= lo || mid >= hi) {
+                done = true;
+                break;
+            }
+            const long long cj = __shfl_sync(gmask, (long long)cnt, j, L);
+            if (cj <= k) {
+                lo = mid;
+                j = 2 * j + 2;
+            } else {
+                hi = mid;
+                j = 2 * j + 1;
+            }
+            ++it;
+        }
+        if (done) break;
+    }
+    if (g == 0) W[off + k] = __dmul_rn(0.5, __dadd_rn(lo, hi));
+}
+
 }  // namespace
+
+// Lanes per eigenvalue for a launch of nprob x nmax eigenvalues: the largest of 32, 16, 8, 4 that
+// keeps the launch within about two warps per SM sub-partition, else 1 (plain bisection).
+int bisect_lanes(int64_t nprob, int64_t nmax)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t target = (int64_t)(sms > 0 ? sms : 1) * 4 * 32 * 2;
+    const int64_t eig = nprob * nmax;
+    for (int L = 32; L >= 4; L >>= 1)
+        if (eig * L <= target) return L;
+    return 1;
+}
 
 // nprob problems; ns/offs are DEVICE arrays (or null for one problem of order n1 at offset 0).
 cudaError_t launch_bisect(int64_t nprob, const int64_t* ns, const int64_t* offs, int64_t n1,
                           int64_t nmax, const double* d, const double* e, double* w, cudaStream_t st)
 {
     if (nprob <= 0 || nmax <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)((nmax + kBisectThreads - 1) / kBisectThreads), (unsigned)nprob);
-    k_bisect<<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, d, e, w);
+    const int L = bisect_lanes(nprob, nmax);
+    const dim3 grid((unsigned)((nmax * L + kBisectThreads - 1) / kBisectThreads), (unsigned)nprob);
+    switch (L) {
+    case 32: k_bisect_tree<32><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, d, e, w); break;
+    case 16: k_bisect_tree<16><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, d, e, w); break;
+    case 8: k_bisect_tree<8><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, d, e, w); break;
+    case 4: k_bisect_tree<4><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, d, e, w); break;
+    default: k_bisect<<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, d, e, w); break;
+    }
     return cudaGetLastError();
 }
 
