@@ -413,19 +413,26 @@ def batch_arm(args):
             with torch.cuda.graph(graph, stream=gs):
                 binding.tinv_batch_device(ns, off_de, off_z, td, te, tw, tz, method=args.method,
                                           info=info, workspace=ws, iters=iters, table_ready=1)
-        graph.replay()
+        # replay() launches on the current stream: make it gs, the stream the events are on
+        with torch.cuda.stream(gs):
+            graph.replay()
         torch.cuda.synchronize()
         gms = []
         for _ in range(2):
             flush.zero_()
+            info.fill_(-1)
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            a.record(gs)
-            graph.replay()
-            b.record(gs)
+            with torch.cuda.stream(gs):
+                a.record(gs)
+                graph.replay()
+                b.record(gs)
             b.synchronize()
             gms.append(a.elapsed_time(b))
+            if int(info.min().item()) < 0 or int(info.max().item()) != 0:
+                raise RuntimeError("graph replay did not complete the batch (info %s)"
+                                   % info.unique().tolist())
         out["graph_replay"] = {"value": M / (statistics.mean(gms) * 1e-3), "unit": "eigvec/s",
                                "ms_per_step": statistics.mean(gms)}
         del graph
