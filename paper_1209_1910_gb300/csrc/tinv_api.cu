@@ -134,22 +134,7 @@ using namespace tinvx;
 namespace {
 
 
-int cuda_code(cudaError_t e)
-{
-    if (e == cudaSuccess) return TINV_OK;
-    if (e == cudaErrorMemoryAllocation) return TINV_ENOMEM;
-    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
-        e == cudaErrorNoKernelImageForDevice || e == cudaErrorInvalidDevice)
-        return TINV_ENODEV;
-    return TINV_ECUDA;
-}
 
-bool all_finite(const double* a, int64_t k)
-{
-    for (int64_t i = 0; i < k; ++i)
-        if (!isfinite(a[i])) return false;
-    return true;
-}
 
 bool ascending(const double* a, int64_t k)
 {
@@ -159,26 +144,6 @@ bool ascending(const double* a, int64_t k)
 }
 
 // Device allocation that is freed on scope exit (stream-ordered when a stream is given).
-struct DevBuf {
-    void* p = nullptr;
-    cudaStream_t st = nullptr;
-    bool async = false;
-    cudaError_t alloc(size_t bytes, cudaStream_t s, bool use_async)
-    {
-        st = s;
-        async = use_async;
-        if (bytes == 0) bytes = 256;
-        return async ? cudaMallocAsync(&p, bytes, st) : cudaMalloc(&p, bytes);
-    }
-    ~DevBuf()
-    {
-        if (!p) return;
-        if (async)
-            cudaFreeAsync(p, st);
-        else
-            cudaFree(p);
-    }
-};
 
 __global__ void k_finish(const int64_t* ctr, int64_t* info)
 {

@@ -21,22 +21,7 @@ namespace {
 
 constexpr int kSplitHalfThreads = 256;
 
-int code_of(cudaError_t e)
-{
-    if (e == cudaSuccess) return TINV_OK;
-    if (e == cudaErrorMemoryAllocation) return TINV_ENOMEM;
-    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
-        e == cudaErrorNoKernelImageForDevice || e == cudaErrorInvalidDevice)
-        return TINV_ENODEV;
-    return TINV_ECUDA;
-}
 
-bool finite_all(const double* x, int64_t k)
-{
-    for (int64_t i = 0; i < k; ++i)
-        if (!isfinite(x[i])) return false;
-    return true;
-}
 
 // T_GK: d2 = 0 (2n), e2 = (a_1, b_1, ..., a_n) (2n - 1).
 __global__ void k_golub_kahan(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
@@ -93,19 +78,6 @@ __global__ void __launch_bounds__(kSplitHalfThreads) k_split_halves(int64_t n, c
     }
 }
 
-struct Buf {
-    void* p = nullptr;
-    cudaStream_t st = nullptr;
-    cudaError_t alloc(size_t bytes, cudaStream_t s)
-    {
-        st = s;
-        return cudaMallocAsync(&p, bytes > 0 ? bytes : 256, s);
-    }
-    ~Buf()
-    {
-        if (p) cudaFreeAsync(p, st);
-    }
-};
 
 }  // namespace
 }  // namespace tinvx
@@ -132,8 +104,8 @@ extern "C" int tinv_bdsvd(int64_t n, const double* a, const double* b, double* s
     if (ldv < n) return -8;
     if (n > (int64_t)INT32_MAX / 4) return TINV_ENOTSUP;
     if (!op.device_ptrs) {
-        if (!finite_all(a, n)) return -2;
-        if (n > 1 && !finite_all(b, n - 1)) return -3;
+        if (!all_finite(a, n)) return -2;
+        if (n > 1 && !all_finite(b, n - 1)) return -3;
     }
     cudaStream_t st = nullptr;
     bool own = false;
@@ -147,15 +119,15 @@ extern "C" int tinv_bdsvd(int64_t n, const double* a, const double* b, double* s
     const int64_t n2 = 2 * n;
     int rc = 0;
     {
-        Buf ba, bb, bu, bv, bd2, be2, bw2, bz2, binfo, bit;
+        DevBuf ba, bb, bu, bv, bd2, be2, bw2, bz2, binfo, bit;
         const double *pa = a, *pb = b;
         double *pu = U, *pv = V;
         cudaError_t ce = cudaSuccess;
         if (!dev) {
-            ce = ba.alloc((size_t)n * sizeof(double), st);
-            if (ce == cudaSuccess) ce = bb.alloc((size_t)(n > 1 ? n - 1 : 1) * sizeof(double), st);
-            if (ce == cudaSuccess) ce = bu.alloc((size_t)(n * ldu) * sizeof(double), st);
-            if (ce == cudaSuccess) ce = bv.alloc((size_t)(n * ldv) * sizeof(double), st);
+            ce = ba.alloc((size_t)n * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = bb.alloc((size_t)(n > 1 ? n - 1 : 1) * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = bu.alloc((size_t)(n * ldu) * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = bv.alloc((size_t)(n * ldv) * sizeof(double), st, true);
             if (ce == cudaSuccess)
                 ce = cudaMemcpyAsync(ba.p, a, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st);
             if (ce == cudaSuccess && n > 1)
@@ -165,12 +137,12 @@ extern "C" int tinv_bdsvd(int64_t n, const double* a, const double* b, double* s
             pu = (double*)bu.p;
             pv = (double*)bv.p;
         }
-        if (ce == cudaSuccess) ce = bd2.alloc((size_t)n2 * sizeof(double), st);
-        if (ce == cudaSuccess) ce = be2.alloc((size_t)(n2 - 1) * sizeof(double), st);
-        if (ce == cudaSuccess) ce = bw2.alloc((size_t)n2 * sizeof(double), st);
-        if (ce == cudaSuccess) ce = bz2.alloc((size_t)(n2 * n) * sizeof(double), st);
-        if (ce == cudaSuccess) ce = binfo.alloc(sizeof(int64_t), st);
-        if (ce == cudaSuccess && op.iters && !dev) ce = bit.alloc((size_t)n * sizeof(int32_t), st);
+        if (ce == cudaSuccess) ce = bd2.alloc((size_t)n2 * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = be2.alloc((size_t)(n2 - 1) * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = bw2.alloc((size_t)n2 * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = bz2.alloc((size_t)(n2 * n) * sizeof(double), st, true);
+        if (ce == cudaSuccess) ce = binfo.alloc(sizeof(int64_t), st, true);
+        if (ce == cudaSuccess && op.iters && !dev) ce = bit.alloc((size_t)n * sizeof(int32_t), st, true);
         if (ce == cudaSuccess) {
             const unsigned g = (unsigned)((n2 + 255) / 256 < 4096 ? (n2 + 255) / 256 : 4096);
             k_golub_kahan<<<g, 256, 0, st>>>(n, pa, pb, (double*)bd2.p, (double*)be2.p);
@@ -180,7 +152,7 @@ extern "C" int tinv_bdsvd(int64_t n, const double* a, const double* b, double* s
         if (ce == cudaSuccess)
             ce = launch_bisect(1, nullptr, nullptr, n2, n2, (const double*)bd2.p, (const double*)be2.p,
                                (double*)bw2.p, st);
-        rc = code_of(ce);
+        rc = cuda_code(ce);
         if (!rc) {
             tinv_opts to = op;
             to.device_ptrs = 1;
@@ -213,7 +185,7 @@ extern "C" int tinv_bdsvd(int64_t n, const double* a, const double* b, double* s
             if (ce == cudaSuccess)
                 ce = cudaMemcpyAsync(&info, binfo.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-            rc = code_of(ce);
+            rc = cuda_code(ce);
             if (!rc) rc = info > INT32_MAX ? INT32_MAX : (int)info;
         }
     }

@@ -226,27 +226,6 @@ cudaError_t launch_bisect(int64_t nprob, const int64_t* ns, const int64_t* offs,
 
 using namespace tinvx;
 
-namespace {
-
-int code_of(cudaError_t e)
-{
-    if (e == cudaSuccess) return TINV_OK;
-    if (e == cudaErrorMemoryAllocation) return TINV_ENOMEM;
-    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
-        e == cudaErrorNoKernelImageForDevice || e == cudaErrorInvalidDevice)
-        return TINV_ENODEV;
-    return TINV_ECUDA;
-}
-
-bool finite_all(const double* a, int64_t k)
-{
-    for (int64_t i = 0; i < k; ++i)
-        if (!isfinite(a[i])) return false;
-    return true;
-}
-
-}  // namespace
-
 extern "C" int tinv_bisect_batch(int64_t nprob, const int64_t* n, const int64_t* off_de,
                                  const double* d, const double* e, double* w, const tinv_opts* o)
 {
@@ -276,8 +255,8 @@ extern "C" int tinv_bisect_batch(int64_t nprob, const int64_t* n, const int64_t*
     if (!op.device_ptrs) {
         for (int64_t q = 0; q < nprob; ++q) {
             if (n[q] == 0) continue;
-            if (!finite_all(d + off_de[q], n[q])) return -4;
-            if (n[q] > 1 && !finite_all(e + off_de[q], n[q] - 1)) return -5;
+            if (!all_finite(d + off_de[q], n[q])) return -4;
+            if (n[q] > 1 && !all_finite(e + off_de[q], n[q] - 1)) return -5;
         }
     }
     cudaStream_t st = nullptr;
@@ -332,7 +311,7 @@ extern "C" int tinv_bisect_batch(int64_t nprob, const int64_t* n, const int64_t*
         if (ce == cudaSuccess) ce = s2;
         cudaStreamDestroy(st);
     }
-    return code_of(ce);
+    return cuda_code(ce);
 }
 
 extern "C" int tinv_bisect(int64_t n, const double* d, const double* e, double* w, const tinv_opts* o)

@@ -24,22 +24,7 @@ namespace {
 constexpr int kSplitThreads = 1024;
 constexpr int64_t kBisectChunk = 65535;  // problems per bisection launch (grid.y limit)
 
-int code_of(cudaError_t e)
-{
-    if (e == cudaSuccess) return TINV_OK;
-    if (e == cudaErrorMemoryAllocation) return TINV_ENOMEM;
-    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
-        e == cudaErrorNoKernelImageForDevice || e == cudaErrorInvalidDevice)
-        return TINV_ENODEV;
-    return TINV_ECUDA;
-}
 
-bool finite_all(const double* a, int64_t k)
-{
-    for (int64_t i = 0; i < k; ++i)
-        if (!isfinite(a[i])) return false;
-    return true;
-}
 
 // ||T||_1 (max over rows of |d_i| + |e_{i-1}| + |e_i|, each row summed in that order; the
 // maximum does not depend on the order of the rows) and the negligible entries: mark[i] = 1 iff
@@ -120,27 +105,14 @@ void blocks_from_marks(int64_t n, const uint8_t* mark, std::vector<int64_t>& sta
     size.push_back(n - b0);
 }
 
-struct Buf {
-    void* p = nullptr;
-    cudaStream_t st = nullptr;
-    cudaError_t alloc(size_t bytes, cudaStream_t s)
-    {
-        st = s;
-        return cudaMallocAsync(&p, bytes > 0 ? bytes : 256, s);
-    }
-    ~Buf()
-    {
-        if (p) cudaFreeAsync(p, st);
-    }
-};
 
 // Split marks for device arrays d, e on stream st, returned in host memory.
 int split_marks(int64_t n, const double* dd, const double* de, std::vector<uint8_t>& mark, cudaStream_t st)
 {
     mark.assign((size_t)(n > 1 ? n - 1 : 1), 0);
     if (n <= 1) return 0;
-    Buf m;
-    cudaError_t ce = m.alloc((size_t)(n - 1), st);
+    DevBuf m;
+    cudaError_t ce = m.alloc((size_t)(n - 1), st, true);
     if (ce == cudaSuccess) {
         k_split<<<1, kSplitThreads, 0, st>>>(n, dd, de, (uint8_t*)m.p);
         ce = cudaGetLastError();
@@ -148,7 +120,7 @@ int split_marks(int64_t n, const double* dd, const double* de, std::vector<uint8
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(mark.data(), m.p, (size_t)(n - 1), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-    return code_of(ce);
+    return cuda_code(ce);
 }
 
 }  // namespace
@@ -171,8 +143,8 @@ extern "C" int tinv_split(int64_t n, const double* d, const double* e, int64_t* 
     if (n > 1 && !e) return -3;
     if (!isplit) return -4;
     if (!op.device_ptrs) {
-        if (!finite_all(d, n)) return -2;
-        if (n > 1 && !finite_all(e, n - 1)) return -3;
+        if (!all_finite(d, n)) return -2;
+        if (n > 1 && !all_finite(e, n - 1)) return -3;
     }
     cudaStream_t st = nullptr;
     bool own = false;
@@ -185,16 +157,16 @@ extern "C" int tinv_split(int64_t n, const double* d, const double* e, int64_t* 
     int rc = 0;
     std::vector<uint8_t> mark;
     {
-        Buf bd, be;
+        DevBuf bd, be;
         const double *pd = d, *pe = e;
         if (!op.device_ptrs) {
-            cudaError_t ce = bd.alloc((size_t)n * sizeof(double), st);
-            if (ce == cudaSuccess) ce = be.alloc((size_t)(n > 1 ? n - 1 : 1) * sizeof(double), st);
+            cudaError_t ce = bd.alloc((size_t)n * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = be.alloc((size_t)(n > 1 ? n - 1 : 1) * sizeof(double), st, true);
             if (ce == cudaSuccess)
                 ce = cudaMemcpyAsync(bd.p, d, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st);
             if (ce == cudaSuccess && n > 1)
                 ce = cudaMemcpyAsync(be.p, e, (size_t)(n - 1) * sizeof(double), cudaMemcpyHostToDevice, st);
-            rc = code_of(ce);
+            rc = cuda_code(ce);
             pd = (const double*)bd.p;
             pe = (const double*)be.p;
         }
@@ -234,8 +206,8 @@ extern "C" int tinv_eig(int64_t n, const double* d, const double* e, double* w, 
     if (!Z) return -5;
     if (ldz < n) return -6;
     if (!op.device_ptrs) {
-        if (!finite_all(d, n)) return -2;
-        if (n > 1 && !finite_all(e, n - 1)) return -3;
+        if (!all_finite(d, n)) return -2;
+        if (n > 1 && !all_finite(e, n - 1)) return -3;
     }
     cudaStream_t st = nullptr;
     bool own = false;
@@ -248,19 +220,19 @@ extern "C" int tinv_eig(int64_t n, const double* d, const double* e, double* w, 
     int rc = 0;
     {
         const bool dev = op.device_ptrs != 0;
-        Buf bd, be, bw, bz, bib, bit;
+        DevBuf bd, be, bw, bz, bib, bit;
         const double *pd = d, *pe = e;
         double *pw = w, *pz = Z;
         int64_t* pib = iblock;
         int32_t* pit = op.iters;
         cudaError_t ce = cudaSuccess;
         if (!dev) {
-            ce = bd.alloc((size_t)n * sizeof(double), st);
-            if (ce == cudaSuccess) ce = be.alloc((size_t)(n > 1 ? n - 1 : 1) * sizeof(double), st);
-            if (ce == cudaSuccess) ce = bw.alloc((size_t)n * sizeof(double), st);
-            if (ce == cudaSuccess) ce = bz.alloc((size_t)(n * ldz) * sizeof(double), st);
-            if (ce == cudaSuccess && iblock) ce = bib.alloc((size_t)n * sizeof(int64_t), st);
-            if (ce == cudaSuccess && op.iters) ce = bit.alloc((size_t)n * sizeof(int32_t), st);
+            ce = bd.alloc((size_t)n * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = be.alloc((size_t)(n > 1 ? n - 1 : 1) * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = bw.alloc((size_t)n * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = bz.alloc((size_t)(n * ldz) * sizeof(double), st, true);
+            if (ce == cudaSuccess && iblock) ce = bib.alloc((size_t)n * sizeof(int64_t), st, true);
+            if (ce == cudaSuccess && op.iters) ce = bit.alloc((size_t)n * sizeof(int32_t), st, true);
             if (ce == cudaSuccess)
                 ce = cudaMemcpyAsync(bd.p, d, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st);
             if (ce == cudaSuccess && n > 1)
@@ -272,7 +244,7 @@ extern "C" int tinv_eig(int64_t n, const double* d, const double* e, double* w, 
             pib = iblock ? (int64_t*)bib.p : nullptr;
             pit = op.iters ? (int32_t*)bit.p : nullptr;
         }
-        rc = code_of(ce);
+        rc = cuda_code(ce);
         // ---- blocks ----
         std::vector<uint8_t> mark;
         if (!rc) rc = split_marks(n, pd, pe, mark, st);
@@ -296,14 +268,14 @@ extern "C" int tinv_eig(int64_t n, const double* d, const double* e, double* w, 
             nmax = std::max(nmax, size[(size_t)b]);
         }
         // ---- per-block eigenvalues (packed by row position) and eigenvectors (packed) ----
-        Buf btab, bwp, bzp, bitp, binfo, bperm, bblk;
+        DevBuf btab, bwp, bzp, bitp, binfo, bperm, bblk;
         if (!rc) {
-            ce = btab.alloc((size_t)(3 * nb) * sizeof(int64_t), st);
-            if (ce == cudaSuccess) ce = bwp.alloc((size_t)n * sizeof(double), st);
-            if (ce == cudaSuccess) ce = bzp.alloc((size_t)zlen * sizeof(double), st);
-            if (ce == cudaSuccess) ce = bitp.alloc((size_t)n * sizeof(int32_t), st);
-            if (ce == cudaSuccess) ce = binfo.alloc((size_t)nb * sizeof(int64_t), st);
-            rc = code_of(ce);
+            ce = btab.alloc((size_t)(3 * nb) * sizeof(int64_t), st, true);
+            if (ce == cudaSuccess) ce = bwp.alloc((size_t)n * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = bzp.alloc((size_t)zlen * sizeof(double), st, true);
+            if (ce == cudaSuccess) ce = bitp.alloc((size_t)n * sizeof(int32_t), st, true);
+            if (ce == cudaSuccess) ce = binfo.alloc((size_t)nb * sizeof(int64_t), st, true);
+            rc = cuda_code(ce);
         }
         std::vector<int64_t> tab;
         if (!rc) {
@@ -319,7 +291,7 @@ extern "C" int tinv_eig(int64_t n, const double* d, const double* e, double* w, 
                 for (int64_t b = c0; b < c0 + cnt; ++b) cmax = std::max(cmax, size[(size_t)b]);
                 ce = launch_bisect(cnt, tn + c0, tn + nb + c0, 0, cmax, pd, pe, (double*)bwp.p, st);
             }
-            rc = code_of(ce);
+            rc = cuda_code(ce);
         }
         if (!rc) {
             tinv_opts bo = op;
@@ -344,7 +316,7 @@ extern "C" int tinv_eig(int64_t n, const double* d, const double* e, double* w, 
                 ce = cudaMemcpyAsync(binf.data(), binfo.p, (size_t)nb * sizeof(int64_t),
                                      cudaMemcpyDeviceToHost, st);
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-            rc = code_of(ce);
+            rc = cuda_code(ce);
         }
         std::vector<int64_t> perm;
         std::vector<int32_t> blk;
@@ -357,8 +329,8 @@ extern "C" int tinv_eig(int64_t n, const double* d, const double* e, double* w, 
             for (int64_t b = 0; b < nb; ++b)
                 for (int64_t r = start[(size_t)b]; r < start[(size_t)b] + size[(size_t)b]; ++r)
                     blk[(size_t)r] = (int32_t)b;
-            ce = bperm.alloc((size_t)n * sizeof(int64_t), st);
-            if (ce == cudaSuccess) ce = bblk.alloc((size_t)n * sizeof(int32_t), st);
+            ce = bperm.alloc((size_t)n * sizeof(int64_t), st, true);
+            if (ce == cudaSuccess) ce = bblk.alloc((size_t)n * sizeof(int32_t), st, true);
             if (ce == cudaSuccess)
                 ce = cudaMemcpyAsync(bperm.p, perm.data(), (size_t)n * sizeof(int64_t), cudaMemcpyHostToDevice, st);
             if (ce == cudaSuccess)
@@ -382,7 +354,7 @@ extern "C" int tinv_eig(int64_t n, const double* d, const double* e, double* w, 
                     ce = cudaMemcpyAsync(op.iters, pit, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st);
             }
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-            rc = code_of(ce);
+            rc = cuda_code(ce);
         }
         if (!rc) {
             int64_t cnt = 0;

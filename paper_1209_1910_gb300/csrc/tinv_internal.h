@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -163,6 +164,48 @@ int batch_enqueue_device(int64_t nprob, const int64_t* n, const int64_t* off_de,
                          const double* e, const double* w, double* Z, int64_t* info,
                          const tinv_opts& o);
 size_t batch_workspace_bytes(int64_t nprob, const int64_t* n, const tinv_opts& o);
+
+// Library status code (include/tinv.h) of a CUDA runtime error.
+inline int cuda_code(cudaError_t e)
+{
+    if (e == cudaSuccess) return TINV_OK;
+    if (e == cudaErrorMemoryAllocation) return TINV_ENOMEM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
+        e == cudaErrorNoKernelImageForDevice || e == cudaErrorInvalidDevice)
+        return TINV_ENODEV;
+    return TINV_ECUDA;
+}
+
+// True when the k host values are all finite (argument checks of host-pointer calls).
+inline bool all_finite(const double* a, int64_t k)
+{
+    for (int64_t i = 0; i < k; ++i)
+        if (!isfinite(a[i])) return false;
+    return true;
+}
+
+// A device allocation owned by a scope: stream-ordered on `st` (cudaMallocAsync/cudaFreeAsync)
+// when `use_async`, else cudaMalloc/cudaFree.  Zero bytes allocate a small block.
+struct DevBuf {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    bool async = false;
+    cudaError_t alloc(size_t bytes, cudaStream_t s, bool use_async)
+    {
+        st = s;
+        async = use_async;
+        if (bytes == 0) bytes = 256;
+        return async ? cudaMallocAsync(&p, bytes, st) : cudaMalloc(&p, bytes);
+    }
+    ~DevBuf()
+    {
+        if (!p) return;
+        if (async)
+            cudaFreeAsync(p, st);
+        else
+            cudaFree(p);
+    }
+};
 
 // Sturm bisection of nprob problems (tinv_bisect.cu); ns/offs are DEVICE arrays, or null for
 // one problem of order n1 at offset 0.

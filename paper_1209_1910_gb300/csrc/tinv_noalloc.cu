@@ -46,14 +46,6 @@ cudaError_t noalloc_scratch(void** out)
     return cudaSuccess;
 }
 
-int code_of(cudaError_t e)
-{
-    if (e == cudaSuccess) return TINV_OK;
-    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
-        e == cudaErrorNoKernelImageForDevice || e == cudaErrorInvalidDevice)
-        return TINV_ENODEV;
-    return TINV_ECUDA;
-}
 
 }  // namespace
 
@@ -76,7 +68,7 @@ extern "C" int tinv_solve_noalloc(int64_t n, const double* d, const double* e, i
     if (L.total > kNoAllocBytes) return TINV_ENOTSUP;
     void* base = nullptr;
     cudaError_t ce = noalloc_scratch(&base);
-    if (ce != cudaSuccess) return code_of(ce);
+    if (ce != cudaSuccess) return cuda_code(ce);
     const Ws w = bind_layout(base, L, D);
     Problem p;
     memset(&p, 0, sizeof(p));
@@ -92,5 +84,5 @@ extern "C" int tinv_solve_noalloc(int64_t n, const double* d, const double* e, i
     if (ce == cudaSuccess)
         ce = launch_lu(n, d, e, m, s, w.fl, w.fr, w.fu1, w.fu2, w.fpiv, w.u0n, w.tolv, st);
     if (ce == cudaSuccess) ce = launch_solve_rhs(n, m, w, X, ldx, scale, st);
-    return code_of(ce);
+    return cuda_code(ce);
 }

@@ -31,16 +31,6 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
-int rt_code(cudaError_t e)
-{
-    if (e == cudaSuccess) return TINV_OK;
-    if (e == cudaErrorMemoryAllocation) return TINV_ENOMEM;
-    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ||
-        e == cudaErrorNoKernelImageForDevice || e == cudaErrorInvalidDevice)
-        return TINV_ENODEV;
-    return TINV_ECUDA;
-}
-
 struct Req {
     uint64_t ticket = 0;
     int64_t n = 0;
@@ -213,7 +203,7 @@ Wave* tinv_server::launch(std::vector<ReqP>&& reqs, int slot)
             if (ce == cudaSuccess)
                 ce = launch_bisect(nb, dtab, dtab + np, 0, nbmax, dev, dev + M, dev + 2 * M, st);
         }
-        rc = rt_code(ce);
+        rc = cuda_code(ce);
     }
     if (!rc) {
         tinv_opts o;
@@ -234,12 +224,12 @@ Wave* tinv_server::launch(std::vector<ReqP>&& reqs, int slot)
         if (ce == cudaSuccess)
             ce = cudaMemcpyAsync(sg.tab + 2 * np, dtab + 2 * np, (size_t)np * sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, st);
-        rc = rt_code(ce);
+        rc = cuda_code(ce);
     }
     if (dev) cudaFreeAsync(dev, st);
     if (dz) cudaFreeAsync(dz, st);
     if (dtab) cudaFreeAsync(dtab, st);
-    if (!rc) rc = rt_code(cudaLaunchHostFunc(st, wave_done_cb, wv));
+    if (!rc) rc = cuda_code(cudaLaunchHostFunc(st, wave_done_cb, wv));
     wv->rc = rc;
     if (rc) {
         cudaStreamSynchronize(st);  // nothing of this wave may still run
@@ -253,7 +243,7 @@ void tinv_server::finish(Wave* wv)
 {
     cudaStream_t st = streams[wv->slot];
     int rc = wv->rc;
-    if (!rc) rc = rt_code(cudaStreamSynchronize(st));
+    if (!rc) rc = cuda_code(cudaStreamSynchronize(st));
     const Staging& sg = staging[wv->slot];
     const int64_t np = (int64_t)wv->reqs.size();
     int64_t zoff = 0;
