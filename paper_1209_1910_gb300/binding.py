@@ -341,14 +341,14 @@ def eig(d, e, method="cwy", seed=0, j0=0, ldz=None, iters=None, **kw):
     n = len(d)
     ldz = n if ldz is None else ldz
     w = np.zeros(max(n, 1))
-    Zb = np.zeros((max(n, 1), max(ldz, 1)))  # row j = column j of the column-major result
+    Zf = np.empty((max(ldz, 1), max(n, 1)), order="F")  # column-major, leading dimension ldz
     iblock = np.zeros(max(n, 1), dtype=np.int64)
     isplit = np.zeros(max(n, 1), dtype=np.int64)
     nb = ctypes.c_int64(0)
     o = _opts(method, seed, j0, iters=_ptr(iters), **kw)
-    info = _check(load().tinv_eig(n, _ptr(d), _ptr(e), _ptr(w), _ptr(Zb), ldz, _ptr(iblock),
+    info = _check(load().tinv_eig(n, _ptr(d), _ptr(e), _ptr(w), _ptr(Zf), ldz, _ptr(iblock),
                                   _ptr(isplit), ctypes.byref(nb), ctypes.byref(o)), "tinv_eig")
-    Z = np.asfortranarray(Zb[:n, :n].T) if n else np.zeros((0, 0))
+    Z = Zf[:n, :n] if n else np.zeros((0, 0))
     return w[:n], Z, iblock[:n], isplit[:nb.value].copy(), info
 
 
@@ -371,14 +371,14 @@ def bdsvd(a, b, method="cwy", seed=0, j0=0, iters=None, **kw):
     a, b = _f64(a), _f64(b)
     n = len(a)
     s = np.zeros(max(n, 1))
-    Ub = np.zeros((max(n, 1), max(n, 1)))  # row j = column j
-    Vb = np.zeros((max(n, 1), max(n, 1)))
+    U = np.empty((max(n, 1), max(n, 1)), order="F")  # column-major, leading dimension n
+    V = np.empty((max(n, 1), max(n, 1)), order="F")
     o = _opts(method, seed, j0, iters=_ptr(iters), **kw)
-    info = _check(load().tinv_bdsvd(n, _ptr(a), _ptr(b), _ptr(s), _ptr(Ub), n, _ptr(Vb), n,
+    info = _check(load().tinv_bdsvd(n, _ptr(a), _ptr(b), _ptr(s), _ptr(U), n, _ptr(V), n,
                                     ctypes.byref(o)), "tinv_bdsvd")
     if n == 0:
         return np.zeros(0), np.zeros((0, 0)), np.zeros((0, 0)), info
-    return s[:n], np.asfortranarray(Ub.T), np.asfortranarray(Vb.T), info
+    return s[:n], U, V, info
 
 
 def bdsvd_device(a, b, s, U, V, method="cwy", seed=0, j0=0, **kw):
