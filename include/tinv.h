@@ -40,7 +40,7 @@ extern "C" {
 #define TINV_ETIMEDOUT (-103) /* a bounded device-side wait expired (see each kernel)      */
 #define TINV_EAGAIN (-104)    /* server: no slot / memory free right now, retry            */
 #define TINV_ECANCELED (-105) /* server: request was cancelled                            */
-#define TINV_ENOTSUP (-106)   /* size beyond what this build supports                      */
+#define TINV_ENOTSUP (-106)   /* size beyond what this library supports                    */
 #define TINV_ENODEV (-107)    /* no CUDA device, or not an sm_103 device                   */
 #define TINV_EWORKSPACE (-108) /* caller-provided workspace is too small                   */
 

@@ -356,7 +356,7 @@ const char* tinv_strerror(int code)
     case TINV_ETIMEDOUT: return "a bounded device-side wait expired";
     case TINV_EAGAIN: return "no capacity right now; retry";
     case TINV_ECANCELED: return "request cancelled";
-    case TINV_ENOTSUP: return "size not supported by this build";
+    case TINV_ENOTSUP: return "size not supported by this library";
     case TINV_ENODEV: return "no usable sm_103 CUDA device";
     case TINV_EWORKSPACE: return "workspace too small";
     default: break;

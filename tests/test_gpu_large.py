@@ -1,5 +1,5 @@
 """Full-size single problems of order 10^4 (one Peters-Wilkinson cluster of nearly all vectors):
-the spec invariants on the whole result (products formed on the GPU), the closed form per
+the residual and orthogonality bounds on the whole result (products formed on the GPU), the closed form per
 sampled vector for d=0, e=1, and the singletons of the uniform matrix against the oracle."""
 import math
 

@@ -5,8 +5,8 @@ Bars (see the design notes for the derivations):
   * solve: |x_gpu - x_orc| <= 50 cond eps |x| for shifts away from the spectrum; for shifts at
     eigenvalues the normalized directions agree to 1e-12;
   * stand-alone orthogonalization: |Q_gpu - Q_orc|_max <= 10 n eps kappa(V);
-  * inverse iteration: residual <= 10 n eps ||T||_1, orthogonality <= 10 n eps (north-star
-    invariants); singletons agree with the oracle per vector within 1e-10 (after DSTEIN's sign
+  * inverse iteration: residual <= 10 n eps ||T||_1, orthogonality <= 10 n eps (the invariants
+    of a correct eigenvector set); singletons agree with the oracle per vector within 1e-10 (after DSTEIN's sign
     convention); clusters agree by the largest principal angle <= 1e-10.
 """
 import math
