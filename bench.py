@@ -237,6 +237,42 @@ def cpu_parallel(name: str, method: str, d, e, w):
     return nv / dt, cores, desc
 
 
+def lapack_dstein_sample(name: str, d, e, w):
+    """Context, not a baseline of this library: LAPACK's own bisection + DSTEIN (MGS
+    reorthogonalization, the paper's comparison method) through SciPy, on the clusters of the
+    single-core oracle sample, in this process with the BLAS library's default threads.  Returns
+    None when SciPy is missing."""
+    try:
+        import scipy.linalg
+    except ImportError:
+        return None
+    import oracle
+
+    oracle.build()
+    head = oracle.plan(d, e, w)[1]
+    starts = np.flatnonzero(head == np.arange(len(head)))
+    ends = np.r_[starts[1:], len(head)]
+    cl = list(zip(starts.tolist(), ends.tolist()))
+    if name == "glued4200":
+        pick = [next(c for c in cl if c[1] - c[0] == 400), next(c for c in cl if c[1] - c[0] == 200)]
+    else:
+        pick, tot = [], 0
+        for c in cl:
+            if tot >= 600:
+                break
+            pick.append(c)
+            tot += c[1] - c[0]
+    t0 = time.perf_counter()
+    nv = 0
+    for a, b in pick:
+        scipy.linalg.eigh_tridiagonal(d, e, select="i", select_range=(a, b - 1),
+                                      lapack_driver="stebz")
+        nv += b - a
+    dt = time.perf_counter() - t0
+    return {"value": nv / dt, "unit": "eigvec/s", "kind": "LAPACK dstebz + dstein (SciPy)",
+            "sample": "%d vectors: the clusters of the oracle sample, eigenvalues included" % nv}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -1006,6 +1042,9 @@ def ours_arm(args):
         v, cores, desc = cpu_parallel(args.workload, args.method, d, e, w)
         out["cpu_baseline_parallel"] = {"value": v, "unit": "eigvec/s", "cores": cores,
                                         "kind": "oracle", "sample": desc}
+        lap = lapack_dstein_sample(args.workload, d, e, w)
+        if lap:
+            out["context_lapack_dstein"] = lap
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
