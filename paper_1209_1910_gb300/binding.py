@@ -334,6 +334,18 @@ def split(d, e, **kw):
     return isplit[:nb.value].copy()
 
 
+def split_device(d, e, **kw):
+    """tinv_split on torch CUDA tensors d[n], e[n-1] (synchronizes their stream); returns the
+    block ends (host int64 array)."""
+    n = d.numel()
+    isplit = np.zeros(max(n, 1), dtype=np.int64)
+    nb = ctypes.c_int64(0)
+    _check(load().tinv_split(n, _ptr(d), _ptr(e), _ptr(isplit), ctypes.byref(nb),
+                             ctypes.byref(_opts(device=True, stream=_stream_of(d), **kw))),
+           "tinv_split")
+    return isplit[:nb.value].copy()
+
+
 def eig(d, e, method="cwy", seed=0, j0=0, ldz=None, iters=None, **kw):
     """All eigenpairs of T split into unreduced blocks (host arrays).  Returns
     (w, Z, iblock, isplit, info): Z is n x n (column j the eigenvector of w[j])."""

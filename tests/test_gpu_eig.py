@@ -115,3 +115,40 @@ def test_eig_full_size_zero_glue(gpu, orc):
     assert len(isp) == 200
     _check(orc, d, e, w, Z, ib, isp, info)
     assert residual_ratio(d, e, w, Z) <= 10 and orth_ratio(Z) <= 10
+
+
+def test_split_device_pointers(gpu, orc):
+    torch = pytest.importorskip("torch")
+    d, e = _cases()["uniform300_cut"]
+    dev = torch.device("cuda:0")
+    isp = gpu.split_device(torch.from_numpy(d).to(dev), torch.from_numpy(e).to(dev))
+    assert np.array_equal(isp, orc.split(d, e))
+
+
+def test_eig_more_blocks_than_one_bisection_launch(gpu):
+    # n = 70000 with every off-diagonal zero: 70000 blocks of order 1, more than one bisection
+    # launch takes (65535 problems), and a 39 GB Z; the result must be the sorted diagonal and an
+    # exact permutation matrix
+    torch = pytest.importorskip("torch")
+    n = 70000
+    dev = torch.device("cuda:0")
+    free, _ = torch.cuda.mem_get_info(dev)
+    if free < 48 * 2**30:
+        pytest.skip("needs ~40 GB of free device memory")
+    g = np.random.default_rng(9)
+    d = np.round(g.uniform(-50.0, 50.0, n), 3)
+    td = torch.from_numpy(d).to(dev)
+    te = torch.zeros(n - 1, dtype=torch.float64, device=dev)
+    tw = torch.zeros(n, dtype=torch.float64, device=dev)
+    tZ = torch.empty((n, n), dtype=torch.float64, device=dev)  # row j = eigenvector j
+    tib = torch.zeros(n, dtype=torch.int64, device=dev)
+    info, isp = gpu.eig_device(td, te, tw, tZ, tib)
+    assert info == 0 and len(isp) == n
+    order = np.argsort(d, kind="stable")
+    assert np.array_equal(tib.cpu().numpy(), order)
+    w = tw.cpu().numpy()
+    assert np.abs(w - d[order]).max() <= 2 * np.finfo(float).eps * 50.0
+    # each eigenvector is the unit vector of its block's row: one entry 1, all others 0
+    assert torch.equal(tZ.argmax(dim=1).cpu(), torch.from_numpy(order))
+    assert float(tZ.sum()) == float(n) and float(tZ.abs().max()) == 1.0
+    del tZ
