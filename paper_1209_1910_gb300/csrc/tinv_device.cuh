@@ -252,9 +252,13 @@ __device__ __noinline__ void seq_back(int64_t n, const Fac& f, const double* y, 
 }
 
 // The same by a whole CTA: warps 1.. stream the coefficients (a, b, r y) of the next block of
-// rows into shared memory while thread 0 runs the current block's recurrence from shared memory,
-// so the single thread pays only its two FMAs per row.  `sh` holds >= 6 kStageRows doubles.
-// Called by every thread of the CTA; y and x may be global or shared (not the same array).
+// rows into shared memory while two lanes of warp 0 run the current block's recurrence from
+// shared memory.  Row k is x_k = fma(a_k, x_{k+1}, t_k) with t_k = fma(b_k, x_{k+2}, r_k y_k);
+// t_k needs only x_{k+2}, so lane 1 forms it while lane 0 forms x_{k+1}: one FP64 instruction
+// for both lanes and one lane exchange per row (a single thread would issue two dependent FP64
+// instructions per row).  The operations and their operands are those of seq_back, so the
+// results are identical.  `sh` holds >= 6 kStageRows doubles.  Called by every thread of the
+// CTA; y and x may be global or shared (not the same array).
 constexpr int kStageRows = 320;
 __device__ __noinline__ void staged_seq_back(int64_t n, const Fac& f, const double* y, double* x,
                                              double* sh, int64_t top0)
@@ -272,8 +276,9 @@ __device__ __noinline__ void staged_seq_back(int64_t n, const Fac& f, const doub
     int64_t top = top0;
     int64_t lo = top > kStageRows ? top - kStageRows : 0;
     stage(lo, top, 0, 0, B);
-    double cur = 0.0, nxt = 0.0;
-    if (t == 0) {
+    // lane 0: cur = x_{k+1}, nxt = x_{k+2}; lane 1: tk = t_k for the next row k
+    double cur = 0.0, nxt = 0.0, tk = 0.0;
+    if (t < 2) {
         cur = top < n ? x[top] : 0.0;
         nxt = top + 1 < n ? x[top + 1] : 0.0;
     }
@@ -281,14 +286,31 @@ __device__ __noinline__ void staged_seq_back(int64_t n, const Fac& f, const doub
     for (int blk = 0;; ++blk) {
         const int64_t nlo = lo > kStageRows ? lo - kStageRows : 0;
         if (t >= 32 && lo > 0) stage(nlo, lo, (blk + 1) & 1, 32, B - 32);
-        if (t == 0) {
+        if (t < 2 && top > lo) {
             const double* sa = sh + (blk & 1) * 3 * kStageRows;
+            const double* sb = sa + kStageRows;
+            const double* sz = sa + 2 * kStageRows;
+            // t for the block's first row from the values both lanes hold
+            tk = fma(sb[top - 1 - lo], nxt, sz[top - 1 - lo]);
             for (int64_t k = top - 1; k >= lo; --k) {
                 const int64_t i = k - lo;
-                const double v = fma(sa[i], cur, fma(sa[kStageRows + i], nxt, sa[2 * kStageRows + i]));
-                x[k] = v;
-                nxt = cur;
-                cur = v;
+                // lane 0 receives t_k, lane 1 receives x_{k+1}
+                const double other = __shfl_xor_sync(0x3u, t == 0 ? cur : tk, 1);
+                const double xk1 = (t == 0) ? cur : other;
+                // lane 0: x_k = a_k x_{k+1} + t_k;  lane 1: t_{k-1} = b_{k-1} x_{k+1} + z_{k-1}
+                // (row k-1 is in this block unless k == lo; that t is formed after the block)
+                const int64_t j = (t == 0 || k == lo) ? i : i - 1;
+                const double p = (t == 0) ? sa[j] : sb[j];
+                const double c = (t == 0) ? other : sz[j];
+                const double v = fma(p, xk1, c);
+                if (t == 0) {
+                    x[k] = v;
+                    nxt = cur;
+                    cur = v;
+                } else {
+                    tk = v;
+                    nxt = xk1;  // x_{k+1}: after the block's last row, the next block's first t
+                }
             }
         }
         __syncthreads();
