@@ -60,7 +60,7 @@ DRIVER_EXTRA_LAUNCHES = {"split4200": 3, "bidiag2000": 3}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (vector and tensor alike), TFLOP/s
 # DRAM bytes (read + write) of one cluster-kernel launch, from ncu on the current kernels
 # (profiles/launches_glued4200_cwy.md); None where no capture exists
-TRAFFIC_BYTES = {("glued4200", "cwy"): 31.54e9}
+TRAFFIC_BYTES = {("glued4200", "cwy"): 33.09e9}
 
 
 def parse():
