@@ -916,8 +916,9 @@ int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int
         }
         rc = cuda_code(ce);
         Ws wsb = bind_layout(ws.p, L, D);
-        // team size for one cluster of m columns: at most n/16 CTAs
-        const int32_t g = (int32_t)((n / 16 < (int64_t)P) ? (n / 16) : P);
+        // team size for one cluster of m columns: at most n/16 CTAs and kTeamMax
+        int32_t g = (int32_t)((n / 16 < (int64_t)P) ? (n / 16) : P);
+        if (g > kTeamMax) g = kTeamMax;
         if (g >= 2 && op.o.method == TINV_CWY) {
             wsb.P = g;
         } else {

@@ -668,7 +668,7 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
     // The chunks' own maps, kept for the value fold below that gives every chunk its boundary
     // values (applying composed maps to values loses accuracy when they span several small
     // pivots; the compositions are used only between warps and between CTAs).
-    double* cm = sh + 128 + 6 * tr.G;  // [6 * PT]; sh holds 2048 doubles, so G <= 192
+    double* cm = sh + 128 + 6 * tr.G;  // [6 * PT]; sh holds 2048 doubles, so G <= kTeamMax
     if (part) {
         double* o = cm + 6 * t;
         o[0] = m00;

@@ -14,6 +14,10 @@ namespace tinvx {
 constexpr int kFirstWarps = 8;      // warps per CTA of the warp-per-eigenvalue solve kernel
 constexpr int kPlanThreads = 1024;  // threads of the single-CTA plan kernel
 constexpr int kScalTeam = 16;       // doubles of per-CTA scalar partials
+// Largest CTA team of the cluster kernel.  The distributed solve keeps, in the CTA's 2048-double
+// scratch, 128 doubles of warp maps, 6 per rank of the maps published by the team and 6 x 128 of
+// chunk maps: (2048 - 128 - 768) / 6 = 192 ranks.
+constexpr int kTeamMax = 192;
 
 // Device error word bits.
 constexpr int kErrTimeout = 1;   // a bounded spin wait expired

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_list(Problem p, Ws w, int
         bool cand = false;
         if (teams && c < K) {
             const double wc = cluster_work(w, c);
-            int64_t gmax = min((int64_t)P, max((int64_t)1, w.segs[w.segj[w.clstart[c]]].n / 16));
+            int64_t gmax = min((int64_t)min(P, kTeamMax), max((int64_t)1, w.segs[w.segj[w.clstart[c]]].n / 16));
             if (max_team > 0) gmax = min(gmax, (int64_t)max_team);
             cand = floor((double)P * wc / wtot) >= 2.0 && gmax >= 2;
         }
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_list(Problem p, Ws w, int
         int32_t used = 0;
         for (int32_t i = 0; i < ncand; ++i) {
             const int32_t c = s_cand[i];
-            int32_t gmax = (int32_t)min((int64_t)P, max((int64_t)1, w.segs[w.segj[w.clstart[c]]].n / 16));
+            int32_t gmax = (int32_t)min((int64_t)min(P, kTeamMax), max((int64_t)1, w.segs[w.segj[w.clstart[c]]].n / 16));
             if (max_team > 0) gmax = min(gmax, max_team);
             const double share = Pteam * cluster_work(w, c) / wteam;
             const int32_t g = min(gmax, (int32_t)floor(share));
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_list(Problem p, Ws w, int
             double bf = -1.0;
             for (int32_t i = 0; i < ncand; ++i) {
                 const int32_t c = s_cand[i];
-                int32_t gmax = (int32_t)min((int64_t)P, max((int64_t)1, w.segs[w.segj[w.clstart[c]]].n / 16));
+                int32_t gmax = (int32_t)min((int64_t)min(P, kTeamMax), max((int64_t)1, w.segs[w.segj[w.clstart[c]]].n / 16));
                 if (max_team > 0) gmax = min(gmax, max_team);
                 if (s_gsz[i] < 2 || s_gsz[i] >= gmax) continue;
                 const double share = Pteam * cluster_work(w, c) / wteam;
@@ -1377,12 +1377,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t
 // ==========================================================================================
 // Launchers
 // ==========================================================================================
-// Threads per CTA of the cluster kernel (one CTA per SM).  The kernel also runs with two
-// 256-thread CTAs per SM, which measured no faster on the glued-Wilkinson workload: the CTAs
-// sharing an SM belong to teams that run the same phases at the same time.
-int32_t chain_threads(int64_t n)
+// Threads per CTA of the cluster kernel (one CTA per SM).  Two 256-thread CTAs per SM measured
+// slower on the glued-Wilkinson workload (173.2 against 170.6 ms) and on the 512-problem batch
+// (205k against 224k eigenvectors/s): the CTAs sharing an SM belong to teams that run the same
+// phases at the same time.
+int32_t chain_threads(int64_t)
 {
-    (void)n;  // two 256-thread CTAs per SM measured no faster than one 512-thread CTA
     return 512;
 }
 
@@ -1396,12 +1396,12 @@ size_t chain_smem_bytes(int64_t n, bool use_smem)
     return (size_t)(2048 + (use_smem ? 2 * n : 0)) * sizeof(double);
 }
 
-int32_t chain_grid(int32_t cap, int64_t n)
+int32_t chain_grid(int32_t cap, int64_t)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int32_t P = (sms > 0 ? sms : 1) * (chain_threads(n) == 256 ? 2 : 1);
+    int32_t P = sms > 0 ? sms : 1;
     if (cap > 0 && cap < P) P = cap;
     return P;
 }
@@ -1498,9 +1498,9 @@ cudaError_t launch_chain(const Problem& p, const Ws& w, int32_t mode, const doub
     const int nt = chain_threads(p.n);
     void* fn;
     if (p.method == 0)
-        fn = (nt == 256) ? (void*)k_chain<0, 256> : (void*)k_chain<0, 512>;
+        fn = (void*)k_chain<0, 512>;
     else
-        fn = (nt == 256) ? (void*)k_chain<1, 256> : (void*)k_chain<1, 512>;
+        fn = (void*)k_chain<1, 512>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, occ = 0, sms = 0;
