@@ -148,10 +148,11 @@ extern "C" int tinv_bdsvd(int64_t n, const double* a, const double* b, double* s
             k_golub_kahan<<<g, 256, 0, st>>>(n, pa, pb, (double*)bd2.p, (double*)be2.p);
             ce = cudaGetLastError();
         }
-        // all 2n eigenvalues by bisection; the n largest are the singular values, ascending
+        // the n largest of the 2n eigenvalues by bisection (indices n .. 2n-1, into bw2 + n):
+        // the singular values, ascending
         if (ce == cudaSuccess)
             ce = launch_bisect(1, nullptr, nullptr, n2, n2, (const double*)bd2.p, (const double*)be2.p,
-                               (double*)bw2.p, st);
+                               (double*)bw2.p, st, n);
         rc = cuda_code(ce);
         if (!rc) {
             tinv_opts to = op;

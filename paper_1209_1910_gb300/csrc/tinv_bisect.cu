@@ -47,13 +47,14 @@ __device__ __forceinline__ int64_t sturm_count(int64_t n, const double* __restri
 
 __global__ void __launch_bounds__(kBisectThreads) k_bisect(const int64_t* __restrict__ ns,
                                                           const int64_t* __restrict__ offs,
-                                                          int64_t n1, const double* __restrict__ D,
+                                                          int64_t n1, int64_t k0,
+                                                          const double* __restrict__ D,
                                                           const double* __restrict__ E,
                                                           double* __restrict__ W)
 {
     const int64_t q = blockIdx.y;
     const int64_t n = ns ? ns[q] : n1;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t off = offs ? offs[q] : 0;
     const double* d = D + off;
@@ -103,7 +104,8 @@ __global__ void __launch_bounds__(kBisectThreads) k_bisect(const int64_t* __rest
 template <int L>
 __global__ void __launch_bounds__(kBisectThreads) k_bisect_tree(const int64_t* __restrict__ ns,
                                                                const int64_t* __restrict__ offs,
-                                                               int64_t n1, const double* __restrict__ D,
+                                                               int64_t n1, int64_t k0,
+                                                               const double* __restrict__ D,
                                                                const double* __restrict__ E,
                                                                double* __restrict__ W)
 {
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kBisectThreads) k_bisect_tree(const int64_t* _
     const int64_t q = blockIdx.y;
     const int64_t n = ns ? ns[q] : n1;
     const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t k = gt / L;  // the whole group of L lanes shares k
+    const int64_t k = k0 + gt / L;  // the whole group of L lanes shares k
     const int g = (int)(gt % L);
     if (k >= n) return;
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1)));
@@ -191,33 +193,40 @@ __global__ void __launch_bounds__(kBisectThreads) k_bisect_tree(const int64_t* _
 
 }  // namespace
 
-// Lanes per eigenvalue for a launch of nprob x nmax eigenvalues: the largest of 32, 16, 8, 4 that
-// keeps the launch within about two warps per SM sub-partition, else 1 (plain bisection).
-int bisect_lanes(int64_t nprob, int64_t nmax)
+// Lanes per eigenvalue for a launch of nprob x neig eigenvalues: the largest of 32, 16, 8, 4 that
+// keeps the launch within about one warp per SM sub-partition, else 1 (plain bisection).  One
+// warp's FP64 instruction holds its sub-partition's FP64 pipe for about 64 cycles, so a single
+// warp of dependent Sturm steps already keeps that pipe busy; more lanes then only add the tree's
+// extra midpoints (2^S - 1 counts for S halvings).
+int bisect_lanes(int64_t nprob, int64_t neig)
 {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t target = (int64_t)(sms > 0 ? sms : 1) * 4 * 32 * 2;
-    const int64_t eig = nprob * nmax;
+    const int64_t target = (int64_t)(sms > 0 ? sms : 1) * 4 * 32;
+    const int64_t eig = nprob * neig;
     for (int L = 32; L >= 4; L >>= 1)
         if (eig * L <= target) return L;
     return 1;
 }
 
 // nprob problems; ns/offs are DEVICE arrays (or null for one problem of order n1 at offset 0).
+// Eigenvalues k0 .. n-1 of each problem are computed (k0 > 0 only for a single problem).
 cudaError_t launch_bisect(int64_t nprob, const int64_t* ns, const int64_t* offs, int64_t n1,
-                          int64_t nmax, const double* d, const double* e, double* w, cudaStream_t st)
+                          int64_t nmax, const double* d, const double* e, double* w, cudaStream_t st,
+                          int64_t k0)
 {
-    if (nprob <= 0 || nmax <= 0) return cudaSuccess;
-    const int L = bisect_lanes(nprob, nmax);
-    const dim3 grid((unsigned)((nmax * L + kBisectThreads - 1) / kBisectThreads), (unsigned)nprob);
+    if (k0 < 0 || (k0 > 0 && ns)) return cudaErrorInvalidValue;
+    const int64_t neig = nmax - k0;
+    if (nprob <= 0 || neig <= 0) return cudaSuccess;
+    const int L = bisect_lanes(nprob, neig);
+    const dim3 grid((unsigned)((neig * L + kBisectThreads - 1) / kBisectThreads), (unsigned)nprob);
     switch (L) {
-    case 32: k_bisect_tree<32><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, d, e, w); break;
-    case 16: k_bisect_tree<16><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, d, e, w); break;
-    case 8: k_bisect_tree<8><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, d, e, w); break;
-    case 4: k_bisect_tree<4><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, d, e, w); break;
-    default: k_bisect<<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, d, e, w); break;
+    case 32: k_bisect_tree<32><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, k0, d, e, w); break;
+    case 16: k_bisect_tree<16><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, k0, d, e, w); break;
+    case 8: k_bisect_tree<8><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, k0, d, e, w); break;
+    case 4: k_bisect_tree<4><<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, k0, d, e, w); break;
+    default: k_bisect<<<grid, kBisectThreads, 0, st>>>(ns, offs, n1, k0, d, e, w); break;
     }
     return cudaGetLastError();
 }

@@ -212,8 +212,11 @@ struct DevBuf {
 };
 
 // Sturm bisection of nprob problems (tinv_bisect.cu); ns/offs are DEVICE arrays, or null for
-// one problem of order n1 at offset 0.
+// one problem of order n1 at offset 0.  k0 > 0 (single problem only) computes eigenvalues
+// k0 .. n1-1 alone, into w[k0 ..]; each index is bisected independently, so they are the same
+// values a full call gives.
 cudaError_t launch_bisect(int64_t nprob, const int64_t* ns, const int64_t* offs, int64_t n1,
-                          int64_t nmax, const double* d, const double* e, double* w, cudaStream_t st);
+                          int64_t nmax, const double* d, const double* e, double* w, cudaStream_t st,
+                          int64_t k0 = 0);
 
 }  // namespace tinvx
