@@ -117,6 +117,39 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
 size_t tinv_workspace_size(int64_t n, int64_t m, const tinv_opts* o);
 
 /*
+ * tinv_tune -- autotuner for the cluster kernel's team cap (tinv_opts.max_team) on one problem.
+ * A cluster's member sweeps (Alg. 4; the passes of Sec. 3.3.2 and the solve) are split over a
+ * team of CTAs that meet at team barriers: a larger team has more FP64 units and waits longer for
+ * its slowest CTA.  The automatic rule sizes teams by each cluster's share of the m_c^2 n work;
+ * tinv_tune measures instead.  It runs tinv_ex on the problem once per candidate cap (the
+ * automatic rule, then 2, 4, 8, ... below the grid, n/16 and 192), one warm-up call and `reps`
+ * timed calls each (CUDA events on its own stream), and keeps the automatic rule unless a cap is
+ * at least 1% faster.
+ *   n, d, e, m, w : the problem, as for tinv_ex; host or device memory per o->device_ptrs (with
+ *            host pointers the values are checked as tinv_ex checks them).
+ *   o      : options (NULL = defaults).  method, seed, j0 and grid_ctas are those tuned for;
+ *            max_team, workspace, iters, info, counters, phase_ms and stream are not used.
+ *   reps   : timed calls per candidate, >= 1.
+ *   max_team : out, the chosen cap (0 = the automatic rule); pass it as tinv_opts.max_team in
+ *            later calls on problems of this shape.
+ *   ms     : optional out, mean device milliseconds of one call with the chosen cap.
+ *   cached : optional out, 1 when the choice came from the tune cache and nothing was run.
+ * Tune cache: choices are kept for the life of the process (thread-safe), keyed by device,
+ * method, grid cap, n, m, the number of clusters with >= 2 members and the largest cluster (from
+ * the plan of step a2, tinv_plan).  A call whose key is cached returns that choice after the plan
+ * alone.  tinv_tune_clear() empties the cache.
+ * The call is synchronous in both pointer modes; it allocates its own Z and workspace (the
+ * device memory of one tinv_ex call with host pointers) and frees them before returning.
+ * Returns 0; -1 n < 0; -2 d; -3 e; -4 m outside [0, n]; -5 w (NULL; with host pointers also
+ * non-finite or not ascending); -6 method; -7 reps < 1; -8 max_team NULL; or a runtime code.
+ */
+int tinv_tune(int64_t n, const double* d, const double* e, int64_t m, const double* w,
+              const tinv_opts* o, int32_t reps, int32_t* max_team, float* ms, int32_t* cached);
+
+/* Empty the tune cache of tinv_tune. */
+void tinv_tune_clear(void);
+
+/*
  * tinv_batch -- all eigenvectors of nprob independent problems of uneven order, computed together
  * by one launch sequence: each problem is Sec. 2.1's problem (every lambda_j of its T), solved as
  * tinv_ex would solve it alone; clusters never span problems, and the clusters and eigenvalues of

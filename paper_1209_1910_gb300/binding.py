@@ -27,7 +27,7 @@ ERRORS = {-101: "ENOMEM", -102: "ECUDA", -103: "ETIMEDOUT", -104: "EAGAIN", -105
 EXPORTS = ["tinv_opts_default", "tinv_strerror", "tinv_version", "tinv", "tinv_ex",
            "tinv_workspace_size", "tinv_batch", "tinv_batch_workspace_size", "tinv_bisect",
            "tinv_bisect_batch", "tinv_split", "tinv_eig", "tinv_bdsvd",
-           "tinv_plan",
+           "tinv_plan", "tinv_tune", "tinv_tune_clear",
            "tinv_lu", "tinv_solve", "tinv_solve_noalloc", "tinv_orth",
            "tinv_server_cfg_default", "tinv_server_create", "tinv_submit", "tinv_poll",
            "tinv_wait", "tinv_cancel", "tinv_server_stats", "tinv_server_destroy"]
@@ -114,6 +114,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
             lib.tinv_eig.restype = ctypes.c_int
             lib.tinv_bdsvd.argtypes = [I64, P, P, P, P, I64, P, I64, ctypes.POINTER(Opts)]
             lib.tinv_bdsvd.restype = ctypes.c_int
+            lib.tinv_tune.argtypes = [I64, P, P, I64, P, ctypes.POINTER(Opts), I32,
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_int32)]
+            lib.tinv_tune.restype = ctypes.c_int
+            lib.tinv_tune_clear.argtypes = []
+            lib.tinv_tune_clear.restype = None
             _lib = lib
     return _lib
 
@@ -186,6 +192,23 @@ def plan(d, e, w, **kw):
     _check(load().tinv_plan(n, _ptr(d), _ptr(e), m, _ptr(w), _ptr(wp), _ptr(head), _ptr(scal),
                             ctypes.byref(o)), "tinv_plan")
     return wp, head, scal
+
+
+def tune(d, e, w, reps=2, **kw):
+    """tinv_tune: (max_team, ms, cached) for this problem; pass max_team to later calls."""
+    dev = kw.get("device", False)
+    if not dev:
+        d, e, w = _f64(d), _f64(e), _f64(w)
+    n, m = len(d), len(w)
+    mt, ms, cached = ctypes.c_int32(0), ctypes.c_float(0.0), ctypes.c_int32(0)
+    o = _opts(**kw)
+    _check(load().tinv_tune(n, _ptr(d), _ptr(e), m, _ptr(w), ctypes.byref(o), reps,
+                            ctypes.byref(mt), ctypes.byref(ms), ctypes.byref(cached)), "tinv_tune")
+    return int(mt.value), float(ms.value), bool(cached.value)
+
+
+def tune_clear():
+    load().tinv_tune_clear()
 
 
 def lu(d, e, s, **kw):

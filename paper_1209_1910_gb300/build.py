@@ -15,7 +15,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libtinv.so")
 OBJDIR = os.path.join(HERE, "_build")
 SOURCES = ["tinv_kernels.cu", "tinv_api.cu", "tinv_noalloc.cu", "tinv_bisect.cu",
-           "tinv_server.cu", "tinv_eig.cu", "tinv_bdsvd.cu"]
+           "tinv_server.cu", "tinv_eig.cu", "tinv_bdsvd.cu", "tinv_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

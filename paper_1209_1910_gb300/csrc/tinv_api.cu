@@ -133,18 +133,6 @@ using namespace tinvx;
 
 namespace {
 
-
-
-
-bool ascending(const double* a, int64_t k)
-{
-    for (int64_t i = 1; i < k; ++i)
-        if (!(a[i] >= a[i - 1])) return false;
-    return true;
-}
-
-// Device allocation that is freed on scope exit (stream-ordered when a stream is given).
-
 __global__ void k_finish(const int64_t* ctr, int64_t* info)
 {
     const int64_t err = ctr[kCtrErr];

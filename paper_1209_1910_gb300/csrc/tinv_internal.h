@@ -188,6 +188,14 @@ inline bool all_finite(const double* a, int64_t k)
     return true;
 }
 
+// a[0..k) non-decreasing (NaN fails)
+inline bool ascending(const double* a, int64_t k)
+{
+    for (int64_t i = 1; i < k; ++i)
+        if (!(a[i] >= a[i - 1])) return false;
+    return true;
+}
+
 // A device allocation owned by a scope: stream-ordered on `st` (cudaMallocAsync/cudaFreeAsync)
 // when `use_async`, else cudaMalloc/cudaFree.  Zero bytes allocate a small block.
 struct DevBuf {

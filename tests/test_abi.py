@@ -178,6 +178,32 @@ def test_bdsvd_argument_checks(lib):
     assert lib.tinv_bdsvd(3, P(a), P(b), P(s), P(U), 3, P(V), 3, ctypes.byref(o)) == -9
 
 
+def test_tune_argument_checks(lib):
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    d, e, w = np.zeros(4), np.ones(3), np.array([-1.5, -0.5, 0.5, 1.5])
+    mt, ms, cached = ctypes.c_int32(7), ctypes.c_float(1.0), ctypes.c_int32(7)
+    R = (ctypes.byref(mt), ctypes.byref(ms), ctypes.byref(cached))
+    assert lib.tinv_tune(-1, None, None, 0, None, None, 1, *R) == -1
+    assert lib.tinv_tune(4, None, P(e), 4, P(w), None, 1, *R) == -2
+    assert lib.tinv_tune(4, P(d), None, 4, P(w), None, 1, *R) == -3
+    assert lib.tinv_tune(4, P(d), P(e), 5, P(w), None, 1, *R) == -4
+    assert lib.tinv_tune(4, P(d), P(e), 4, None, None, 1, *R) == -5
+    assert lib.tinv_tune(4, P(d), P(e), 4, P(w[::-1].copy()), None, 1, *R) == -5
+    assert lib.tinv_tune(4, P(np.array([0.0, np.inf, 0.0, 0.0])), P(e), 4, P(w), None, 1, *R) == -2
+    o = binding.Opts()
+    lib.tinv_opts_default(ctypes.byref(o))
+    o.method = 3
+    assert lib.tinv_tune(4, P(d), P(e), 4, P(w), ctypes.byref(o), 1, *R) == -6
+    assert lib.tinv_tune(4, P(d), P(e), 4, P(w), None, 0, *R) == -7
+    assert lib.tinv_tune(4, P(d), P(e), 4, P(w), None, 1, None, None, None) == -8
+    # nothing to tune: order 0 or 1, or no eigenvalues; the outputs are reset
+    assert lib.tinv_tune(0, None, None, 0, None, None, 1, *R) == 0
+    assert (mt.value, ms.value, cached.value) == (0, 0.0, 0)
+    assert lib.tinv_tune(1, P(np.array([2.0])), None, 1, P(np.array([2.0])), None, 1, *R) == 0
+    assert lib.tinv_tune(4, P(d), P(e), 0, None, None, 1, *R) == 0
+    lib.tinv_tune_clear()
+
+
 def test_server_config_and_null_checks(lib):
     c = binding.ServerCfg()
     lib.tinv_server_cfg_default(ctypes.byref(c))

@@ -1,0 +1,51 @@
+"""The team-cap autotuner (tinv_tune through the C ABI): its choice is the automatic rule or a
+power-of-two cap, a repeated call on the same shape is served from the tune cache without running
+anything, a different spectrum of the same order is a different key, MGS has nothing to tune, and
+a call with the chosen cap meets the residual and orthogonality bounds."""
+import numpy as np
+import pytest
+
+from helpers import orth_ratio, residual_ratio
+from paper_1209_1910_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1209_1910_gb300 import binding, build
+
+    build.build()
+    binding.load()
+    return binding
+
+
+def test_tune_choice_cache_and_bounds(gpu, orc):
+    d, e = inputs.glued_wilkinson(100, 1e-10)  # n = 2100: 7 clusters of 200 and 400 members
+    w = orc.bisect(d, e)
+    gpu.tune_clear()
+    mt, ms, cached = gpu.tune(d, e, w, reps=1)
+    assert not cached and ms > 0.0
+    assert mt == 0 or (2 <= mt <= 128 and mt & (mt - 1) == 0)
+    mt2, ms2, cached2 = gpu.tune(d, e, w, reps=1)
+    assert cached2 and (mt2, ms2) == (mt, ms)
+    Z = gpu.tinv(d, e, w, max_team=mt)
+    assert residual_ratio(d, e, w, Z) <= 10 and orth_ratio(Z) <= 10
+    # the same order with another spectrum (uniform random d, e) is another key: timed anew
+    d3, e3 = inputs.uniform(2100, seed=4)
+    w3 = orc.bisect(d3, e3)
+    _, _, cached3 = gpu.tune(d3, e3, w3, reps=1)
+    assert not cached3
+    gpu.tune_clear()
+    _, _, cached4 = gpu.tune(d, e, w, reps=1)
+    assert not cached4
+
+
+def test_tune_mgs_keeps_the_automatic_rule(gpu, orc):
+    d, e = inputs.glued_wilkinson(10, 1e-10)  # n = 210
+    w = orc.bisect(d, e)
+    mt, ms, _ = gpu.tune(d, e, w, method="mgs", reps=1)
+    assert mt == 0 and ms > 0.0
