@@ -134,10 +134,13 @@ size_t tinv_workspace_size(int64_t n, int64_t m, const tinv_opts* o);
  *            later calls on problems of this shape.
  *   ms     : optional out, mean device milliseconds of one call with the chosen cap.
  *   cached : optional out, 1 when the choice came from the tune cache and nothing was run.
- * Tune cache: choices are kept for the life of the process (thread-safe), keyed by device,
- * method, grid cap, n, m, the number of clusters with >= 2 members and the largest cluster (from
- * the plan of step a2, tinv_plan).  A call whose key is cached returns that choice after the plan
- * alone.  tinv_tune_clear() empties the cache.
+ * Tune cache: choices are kept for the life of the process (thread-safe), keyed by the device's
+ * name and SM count, method, grid cap, n, m, the number of clusters with >= 2 members and the
+ * largest cluster (from the plan of step a2, tinv_plan).  A call whose key is cached returns that
+ * choice after the plan alone.  tinv_tune_clear() empties the cache; tinv_tune_save/_load write
+ * and read it as a text file.  If the environment variable TINV_TUNE_CACHE names a file, the
+ * first tinv_tune call of the process merges that file into the cache, and every new choice
+ * rewrites the file (best effort: a file that cannot be written is not an error of the call).
  * The call is synchronous in both pointer modes; it allocates its own Z and workspace (the
  * device memory of one tinv_ex call with host pointers) and frees them before returning.
  * Returns 0; -1 n < 0; -2 d; -3 e; -4 m outside [0, n]; -5 w (NULL; with host pointers also
@@ -148,6 +151,22 @@ int tinv_tune(int64_t n, const double* d, const double* e, int64_t m, const doub
 
 /* Empty the tune cache of tinv_tune. */
 void tinv_tune_clear(void);
+
+/*
+ * tinv_tune_save -- write the tune cache to `path` (created or truncated): a tag line
+ * "# tinv tune cache v1", then one entry per line with tab-separated fields: device name, SM
+ * count, method, grid cap, n, m, clusters with >= 2 members, largest cluster, chosen cap,
+ * milliseconds.  Returns 0, -1 (path NULL) or -2 (the file cannot be written).
+ */
+int tinv_tune_save(const char* path);
+
+/*
+ * tinv_tune_load -- merge the entries of a file written by tinv_tune_save into the tune cache
+ * (an entry with the same key is replaced).  Returns the number of entries read (>= 0), -1 (path
+ * NULL), -2 (the file cannot be read or lacks the tag line) or -3 (a malformed entry: the
+ * entries before it are kept, the rest of the file is not read).  No device is needed.
+ */
+int tinv_tune_load(const char* path);
 
 /*
  * tinv_batch -- all eigenvectors of nprob independent problems of uneven order, computed together

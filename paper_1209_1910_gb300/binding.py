@@ -27,7 +27,7 @@ ERRORS = {-101: "ENOMEM", -102: "ECUDA", -103: "ETIMEDOUT", -104: "EAGAIN", -105
 EXPORTS = ["tinv_opts_default", "tinv_strerror", "tinv_version", "tinv", "tinv_ex",
            "tinv_workspace_size", "tinv_batch", "tinv_batch_workspace_size", "tinv_bisect",
            "tinv_bisect_batch", "tinv_split", "tinv_eig", "tinv_bdsvd",
-           "tinv_plan", "tinv_tune", "tinv_tune_clear",
+           "tinv_plan", "tinv_tune", "tinv_tune_clear", "tinv_tune_save", "tinv_tune_load",
            "tinv_lu", "tinv_solve", "tinv_solve_noalloc", "tinv_orth",
            "tinv_server_cfg_default", "tinv_server_create", "tinv_submit", "tinv_poll",
            "tinv_wait", "tinv_cancel", "tinv_server_stats", "tinv_server_destroy"]
@@ -120,6 +120,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
             lib.tinv_tune.restype = ctypes.c_int
             lib.tinv_tune_clear.argtypes = []
             lib.tinv_tune_clear.restype = None
+            lib.tinv_tune_save.argtypes = [ctypes.c_char_p]
+            lib.tinv_tune_save.restype = ctypes.c_int
+            lib.tinv_tune_load.argtypes = [ctypes.c_char_p]
+            lib.tinv_tune_load.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -209,6 +213,15 @@ def tune(d, e, w, reps=2, **kw):
 
 def tune_clear():
     load().tinv_tune_clear()
+
+
+def tune_save(path: str) -> None:
+    _check(load().tinv_tune_save(os.fsencode(path)), "tinv_tune_save")
+
+
+def tune_load(path: str) -> int:
+    """Merge a saved tune cache; returns the number of entries read."""
+    return _check(load().tinv_tune_load(os.fsencode(path)), "tinv_tune_load")
 
 
 def lu(d, e, s, **kw):

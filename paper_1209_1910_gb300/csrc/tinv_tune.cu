@@ -5,11 +5,17 @@
 // team has more FP64 units but waits longer at every barrier for its slowest CTA; the automatic
 // rule gives each cluster a share of the grid proportional to its m_c^2 n work (capped at n/16
 // and kTeamMax).  The tuner measures instead: it times tinv_ex on the caller's problem once per
-// candidate cap and keeps the fastest, and caches the choice for the problem's shape.
+// candidate cap and keeps the fastest, and caches the choice for the problem's shape.  The cache
+// can be written to and read from a text file (tinv_tune_save / tinv_tune_load, or the file named
+// by the environment variable TINV_TUNE_CACHE), keyed by the device's name and SM count so that a
+// file carries over between processes and machines with the same GPU.
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -20,15 +26,15 @@ using namespace tinvx;
 
 namespace {
 
-// Shape of a problem as far as the team schedule sees it.
+// The device model and the shape of a problem as far as the team schedule sees it.
 struct TuneKey {
-    int dev;
-    int32_t method, grid;
+    std::string dev;  // device name (tabs and line breaks replaced by '_')
+    int32_t sms, method, grid;
     int64_t n, m, nclu, largest;
     bool operator<(const TuneKey& b) const
     {
-        return std::tie(dev, method, grid, n, m, nclu, largest) <
-               std::tie(b.dev, b.method, b.grid, b.n, b.m, b.nclu, b.largest);
+        return std::tie(dev, sms, method, grid, n, m, nclu, largest) <
+               std::tie(b.dev, b.sms, b.method, b.grid, b.n, b.m, b.nclu, b.largest);
     }
 };
 
@@ -38,7 +44,96 @@ struct TuneVal {
 };
 
 std::mutex g_mu;
-std::map<TuneKey, TuneVal> g_cache;
+std::map<TuneKey, TuneVal> g_cache;  // guarded by g_mu
+bool g_env_loaded = false;          // guarded by g_mu
+
+constexpr const char* kFileTag = "# tinv tune cache v1";
+
+// File format: the tag line, then one entry per line, tab-separated: device name, SM count,
+// method, grid cap, n, m, clusters with >= 2 members, largest cluster, chosen cap, milliseconds.
+int save_locked(const char* path)
+{
+    FILE* f = fopen(path, "w");
+    if (!f) return -2;
+    int ok = fprintf(f, "%s\n", kFileTag) > 0;
+    for (const auto& kv : g_cache) {
+        const TuneKey& k = kv.first;
+        ok = ok && fprintf(f, "%s\t%d\t%d\t%d\t%lld\t%lld\t%lld\t%lld\t%d\t%.6g\n", k.dev.c_str(),
+                           k.sms, k.method, k.grid, (long long)k.n, (long long)k.m,
+                           (long long)k.nclu, (long long)k.largest, kv.second.max_team,
+                           (double)kv.second.ms) > 0;
+    }
+    ok = (fclose(f) == 0) && ok;
+    return ok ? 0 : -2;
+}
+
+// Merges the file's entries into the cache; returns the number read, -2 (unreadable or not a
+// cache file) or -3 (a malformed entry: the entries before it are kept).
+int load_locked(const char* path)
+{
+    FILE* f = fopen(path, "r");
+    if (!f) return -2;
+    char line[1024];
+    if (!fgets(line, sizeof line, f) || strncmp(line, kFileTag, strlen(kFileTag)) != 0) {
+        fclose(f);
+        return -2;
+    }
+    int count = 0, rc = 0;
+    while (fgets(line, sizeof line, f)) {
+        if (line[0] == '\n' || line[0] == '\0') continue;
+        char* tab = strchr(line, '\t');
+        if (!tab || tab == line) {
+            rc = -3;
+            break;
+        }
+        TuneKey k;
+        k.dev.assign(line, (size_t)(tab - line));
+        long long n, m, nclu, largest;
+        int sms, method, grid, mt;
+        double ms;
+        char tail;
+        if (sscanf(tab + 1, "%d\t%d\t%d\t%lld\t%lld\t%lld\t%lld\t%d\t%lf %c", &sms, &method, &grid, &n,
+                   &m, &nclu, &largest, &mt, &ms, &tail) != 9 ||
+            n < 0 || m < 0 || m > n || mt < 0 || mt > kTeamMax || (method != TINV_CWY && method != TINV_MGS)) {
+            rc = -3;
+            break;
+        }
+        k.sms = sms;
+        k.method = method;
+        k.grid = grid;
+        k.n = n;
+        k.m = m;
+        k.nclu = nclu;
+        k.largest = largest;
+        g_cache[k] = TuneVal{mt, (float)ms};
+        ++count;
+    }
+    fclose(f);
+    return rc ? rc : count;
+}
+
+// The file named by TINV_TUNE_CACHE is read once, before the first lookup.
+void load_env_locked()
+{
+    if (g_env_loaded) return;
+    g_env_loaded = true;
+    const char* p = getenv("TINV_TUNE_CACHE");
+    if (p && *p) load_locked(p);
+}
+
+std::string device_name(int dev, int* sms)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        *sms = 0;
+        return std::string("unknown");
+    }
+    *sms = prop.multiProcessorCount;
+    std::string s(prop.name);
+    for (char& c : s)
+        if (c == '\t' || c == '\n' || c == '\r') c = '_';
+    return s.empty() ? std::string("unknown") : s;
+}
 
 // Clusters with >= 2 members and the largest cluster, from the plan's head indices (members of
 // a cluster are consecutive and share their head).
@@ -65,6 +160,20 @@ extern "C" void tinv_tune_clear(void)
 {
     std::lock_guard<std::mutex> g(g_mu);
     g_cache.clear();
+}
+
+extern "C" int tinv_tune_save(const char* path)
+{
+    if (!path) return -1;
+    std::lock_guard<std::mutex> g(g_mu);
+    return save_locked(path);
+}
+
+extern "C" int tinv_tune_load(const char* path)
+{
+    if (!path) return -1;
+    std::lock_guard<std::mutex> g(g_mu);
+    return load_locked(path);
 }
 
 extern "C" int tinv_tune(int64_t n, const double* d, const double* e, int64_t m, const double* w,
@@ -144,11 +253,18 @@ extern "C" int tinv_tune(int64_t n, const double* d, const double* e, int64_t m,
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
             rc = cuda_code(ce);
         }
-        TuneKey key{dev, op.method, op.grid_ctas, n, m, 0, 0};
+        TuneKey key;
+        key.dev = device_name(dev, &key.sms);
+        key.method = op.method;
+        key.grid = op.grid_ctas;
+        key.n = n;
+        key.m = m;
+        key.nclu = key.largest = 0;
         bool hit = false;
         if (!rc) {
             signature(head, &key.nclu, &key.largest);
             std::lock_guard<std::mutex> g(g_mu);
+            load_env_locked();
             auto it = g_cache.find(key);
             if (it != g_cache.end()) {
                 *max_team = it->second.max_team;
@@ -208,6 +324,8 @@ extern "C" int tinv_tune(int64_t n, const double* d, const double* e, int64_t m,
                 if (ms) *ms = best;
                 std::lock_guard<std::mutex> g(g_mu);
                 g_cache[key] = TuneVal{pick, best};
+                const char* p = getenv("TINV_TUNE_CACHE");
+                if (p && *p) save_locked(p);  // best effort: the choice is returned either way
             }
         }
         cudaStreamSynchronize(st);

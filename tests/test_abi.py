@@ -204,6 +204,40 @@ def test_tune_argument_checks(lib):
     lib.tinv_tune_clear()
 
 
+def test_tune_cache_file_round_trip(lib, tmp_path):
+    # the tune cache's file form needs no device: load, save, reload give the same entries
+    tag = "# tinv tune cache v1\n"
+    rows = ["NVIDIA GB300\t152\t0\t0\t4200\t4200\t14\t400\t0\t171.894\n",
+            "NVIDIA GB300\t152\t0\t0\t2100\t2100\t14\t200\t16\t43.15\n",
+            "NVIDIA GB300\t152\t1\t0\t210\t210\t14\t20\t0\t3.5\n"]
+    src, out, out2 = tmp_path / "a.txt", tmp_path / "b.txt", tmp_path / "c.txt"
+    src.write_text(tag + "".join(rows))
+    lib.tinv_tune_clear()
+    assert lib.tinv_tune_load(str(src).encode()) == 3
+    assert lib.tinv_tune_save(str(out).encode()) == 0
+    text = out.read_text()
+    assert text.startswith(tag) and sorted(text[len(tag):].splitlines()) == sorted(
+        r.rstrip("\n") for r in rows)
+    # the same entries again replace, they do not duplicate
+    assert binding.tune_load(str(out)) == 3
+    binding.tune_save(str(out2))
+    assert out2.read_text() == text
+    # errors: NULL path, missing file, no tag line, a malformed entry (earlier entries kept)
+    assert lib.tinv_tune_save(None) == -1 and lib.tinv_tune_load(None) == -1
+    assert lib.tinv_tune_load(str(tmp_path / "missing.txt").encode()) == -2
+    (tmp_path / "notag.txt").write_text("".join(rows))
+    assert lib.tinv_tune_load(str(tmp_path / "notag.txt").encode()) == -2
+    lib.tinv_tune_clear()
+    bad = tmp_path / "bad.txt"
+    bad.write_text(tag + rows[0] + "NVIDIA GB300\t152\t0\t0\t10\t20\t1\t2\t0\t1.0\n" + rows[1])
+    assert lib.tinv_tune_load(str(bad).encode()) == -3  # m > n
+    assert lib.tinv_tune_save(str(out).encode()) == 0
+    assert out.read_text() == tag + rows[0]
+    lib.tinv_tune_clear()
+    assert lib.tinv_tune_save(str(out).encode()) == 0 and out.read_text() == tag
+    assert lib.tinv_tune_save(str(tmp_path / "no" / "such" / "dir.txt").encode()) == -2
+
+
 def test_server_config_and_null_checks(lib):
     c = binding.ServerCfg()
     lib.tinv_server_cfg_default(ctypes.byref(c))

@@ -1,7 +1,8 @@
 """The team-cap autotuner (tinv_tune through the C ABI): its choice is the automatic rule or a
 power-of-two cap, a repeated call on the same shape is served from the tune cache without running
 anything, a different spectrum of the same order is a different key, MGS has nothing to tune, and
-a call with the chosen cap meets the residual and orthogonality bounds."""
+a call with the chosen cap meets the residual and orthogonality bounds, and choices saved to a
+file and loaded again are served from the cache."""
 import numpy as np
 import pytest
 
@@ -23,7 +24,7 @@ def gpu():
     return binding
 
 
-def test_tune_choice_cache_and_bounds(gpu, orc):
+def test_tune_choice_cache_and_bounds(gpu, orc, tmp_path):
     d, e = inputs.glued_wilkinson(100, 1e-10)  # n = 2100: 7 clusters of 200 and 400 members
     w = orc.bisect(d, e)
     gpu.tune_clear()
@@ -39,9 +40,20 @@ def test_tune_choice_cache_and_bounds(gpu, orc):
     w3 = orc.bisect(d3, e3)
     _, _, cached3 = gpu.tune(d3, e3, w3, reps=1)
     assert not cached3
+    # the cache through a file: the device-name keys written by tinv_tune_save match the keys a
+    # later tinv_tune builds, so reloaded choices are served without timing
+    path = str(tmp_path / "tune.txt")
+    gpu.tune_save(path)
+    lines = open(path).read().splitlines()
+    assert lines[0] == "# tinv tune cache v1" and len(lines) == 3
     gpu.tune_clear()
     _, _, cached4 = gpu.tune(d, e, w, reps=1)
     assert not cached4
+    gpu.tune_clear()
+    assert gpu.tune_load(path) == 2
+    mt5, ms5, cached5 = gpu.tune(d, e, w, reps=1)
+    assert cached5 and mt5 == mt
+    gpu.tune_clear()
 
 
 def test_tune_mgs_keeps_the_automatic_rule(gpu, orc):
