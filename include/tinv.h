@@ -163,8 +163,11 @@ int tinv_tune_save(const char* path);
 /*
  * tinv_tune_load -- merge the entries of a file written by tinv_tune_save into the tune cache
  * (an entry with the same key is replaced).  Returns the number of entries read (>= 0), -1 (path
- * NULL), -2 (the file cannot be read or lacks the tag line) or -3 (a malformed entry: the
- * entries before it are kept, the rest of the file is not read).  No device is needed.
+ * NULL), -2 (the file cannot be read or lacks the tag line) or -3 (a malformed entry -- a
+ * missing or non-numeric field, trailing text, a line longer than 1023 bytes, or a value out of
+ * range: SM count <= 0, m > n, largest cluster > m, cap outside [0, 192], time negative or not
+ * finite, unknown method; the entries before it are kept, the rest of the file is not read).
+ * No device is needed.
  */
 int tinv_tune_load(const char* path);
 

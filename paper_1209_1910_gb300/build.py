@@ -33,23 +33,32 @@ def _deps():
 
 
 def build(force: bool = False, verbose: bool = False, debug: bool = False,
-          profile: bool = False) -> str:
-    """Compile libtinv.so (or, with profile=True, the phase-timing diagnostic variant
-    libtinv_prof.so, which prints per-CTA phase cycle counts of the cluster kernel)."""
-    lib = LIB.replace("libtinv.so", "libtinv_prof.so") if profile else LIB
-    objdir = OBJDIR + ("_prof" if profile else "")
+          profile: bool = False, sanitize: bool = False) -> str:
+    """Compile libtinv.so, or a diagnostic variant with its own library file and objects:
+    profile=True gives libtinv_prof.so (per-CTA phase cycle counts of the cluster kernel),
+    debug=True libtinv_debug.so (device bounds checks, TINV_DEBUG), sanitize=True
+    libtinv_asan.so (host code under AddressSanitizer and UBSan; load it with the ASan runtime
+    preloaded).  Variants combine, e.g. libtinv_debug_asan.so."""
+    suffix = ("_prof" if profile else "") + ("_debug" if debug else "") + ("_asan" if sanitize else "")
+    lib = LIB.replace("libtinv.so", "libtinv%s.so" % suffix)
+    objdir = OBJDIR + suffix
     if not force and os.path.exists(lib):
         if os.path.getmtime(lib) >= max(os.path.getmtime(f) for f in _deps()):
             return lib
     os.makedirs(objdir, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                     "--expt-relaxed-constexpr", "-I", INCLUDE]
+    # one flag per option: -Xcompiler splits its argument at commas
+    san = ["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined",
+           "-Xcompiler", "-fno-omit-frame-pointer"]
     if verbose:
         flags += ["-Xptxas", "-v"]
     if debug:
         flags += ["-DTINV_DEBUG=1"]
     if profile:
         flags += ["-DTINV_PHASE_PROFILE=1"]
+    if sanitize:
+        flags += san
 
     def compile_one(src):
         obj = os.path.join(objdir, src.replace(".cu", ".o"))
@@ -64,7 +73,7 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False,
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = lib + ".%d.tmp" % os.getpid()
-    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
+    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"] + (san if sanitize else [])
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -94,7 +94,9 @@ int load_locked(const char* path)
         char tail;
         if (sscanf(tab + 1, "%d\t%d\t%d\t%lld\t%lld\t%lld\t%lld\t%d\t%lf %c", &sms, &method, &grid, &n,
                    &m, &nclu, &largest, &mt, &ms, &tail) != 9 ||
-            n < 0 || m < 0 || m > n || mt < 0 || mt > kTeamMax || (method != TINV_CWY && method != TINV_MGS)) {
+            sms <= 0 || grid < 0 || n < 0 || m < 0 || m > n || nclu < 0 || largest < 0 ||
+            largest > m || mt < 0 || mt > kTeamMax || !(ms >= 0.0 && ms < 1e30) ||
+            (method != TINV_CWY && method != TINV_MGS)) {
             rc = -3;
             break;
         }
