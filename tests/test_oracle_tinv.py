@@ -130,3 +130,29 @@ def test_edge_cases(orc):
     Z, info, *_ = orc.tinv(d, e, w[10:30], "cwy", j0=10)
     assert Z.shape == (50, 20) and info == 0
     assert residual_ratio(d, e, w[10:30], Z) <= 10
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_sweep_counts_pin_extra_and_maxits(orc, method):
+    # DSTEIN's structure (reading c3): a vector stops after its first sweep that passes the growth
+    # test ||x||_inf >= sqrt(0.1/n) plus EXTRA = 2 more, or after MAXITS = 5 sweeps.  On these
+    # inputs every first sweep passes, so every vector takes exactly 1 + EXTRA sweeps.
+    for case in ("uniform300", "glued420", "zero301"):
+        d, e = CASES[case]
+        w = orc.bisect(d, e)
+        _, info, _, iters, _ = orc.tinv(d, e, w, method)
+        assert info == 0 and np.all(iters == 3), (case, np.bincount(iters))
+    # A simple eigenvalue asked for twice (or three times): the later copies are orthogonalized
+    # against the eigenvector already found and no other eigenvector lies within the cluster
+    # tolerance, so their iterates never grow; they run MAXITS sweeps and are reported in ifail.
+    d, e = inputs.uniform(50, seed=4)
+    w = orc.bisect(d, e)
+    for copies in (2, 3):
+        ww = np.full(copies, w[10])
+        Z, info, ifail, iters, _ = orc.tinv(d, e, ww, method)
+        assert info == copies - 1 and ifail.tolist() == list(range(1, copies))
+        assert iters[0] == 3 and np.all(iters[1:] == 5)
+        assert np.allclose(np.linalg.norm(Z, axis=0), 1.0, atol=1e-14)
+        assert np.abs(Z[:, 0] @ Z[:, 1:]).max() <= 1e-12
+        Zs = orc.tinv(d, e, w[10:11], method, j0=0)[0]
+        assert np.abs(np.abs(Z[:, 0] @ Zs[:, 0]) - 1.0) <= 1e-12
