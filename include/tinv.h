@@ -15,14 +15,16 @@
  *   - Unless tinv_opts.device_ptrs is set, every pointer is HOST memory owned by the caller;
  *     the call copies inputs to the GPU, runs, copies results back and synchronizes.
  *     With device_ptrs set, every array pointer is DEVICE memory of the current device, the
- *     work is enqueued on tinv_opts.stream and the call returns without synchronizing.
+ *     work is enqueued on tinv_opts.stream and the call returns without synchronizing (except
+ *     tinv_tune, and calls given tinv_opts.phase_ms, which synchronize).
  *   - Return codes: 0 = success; -k = argument k is invalid (1-based position in the call);
  *     > 0 = number of eigenvectors that did not converge within MAXITS = 5 sweeps (their
  *     columns are still written, as LAPACK DSTEIN does); values <= -100 are runtime errors
  *     listed below.  tinv_strerror() gives a message for any code.
  *   - Thread safety: calls on different streams may run concurrently from different host
  *     threads; the library keeps no global mutable state besides a per-device cache of the
- *     number of SMs, and the shared scratch of tinv_solve_noalloc (see there).
+ *     number of SMs, the tune cache of tinv_tune (guarded by a lock), and the shared scratch
+ *     of tinv_solve_noalloc (see there).
  */
 #ifndef TINV_H
 #define TINV_H
