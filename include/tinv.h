@@ -15,8 +15,9 @@
  *   - Unless tinv_opts.device_ptrs is set, every pointer is HOST memory owned by the caller;
  *     the call copies inputs to the GPU, runs, copies results back and synchronizes.
  *     With device_ptrs set, every array pointer is DEVICE memory of the current device, the
- *     work is enqueued on tinv_opts.stream and the call returns without synchronizing (except
- *     tinv_tune, and calls given tinv_opts.phase_ms, which synchronize).
+ *     work is enqueued on tinv_opts.stream and the call returns without synchronizing, except
+ *     where an entry point says otherwise (tinv_split, tinv_eig, tinv_bdsvd and tinv_tune form
+ *     host-side tables or timings; any call given tinv_opts.phase_ms).
  *   - Return codes: 0 = success; -k = argument k is invalid (1-based position in the call);
  *     > 0 = number of eigenvectors that did not converge within MAXITS = 5 sweeps (their
  *     columns are still written, as LAPACK DSTEIN does); values <= -100 are runtime errors
