@@ -25,7 +25,7 @@ def gpu():
 
 
 def test_tune_choice_cache_and_bounds(gpu, orc, tmp_path):
-    d, e = inputs.glued_wilkinson(100, 1e-10)  # n = 2100: 7 clusters of 200 and 400 members
+    d, e = inputs.glued_wilkinson(100, 1e-10)  # n = 2100: 7 clusters of 200 and 7 of 100 members
     w = orc.bisect(d, e)
     gpu.tune_clear()
     mt, ms, cached = gpu.tune(d, e, w, reps=1)
