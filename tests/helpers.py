@@ -58,3 +58,35 @@ def sign_fix(Z):
     s = np.sign(Z[idx, np.arange(Z.shape[1])])
     s[s == 0] = 1
     return Z * s
+
+
+def first_max_ties(z, rel=1e-8):
+    """True when the first entry of largest magnitude of z is not clear-cut: another entry's
+    magnitude is within a relative `rel` of the largest (rounding can then pick either)."""
+    a = np.abs(np.asarray(z))
+    top = a.max()
+    return int(np.sum(a >= top * (1.0 - rel))) > 1
+
+
+def check_sign_convention(Z):
+    """DSTEIN's convention on every column that has a clear-cut first entry of largest
+    magnitude: that entry is positive.  Returns the number of columns checked."""
+    Z = np.asarray(Z)
+    checked = 0
+    for j in range(Z.shape[1]):
+        z = Z[:, j]
+        if first_max_ties(z):
+            continue
+        assert z[int(np.argmax(np.abs(z)))] > 0.0, j
+        checked += 1
+    return checked
+
+
+def singleton_equal(zg, zo, tol):
+    """A singleton's vector against the oracle's, WITHOUT re-applying the sign convention:
+    equal within tol when the oracle's first largest entry is clear-cut (so both sides must have
+    chosen the same sign), equal up to sign otherwise."""
+    zg, zo = np.asarray(zg).ravel(), np.asarray(zo).ravel()
+    if first_max_ties(zo):
+        return min(np.abs(zg - zo).max(), np.abs(zg + zo).max()) <= tol
+    return np.abs(zg - zo).max() <= tol

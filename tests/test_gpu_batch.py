@@ -9,7 +9,7 @@ teams the reduction shapes differ and the subspaces agree within 1e-10.
 import numpy as np
 import pytest
 
-from helpers import clusters_from_heads, orth_ratio, residual_ratio, sign_fix, sin_angle
+from helpers import clusters_from_heads, orth_ratio, residual_ratio, sin_angle, singleton_equal
 from paper_1209_1910_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -47,7 +47,7 @@ SIZES = [1, 2, 7, 21, 64, 105, 200, 420, 333, 63, 1000, 210]
 def _compare(Z, Zo, head, tol=1e-10):
     for idx in clusters_from_heads(head):
         if len(idx) == 1:
-            assert np.abs(sign_fix(Z[:, idx]) - sign_fix(Zo[:, idx])).max() <= tol, idx[0]
+            assert singleton_equal(Z[:, idx[0]], Zo[:, idx[0]], tol), idx[0]
         else:
             assert sin_angle(Zo[:, idx], Z[:, idx]) <= tol, (idx[0], len(idx))
 
@@ -90,7 +90,7 @@ def test_batch_with_teams_matches_single_calls(gpu):
         wp, head, _ = gpu.plan(d, e, w)  # clusters of the single call's plan
         for idx in clusters_from_heads(head):
             if len(idx) == 1:
-                assert np.abs(sign_fix(Z[:, idx]) - sign_fix(Z1[:, idx])).max() <= 1e-10
+                assert singleton_equal(Z[:, idx[0]], Z1[:, idx[0]], 1e-10)
             else:
                 assert sin_angle(Z1[:, idx], Z[:, idx]) <= 1e-10
 

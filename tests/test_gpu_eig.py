@@ -6,7 +6,7 @@ convention, clusters by the largest principal angle <= 1e-10)."""
 import numpy as np
 import pytest
 
-from helpers import clusters_from_heads, orth_ratio, residual_ratio, sign_fix, sin_angle
+from helpers import clusters_from_heads, orth_ratio, residual_ratio, sin_angle, singleton_equal
 from paper_1209_1910_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -54,7 +54,7 @@ def _check(orc, d, e, w, Z, ib, isp, info, method="cwy"):
         for idx in clusters_from_heads(head):
             c = cols[idx]
             if len(idx) == 1:
-                assert np.abs(sign_fix(Z[s:t, c]) - sign_fix(Zo[s:t, c])).max() <= 1e-10, (b, c)
+                assert singleton_equal(Z[s:t, c], Zo[s:t, c], 1e-10), (b, c)
             else:
                 assert sin_angle(Zo[s:t, c], Z[s:t, c]) <= 1e-10, (b, len(idx))
 

@@ -6,7 +6,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import EPS, clusters_from_heads, sign_fix
+from helpers import EPS, clusters_from_heads, singleton_equal
 from paper_1209_1910_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -87,4 +87,4 @@ def test_uniform_10000_invariants_and_singletons(gpu, orc):
         zo, oinfo, *_ = orc.tinv(d, e, w[j:j + 1], "cwy", j0=j)
         assert oinfo == 0
         z = Zt[j].cpu().numpy()[:, None]
-        assert np.abs(sign_fix(z) - sign_fix(zo)).max() <= 1e-10, j
+        assert singleton_equal(z, zo, 1e-10), j

@@ -30,12 +30,9 @@ def gpu():
 
 
 def _ok(d, e, w, Z):
-    """Residual and orthogonality invariants: 10 n eps for uniform matrices; for glued Wilkinson
-    matrices the method itself (the oracle too, depending on the start vectors) exceeds that
-    between nearly coincident clusters, so those are held to 100 n eps, as the n = 4200 case."""
-    glued = len(d) % 21 == 0 and np.all(d[:21] == np.abs(11.0 - np.arange(1, 22)))
-    lim = 100 if glued else 10
-    return residual_ratio(d, e, w, Z) <= lim and orth_ratio(Z) <= lim
+    """The invariants of a correct eigenvector set: residual <= 10 n eps ||T||_1 and
+    orthogonality <= 10 n eps."""
+    return residual_ratio(d, e, w, Z) <= 10 and orth_ratio(Z) <= 10
 
 
 def _mix(count, seed, lo=40, hi=700):
@@ -166,3 +163,38 @@ def test_server_concurrent_submitters(gpu):
     for q, (Z, info) in res.items():
         d, e, w = probs[q]
         assert info == 0 and _ok(d, e, w, Z)
+
+
+def test_server_cancel_is_exclusive_with_delivery(gpu):
+    # A cancel that races with the copy of a finished wave's result into Z: either it succeeds
+    # (returns 0) and Z is never written, or it reports the request as completed (1) and the
+    # request delivers a full result.  Cancels are issued at spread-out times around the end of
+    # the wave, so some land during the copy into the caller's buffer.
+    d, e = inputs.glued_wilkinson(60, 1e-10)  # n = 1260: a 12.7 MB result per request
+    w = inputs.eigenvalues(d, e)
+    sentinel = 123.0
+    outcomes = set()
+    with gpu.Server(max_inflight=1) as srv:
+        _, info = srv.wait(srv.submit(d, e, w))  # warm-up, and the wave's duration
+        assert info == 0
+        t0 = time.perf_counter()
+        srv.wait(srv.submit(d, e, w))
+        dur = time.perf_counter() - t0
+        for k in range(24):
+            Z = np.full((len(d), len(d)), sentinel, order="F")
+            t = srv.submit(d, e, w, out=Z)
+            time.sleep(dur * (0.6 + 0.05 * k))
+            rc = srv.cancel(t)
+            assert rc in (0, 1), rc
+            outcomes.add(rc)
+            if rc == 0:
+                with pytest.raises(gpu.TinvError) as ex:
+                    srv.wait(t)
+                assert ex.value.code == -105  # TINV_ECANCELED
+                time.sleep(0.01)
+                assert np.all(Z == sentinel), k  # never written, not even partly
+            else:
+                Zr, info = srv.wait(t)
+                assert info == 0 and not np.any(Zr == sentinel)
+                assert _ok(d, e, w, Zr)
+    assert outcomes  # at least one cancel was decided

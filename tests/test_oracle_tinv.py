@@ -6,7 +6,8 @@ import numpy as np
 import pytest
 import scipy.linalg.lapack as lapack
 
-from helpers import EPS, clusters_from_heads, dense, orth_ratio, residual_ratio, sign_fix, sin_angle
+from helpers import (EPS, clusters_from_heads, dense, orth_ratio, residual_ratio, sign_fix, sin_angle,
+                     singleton_equal)
 from paper_1209_1910_gb300 import inputs
 
 METHODS = ["cwy", "mgs", "house"]
@@ -94,7 +95,9 @@ def test_lapack_dstein_black_box(orc, case):
     for idx in clusters_from_heads(head):
         assert sin_angle(Zl[:, idx], Z[:, idx]) < 1e-10
         if len(idx) == 1:
-            assert np.abs(sign_fix(Z[:, idx]) - sign_fix(Zl[:, idx])).max() < 1e-10
+            # DSTEIN's own final normalization makes the first largest entry positive, as the
+            # oracle does (reading c12): compared as computed, not re-applied
+            assert singleton_equal(Z[:, idx[0]], Zl[:, idx[0]], 1e-10)
 
 
 @pytest.mark.parametrize("method", METHODS)
@@ -156,3 +159,14 @@ def test_sweep_counts_pin_extra_and_maxits(orc, method):
         assert np.abs(Z[:, 0] @ Z[:, 1:]).max() <= 1e-12
         Zs = orc.tinv(d, e, w[10:11], method, j0=0)[0]
         assert np.abs(np.abs(Z[:, 0] @ Zs[:, 0]) - 1.0) <= 1e-12
+
+
+@pytest.mark.parametrize("blocks", [100, 148])
+def test_lapack_dstein_meets_the_bounds_on_glued_wilkinson(blocks):
+    # The paper's baseline (LAPACK's bisection and DSTEIN, run as a black box through SciPy)
+    # meets the invariant bounds 10 n eps on the glued Wilkinson matrices, so the GPU parity
+    # tests hold the library to them there as everywhere else.
+    sl = pytest.importorskip("scipy.linalg")
+    d, e = inputs.glued_wilkinson(blocks, 1e-10)
+    w, Z = sl.eigh_tridiagonal(d, e, lapack_driver="stebz")
+    assert residual_ratio(d, e, w, Z) <= 10 and orth_ratio(Z) <= 10
