@@ -58,8 +58,8 @@ LAUNCHES = {"cwy": 8, "mgs": 7}
 # half split (tinv_bdsvd)
 DRIVER_EXTRA_LAUNCHES = {"split4200": 3, "bidiag2000": 3}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (vector and tensor alike), TFLOP/s
-# DRAM bytes (read + write) of one cluster-kernel launch, from ncu on the current kernels
-# (profiles/launches_glued4200_cwy.md); None where no capture exists
+# DRAM bytes (read + write) of one cluster-kernel launch, from one ncu capture of the current
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum); None where no capture exists
 TRAFFIC_BYTES = {("glued4200", "cwy"): 33.09e9}
 
 
@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--phases", action="store_true",
+                    help="phase timing of the cluster kernel (diagnostic build), no bench line")
+    ap.add_argument("--phases-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -484,7 +487,7 @@ def batch_arm(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                      "kernel": "k_chain", "kernel_ms": kern_ms, "flops_per_launch": flops,
-                     "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (derived in the design notes)",
+                     "peak_source": "nominal GB300 FP64: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz = 1.26 TFLOP/s",
                      "phase_ms": {"plan": float(phase[0]), "lu": float(phase[1]),
                                   "first": float(phase[2]), "chain": float(phase[3])}},
         "gpu_launches": LAUNCHES[args.method] * args.steps,
@@ -838,7 +841,7 @@ def driver_arm(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                      "kernel": "k_chain", "kernel_ms": kern_ms, "flops_per_launch": flops,
-                     "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (derived in the design notes)",
+                     "peak_source": "nominal GB300 FP64: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz = 1.26 TFLOP/s",
                      "phase_ms": {"plan": float(phase[0]), "lu": float(phase[1]),
                                   "first": float(phase[2]), "chain": float(phase[3])}},
         "gpu_launches": (LAUNCHES[args.method] + DRIVER_EXTRA_LAUNCHES[args.workload]) * args.steps,
@@ -976,7 +979,7 @@ def ours_arm(args):
             "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": TRAFFIC_BYTES.get((args.workload, args.method)), "kernel": "k_chain",
             "kernel_ms": kern_ms, "flops_per_launch": flops,
-            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (derived in the design notes)",
+            "peak_source": "nominal GB300 FP64: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz = 1.26 TFLOP/s",
             "phase_ms": {"plan": float(phase[0]), "lu": float(phase[1]),
                          "first": float(phase[2]), "chain": float(phase[3])}}
 
@@ -1052,8 +1055,76 @@ def ours_arm(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------------------------------
+# phase timing of the cluster kernel (diagnostic: a separate library file, libtinv_prof.so,
+# compiled with -DTINV_PHASE_PROFILE; thread 0 of every CTA of the cluster kernel adds clock64
+# cycles per phase and prints them when the CTA ends)
+# ------------------------------------------------------------------------------------------
+PHASES = ["total", "solve", "A", "b1", "T1red", "T1", "b2", "Bload", "Brow", "Bsum", "B", "b3",
+          "T2refl", "T2row", "T2", "b4", "Cload", "Crow", "C", "b5", "load", "end"]
+
+
+def _phases_child(args):
+    from paper_1209_1910_gb300 import binding, build
+
+    path = build.build(profile=True)
+    binding.load(path)
+    d, e, w = inputs.workload(args.workload)
+    ph = np.zeros(4, dtype=np.float32)
+    binding.tinv(d, e, w, method=args.method, phase_ms=ph.ctypes.data)
+    print("PHASES_MS plan=%.3f lu=%.3f first=%.3f chain=%.3f" % tuple(ph.tolist()), flush=True)
+
+
+def summarize_phases(text: str):
+    """Per team size G: the slowest team's mean phase cycles over its CTAs, the number of teams
+    of that size and the slowest team's index, from the PROF lines of a diagnostic run; and the
+    line with the kernels' event times."""
+    import collections
+    import re
+
+    teams = collections.defaultdict(list)
+    chain = ""
+    for line in text.splitlines():
+        if line.startswith("PHASES_MS"):
+            chain = line
+        if not line.startswith("PROF "):
+            continue
+        kv = {k: int(v) for k, v in re.findall(r"(\w+)=(-?\d+)", line)}
+        if kv.get("team", -1) >= 0:
+            teams[(kv["team"], kv["G"])].append(kv)
+    by_g = collections.defaultdict(list)
+    for (team, g), rows in teams.items():
+        mean = {p: sum(r.get(p, 0) for r in rows) / len(rows) for p in PHASES}
+        by_g[g].append((mean["total"], team, mean))
+    out = {}
+    for g, lst in by_g.items():
+        lst.sort(reverse=True)
+        out[g] = (lst[0][1], len(lst), lst[0][2])
+    return out, chain
+
+
+def phases_arm(args):
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--phases-child",
+                        "--workload", args.workload, "--method", args.method],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(r.stdout[-4000:] + r.stderr[-4000:])
+        raise SystemExit(r.returncode)
+    res, chain = summarize_phases(r.stdout)
+    print("workload %s, method %s; %s" % (args.workload, args.method, chain))
+    print("slowest team of each size, mean over its CTAs, millions of SM cycles:")
+    for g in sorted(res):
+        team, count, mean = res[g]
+        print("G=%d (%d teams, slowest %d): " % (g, count, team) +
+              " ".join("%s=%.1f" % (p, mean[p] / 1e6) for p in PHASES))
+
+
 def main():
     args = parse()
+    if args.phases_child:
+        return _phases_child(args)
+    if args.phases:
+        return phases_arm(args)
     if args.impl == "reference":
         reference_arm(args)
     else:

@@ -22,7 +22,7 @@
  *   orc_tinv            -- classical inverse iteration (Alg. 1) and DSTEIN-cWY (Alg. 4).
  *   orc_jacobi          -- cyclic Jacobi (Golub & Van Loan), brute force for small n.
  *
- * Readings of points the paper leaves open (each is also listed in the design notes):
+ * Readings of points the paper leaves open:
  *   - q_j is formed with T_j, not T_j^T (Sec. 3.3.1/3.3.2 print T^T; Eq. cwy2 needs T).
  *   - the first q of Alg. 3 is formed with e_1 (printed e_j).
  *   - "Normalize v" before the solve is DSTEIN's 1-norm scaling

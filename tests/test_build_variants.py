@@ -1,6 +1,6 @@
 """The diagnostic builds of the library compile and export the same C ABI as the product build
 (CPU only; nothing is launched): the TINV_DEBUG variant with device bounds checks and the
-phase-timing variant used by `python -m paper_1209_1910_gb300.phase_profile`.  Each variant has
+phase-timing variant used by `python bench.py --phases`.  Each variant has
 its own library file, so building one never replaces the product library."""
 import ctypes
 import os

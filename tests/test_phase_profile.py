@@ -1,5 +1,7 @@
-"""The phase-timing summary (CPU): per team size, the slowest team's mean over its CTAs."""
-from paper_1209_1910_gb300.phase_profile import PHASES, summarize
+"""The phase-timing summary of `bench.py --phases` (CPU): per team size, the slowest team's mean
+over its CTAs."""
+import bench
+from bench import PHASES
 
 
 def _line(cta, team, g, total, solve):
@@ -18,7 +20,7 @@ def test_summary_picks_the_slowest_team_of_each_size():
         _line(5, -1, 1, 999, 999),                             # a queue CTA: not a team
         "unrelated output",
     ])
-    res, chain = summarize(text)
+    res, chain = bench.summarize_phases(text)
     assert chain.startswith("PHASES_MS") and "chain=4.000" in chain
     assert sorted(res) == [1, 2]
     team, count, mean = res[2]
