@@ -331,10 +331,13 @@ int tinv_solve(int64_t n, const double* d, const double* e, int64_t m, const dou
  * Scratch: a fixed 20 MiB array in device memory, part of the library image (every GPU that
  * loads the library holds it until the process exits); it takes m * n <= 262144 and
  * m <= 131072 (for example 512 shifts of order 512).  Larger sizes return TINV_ENOTSUP.  The
- * call performs no cudaMalloc or cudaFree.  The first call on a device looks up the array's device address (with that
- * device current) and caches it; make that first call before any stream capture.  All calls on
- * a device share the array and it keeps the last call's contents (each call writes every entry
- * it reads), so calls whose work overlaps on the GPU race: serialize them, e.g. on one stream.
+ * call performs no cudaMalloc or cudaFree.  The first call in a CUDA context (the device's
+ * primary context, or a driver context the caller made current) looks up the array's device
+ * address in that context and caches it under the context's unique id; make that first call
+ * before any stream capture.  All calls on a device share the array and it keeps the last call's
+ * contents (each call writes every entry it reads), so calls whose work overlaps on the GPU race:
+ * serialize them, e.g. on one stream.  X is written only in its rows [0, n) of each of its m
+ * columns; the rows n..ldx-1 are left untouched.
  */
 int tinv_solve_noalloc(int64_t n, const double* d, const double* e, int64_t m, const double* s,
                        double* X, int64_t ldx, int32_t scale, void* stream);
@@ -354,11 +357,19 @@ int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int
  * Serving: a request queue with continuous batching.  The paper has no counterpart; it serves
  * many independent problems (each the problem of Sec. 2.1) arriving over time through the
  * batched path.  A worker thread owns the GPU: whenever one of its max_inflight streams is free
- * it admits the pending requests in arrival order, as far as max_slots and the memory budget
- * allow, and runs them as one wave (bisection for requests without eigenvalues, then the batched
- * inverse iteration of tinv_batch); waves on different streams overlap on the device (each
- * wave's persistent cluster kernel holds its share of the SMs, wave_ctas), so a request that
- * arrives while others are on the GPU starts as soon as a stream and memory free up.
+ * and at least one stream's share of the SMs (wave_ctas) is free, it forms a wave from the
+ * pending requests and runs it (bisection for requests without eigenvalues, then the batched
+ * inverse iteration of tinv_batch).  Requests are taken in arrival order until the wave holds
+ * its share of the pending work (the free streams divide it; a request's work counts as n^3);
+ * a request that does not fit max_slots or the memory budget right now is passed over, so
+ * smaller requests behind it go first, but once 8 waves have passed it over it blocks the
+ * requests behind it until it fits.  The memory budget is re-read at every admission:
+ * hbm_fraction x (device memory free now + the estimate held by the server's waves in flight),
+ * 57 n^2 + O(n) bytes per request.  The wave's persistent cluster kernel gets the free SMs in
+ * proportion to its share of the pending work; a wave that empties the queue leaves one share
+ * free for later arrivals while other streams are idle.  The grids of the waves in flight never
+ * exceed the SM count, so their kernels are co-resident and overlap on the device, and a request
+ * that arrives while others are on the GPU starts as soon as a stream, SMs and memory free up.
  * A problem's result does not depend on the other problems of its wave except through the CTA
  * team a large cluster gets (rounding only); with max_team = 1 it is bit-identical to a tinv_ex
  * call with the same seed.
@@ -367,16 +378,18 @@ typedef struct tinv_server tinv_server; /* opaque */
 
 typedef struct tinv_server_cfg {
     int32_t max_slots;    /* most problems on the GPU at once (default 4096)                  */
-    int32_t max_inflight; /* most waves in flight at once, one stream each (default 2, <= 8)  */
-    double hbm_fraction;  /* share of the device memory free at creation that the server may  */
-                          /*   use for waves (default 0.5, < 0.95)                             */
+    int32_t max_inflight; /* most waves in flight at once, one stream each (default 4, <= 8)  */
+    double hbm_fraction;  /* share of the free device memory (re-read at each admission, plus  */
+                          /*   what the server's waves hold) that waves may use (default 0.5,  */
+                          /*   < 0.95); tinv_submit refuses a request above this share of the  */
+                          /*   memory free at creation                                         */
     int32_t method;       /* TINV_CWY (default) or TINV_MGS                                    */
     int32_t max_team;     /* as tinv_opts.max_team                                             */
     int32_t max_pending;  /* queued requests beyond which tinv_submit returns TINV_EAGAIN      */
                           /*   (default 65536)                                                 */
     int32_t device;       /* CUDA device ordinal                                               */
-    int32_t wave_ctas;    /* SMs (persistent CTAs) of one wave's cluster kernel; 0 = the SM    */
-                          /*   count / max_inflight, so concurrent waves split the GPU         */
+    int32_t wave_ctas;    /* one stream's share of the SMs (persistent CTAs of a wave's       */
+                          /*   cluster kernel, at least); 0 = the SM count / max_inflight      */
     int32_t reserved[7];
 } tinv_server_cfg;
 
@@ -429,8 +442,10 @@ int tinv_poll(tinv_server* srv, uint64_t ticket, int32_t* state);
 int tinv_wait(tinv_server* srv, uint64_t ticket, int32_t timeout_ms, int64_t* info);
 
 /* Cancel a request: a pending one is removed from the queue at once; a running one finishes on
- * the GPU but its result is not written.  Returns 0, TINV_ECANCELED if it was already cancelled,
- * 1 if it had already completed, -2 for an unknown ticket. */
+ * the GPU but its result is not written.  Returns 0 (Z will not be written by the server),
+ * TINV_ECANCELED if it was already cancelled, 1 if it had already completed or its result is
+ * being copied into Z (the request then completes normally and Z must stay valid until
+ * tinv_wait returns), -2 for an unknown ticket. */
 int tinv_cancel(tinv_server* srv, uint64_t ticket);
 
 /* Counters and latency percentiles so far. */

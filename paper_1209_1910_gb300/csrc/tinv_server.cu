@@ -1,14 +1,19 @@
 // tinv_server.cu -- request-queue API with continuous batching (tinv_server_* in tinv.h).
 //
-// Callers submit eigenvector problems of any order at any time.  A worker thread owns the GPU:
-// whenever one of its streams is free it takes the pending requests in arrival order, as many as
-// the slot limit and the memory budget admit, and enqueues them as one wave: host-to-device copy
-// of the packed inputs, Sturm bisection for requests that came without eigenvalues, the batched
-// inverse-iteration path (tinv_batch's device form, one problem table for the wave) and the copy
-// of the eigenvectors back to pinned staging.  Up to max_inflight waves run at once on separate
-// streams, so requests that arrive while a wave is on the GPU start in the next wave without
-// waiting for the first to finish, and the waves' kernels and copies overlap on the device.  A
-// completed wave's vectors are copied into the callers' buffers and their requests complete.
+// Callers submit eigenvector problems of any order at any time.  A worker thread owns the GPU.
+// Whenever one of its streams is free and enough SMs are free, it forms a wave from the pending
+// requests: in arrival order, skipping requests that do not fit the slot limit or the memory
+// budget right now (so small requests pass a large one that waits for memory; a request passed
+// over too often stops the others from passing it), until the wave holds its share of the
+// pending work.  The memory budget is re-read at every admission (hbm_fraction of the device
+// memory free now plus what the server's own waves hold).  The wave is enqueued on its stream:
+// host-to-device copy of the packed inputs, Sturm bisection for requests that came without
+// eigenvalues, the batched inverse-iteration path (tinv_batch's device form, one problem table
+// for the wave) with a persistent grid sized from the free SMs, and the copy of the
+// eigenvectors back to pinned staging.  Up to max_inflight waves run at once, so requests that
+// arrive while waves are on the GPU start as soon as a stream and SMs free up, and the waves'
+// kernels and copies overlap on the device.  A completed wave's vectors are copied into the
+// callers' buffers and their requests complete.
 #include <math.h>
 #include <string.h>
 
@@ -40,6 +45,8 @@ struct Req {
     uint64_t seed = 0;
     int32_t state = TINV_REQ_PENDING;
     bool cancel = false;          // cancelled while running: the result is dropped
+    bool delivering = false;      // the result is being copied to Z: too late to cancel
+    int skipped = 0;              // admissions that passed over this request
     int64_t info = 0;
     int rc = 0;
     size_t bytes = 0;             // device bytes the request adds to a wave
@@ -60,6 +67,7 @@ struct Staging {
 struct Wave {
     std::vector<ReqP> reqs;
     int slot = 0;
+    int ctas = 0;       // persistent CTAs (SMs) of the wave's cluster kernel
     size_t bytes = 0;
     int rc = 0;
     std::atomic<bool> finished{false};
@@ -89,6 +97,17 @@ size_t request_bytes(int64_t n)
     return (size_t)(57.0 * nn * nn + 256.0 * nn + 4096.0);
 }
 
+// Work estimate of a request for dividing the pending requests among waves and SMs: the
+// reorthogonalization grows as (cluster size)^2 n, at most n^3.
+double request_work(int64_t n)
+{
+    const double nn = (double)n;
+    return nn * nn * nn + 1.0e6;
+}
+
+// Admissions that may pass over a pending request before it blocks the requests behind it.
+constexpr int kMaxSkips = 8;
+
 }  // namespace
 
 struct tinv_server {
@@ -106,6 +125,7 @@ struct tinv_server {
     std::vector<Wave*> inflight;
     std::vector<bool> slot_busy;
     size_t inflight_bytes = 0;
+    int sms_used = 0;  // persistent CTAs of the waves in flight
     int64_t inflight_problems = 0;
     uint64_t next_ticket = 1;
     bool stopping = false;
@@ -119,7 +139,8 @@ struct tinv_server {
     Clock::time_point t_first, t_last;
 
     void run();
-    Wave* launch(std::vector<ReqP>&& reqs, int slot);
+    Wave* launch(std::vector<ReqP>&& reqs, int slot, int ctas);
+    bool admit();
     void finish(Wave* w);
 };
 
@@ -137,11 +158,12 @@ void CUDART_CB wave_done_cb(void* arg)
 }  // namespace
 
 // Enqueue one wave on streams[slot].  Returns the wave (rc != 0 if enqueueing failed).
-Wave* tinv_server::launch(std::vector<ReqP>&& reqs, int slot)
+Wave* tinv_server::launch(std::vector<ReqP>&& reqs, int slot, int ctas)
 {
     Wave* wv = new Wave;
     wv->reqs = std::move(reqs);
     wv->slot = slot;
+    wv->ctas = ctas;
     wv->srv = this;
     cudaStream_t st = streams[slot];
     Staging& sg = staging[slot];
@@ -212,10 +234,10 @@ Wave* tinv_server::launch(std::vector<ReqP>&& reqs, int slot)
         o.device_ptrs = 1;
         o.stream = st;
         o.max_team = cfg.max_team;
-        // each wave's persistent kernel holds one CTA on each of its SMs for its whole run
-        // (a CTA fills an SM's registers), so concurrent waves split the SMs between them
-        o.grid_ctas = cfg.wave_ctas > 0 ? std::min(cfg.wave_ctas, sms)
-                                        : std::max(1, sms / (int)streams.size());
+        // each wave's persistent kernel holds one CTA on each of its SMs (a CTA fills an SM's
+        // registers), and the worker keeps the grids of the waves in flight within the SM count,
+        // so every wave's CTAs are co-resident
+        o.grid_ctas = wv->ctas;
         rc = batch_enqueue_device(np, ns.data(), off_de.data(), off_z.data(), seeds.data(), dev,
                                   dev + M, dev + 2 * M, dz, dtab + 2 * np, o);
     }
@@ -251,12 +273,15 @@ void tinv_server::finish(Wave* wv)
         Req& r = *wv->reqs[q];
         if (!rc) {
             r.info = sg.tab[2 * np + q];
-            bool drop;
+            bool deliver;
             {
+                // decided under the lock: from here on tinv_cancel reports the request as
+                // completed, so a caller never sees a successful cancel while Z is written
                 std::lock_guard<std::mutex> lk(mu);
-                drop = r.cancel;
+                deliver = !r.cancel && r.info >= 0;
+                r.delivering = deliver;
             }
-            if (!drop && r.info >= 0) memcpy(r.Z, sg.z + zoff, (size_t)(r.n * r.n) * sizeof(double));
+            if (deliver) memcpy(r.Z, sg.z + zoff, (size_t)(r.n * r.n) * sizeof(double));
         }
         zoff += r.n * r.n;
     }
@@ -282,8 +307,86 @@ void tinv_server::finish(Wave* wv)
     }
     inflight_bytes -= wv->bytes;
     inflight_problems -= np;
+    sms_used -= wv->ctas;
     slot_busy[wv->slot] = false;
     cv_done.notify_all();
+}
+
+// Form and enqueue one wave if a stream and enough SMs are free and some pending request fits.
+// Called by the worker with `mu` held; releases it while the wave is enqueued.  Returns true when
+// a wave was launched.
+bool tinv_server::admit()
+{
+    if (pending.empty()) return false;
+    int slot = -1, free_streams = 0;
+    for (int s = 0; s < (int)streams.size(); ++s)
+        if (!slot_busy[s]) {
+            if (slot < 0) slot = s;
+            ++free_streams;
+        }
+    if (slot < 0) return false;
+    const int share = cfg.wave_ctas > 0 ? std::min(cfg.wave_ctas, sms)
+                                        : std::max(1, sms / (int)streams.size());
+    const int free_sms = sms - sms_used;
+    if (free_sms < share && !inflight.empty()) return false;
+    // memory budget now: hbm_fraction of the free device memory plus what the waves hold
+    size_t budget_now = budget;
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+            budget_now = (size_t)(cfg.hbm_fraction * (double)(free_b + inflight_bytes));
+    }
+    double pend_work = 0.0;
+    for (const ReqP& r : pending) pend_work += request_work(r->n);
+    // this wave's share of the pending work: the free streams divide it
+    const double target = pend_work / (double)free_streams;
+    std::vector<ReqP> take, passed;
+    size_t bytes = 0;
+    double work = 0.0;
+    for (auto it = pending.begin(); it != pending.end() && work < target;) {
+        ReqP r = *it;
+        const bool first = take.empty() && inflight.empty();
+        bool fits = first;
+        if (!first)
+            fits = inflight_problems + (int64_t)take.size() + 1 <= cfg.max_slots &&
+                   inflight_bytes + bytes + r->bytes <= budget_now;
+        if (!fits) {
+            // a request passed over by kMaxSkips waves stops the ones behind it from passing it
+            if (r->skipped >= kMaxSkips) break;
+            passed.push_back(r);
+            ++it;
+            continue;
+        }
+        it = pending.erase(it);
+        r->state = TINV_REQ_RUNNING;
+        bytes += r->bytes;
+        work += request_work(r->n);
+        take.push_back(r);
+    }
+    if (take.empty()) return false;
+    for (ReqP& r : passed) ++r->skipped;
+    // SMs: the wave's share of the free SMs by work; one stream's share stays free for later
+    // arrivals while other streams are free and requests remain, unless this is the last one
+    const double rest = pend_work - work;
+    int ctas = free_sms;
+    if (free_streams > 1 && pend_work > 0.0)
+        ctas = (int)llround((double)free_sms * work / pend_work);
+    if (free_streams > 1 && rest <= 0.0) ctas = free_sms - share;
+    ctas = std::max(std::min(share, free_sms), std::min(ctas, free_sms));
+    ctas = std::max(1, ctas);
+    slot_busy[slot] = true;
+    inflight_bytes += bytes;
+    inflight_problems += (int64_t)take.size();
+    sms_used += ctas;
+    ++waves;
+    wave_problems += take.size();
+    cv_done.notify_all();  // states changed to running
+    mu.unlock();
+    Wave* w = launch(std::move(take), slot, ctas);
+    mu.lock();
+    inflight.push_back(w);
+    max_inflight_seen = std::max<uint64_t>(max_inflight_seen, inflight.size());
+    return true;
 }
 
 void tinv_server::run()
@@ -310,43 +413,8 @@ void tinv_server::run()
             lk.lock();
             continue;
         }
-        // admission: one wave per free stream, requests in arrival order
-        int slot = -1;
-        for (int s = 0; s < (int)streams.size(); ++s)
-            if (!slot_busy[s]) {
-                slot = s;
-                break;
-            }
-        if (slot >= 0 && !pending.empty()) {
-            std::vector<ReqP> take;
-            size_t bytes = 0;
-            while (!pending.empty()) {
-                ReqP r = pending.front();
-                const bool first = take.empty() && inflight.empty();
-                if (!first) {
-                    if (inflight_problems + (int64_t)take.size() + 1 > cfg.max_slots) break;
-                    if (inflight_bytes + bytes + r->bytes > budget) break;
-                }
-                pending.pop_front();
-                r->state = TINV_REQ_RUNNING;
-                bytes += r->bytes;
-                take.push_back(r);
-            }
-            if (!take.empty()) {
-                slot_busy[slot] = true;
-                inflight_bytes += bytes;
-                inflight_problems += (int64_t)take.size();
-                ++waves;
-                wave_problems += take.size();
-                cv_done.notify_all();  // states changed to running
-                lk.unlock();
-                Wave* w = launch(std::move(take), slot);
-                lk.lock();
-                inflight.push_back(w);
-                max_inflight_seen = std::max<uint64_t>(max_inflight_seen, inflight.size());
-                continue;
-            }
-        }
+        // admission (takes and releases the lock around the wave's enqueueing)
+        if (admit()) continue;
         if (stopping && pending.empty() && inflight.empty()) break;
         // sleep until something changes (a bounded wait guards against a lost wake-up)
         cv_work.wait_for(lk, std::chrono::milliseconds(inflight.empty() ? 50 : 2));
@@ -360,7 +428,7 @@ void tinv_server_cfg_default(tinv_server_cfg* c)
     if (!c) return;
     memset(c, 0, sizeof(*c));
     c->max_slots = 4096;
-    c->max_inflight = 2;
+    c->max_inflight = 4;
     c->hbm_fraction = 0.5;
     c->method = TINV_CWY;
     c->max_pending = 65536;
@@ -511,7 +579,8 @@ int tinv_cancel(tinv_server* srv, uint64_t ticket)
         return 0;
     }
     if (r.state == TINV_REQ_RUNNING) {
-        r.cancel = true;  // the GPU work finishes; its result is not written to Z
+        if (r.delivering) return 1;  // its result is being written to Z: it completes
+        r.cancel = true;             // the GPU work finishes; its result is not written to Z
         return 0;
     }
     return r.state == TINV_REQ_CANCELLED ? TINV_ECANCELED : 1;  // 1: already finished

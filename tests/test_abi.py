@@ -242,7 +242,7 @@ def test_server_config_and_null_checks(lib):
     c = binding.ServerCfg()
     lib.tinv_server_cfg_default(ctypes.byref(c))
     assert (c.max_slots, c.max_inflight, c.hbm_fraction, c.method, c.max_pending) == \
-        (4096, 2, 0.5, binding.TINV_CWY, 65536)
+        (4096, 4, 0.5, binding.TINV_CWY, 65536)
     assert ctypes.sizeof(binding.ServerCfg) == 64 and ctypes.sizeof(binding.Stats) == 184
     t = ctypes.c_uint64()
     d = np.zeros(3)
