@@ -4,8 +4,11 @@
 // Its scratch (the LU factors of every shift, the pivot bits and a few per-call scalars) lives
 // in one file-scope __device__ array of fixed size, which every GPU that loads the library holds
 // until the process exits.  Host code cannot pass that array's name to a kernel (on the host the
-// name denotes a host-side stand-in, not device memory), so the device address is looked up once
-// per device with cudaGetSymbolAddress, with that device current, and cached.
+// name denotes a host-side stand-in, not device memory), so the device address is looked up with
+// cudaGetSymbolAddress, with the device current, and cached.  A symbol's address belongs to a
+// CUDA context (a driver context the caller made current, or a primary context re-created after
+// cudaDeviceReset, has its own), so the cache is keyed by the unique id of the current context.
+#include <cuda.h>
 #include <mutex>
 #include <string.h>
 
@@ -24,25 +27,70 @@ constexpr size_t kNoAllocBytes = 20u << 20;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {};
+// Context ids come from the driver API, reached through the runtime's entry-point lookup (the
+// library does not link the driver library itself).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
-// Device address of the scratch on the current device (looked up on the first call there).
+constexpr int kCacheSize = 64;
+struct CacheEntry {
+    unsigned long long ctx_id;
+    void* ptr;
+};
+std::mutex g_noalloc_mu;
+CacheEntry g_noalloc_cache[kCacheSize] = {};
+int g_noalloc_used = 0;
+int g_noalloc_next = 0;  // slot replaced when the cache is full
+bool g_noalloc_fn_init = false;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Unique id of the current context; false when it cannot be determined.
+bool current_context_id(unsigned long long* id)
+{
+    if (!g_noalloc_fn_init) {
+        g_noalloc_fn_init = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = (CtxGetIdFn)f;
+    }
+    if (!g_ctx_get_current || !g_ctx_get_id) return false;
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return g_ctx_get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch in the current context (looked up on the first call there).
 cudaError_t noalloc_scratch(void** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);
+    if (have_id) {
+        for (int i = 0; i < g_noalloc_used; ++i)
+            if (g_noalloc_cache[i].ctx_id == id) {
+                *out = g_noalloc_cache[i].ptr;
+                return cudaSuccess;
+            }
     }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // also makes the primary context current
+    if (e != cudaSuccess) return e;
+    if (!have_id) have_id = current_context_id(&id);
+    if (have_id) {
+        int slot = g_noalloc_used < kCacheSize ? g_noalloc_used++ : (g_noalloc_next++ % kCacheSize);
+        g_noalloc_cache[slot] = {id, p};
+    }
+    *out = p;
     return cudaSuccess;
 }
 
