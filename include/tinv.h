@@ -301,8 +301,11 @@ int tinv_plan(int64_t n, const double* d, const double* e, int64_t m, const doub
               double* wp, int32_t* head, double* scal, const tinv_opts* o);
 
 /*
- * tinv_lu -- step a3 alone: LU with scaled partial pivoting of T - s_j I (the matrix of Eq. 1)
- * for every shift s[0..m).  Outputs are m x n arrays, row j (stride n) for shift j:
+ * tinv_lu -- step a3 alone: LU with partial pivoting and implicit row scaling of T - s_j I (the
+ * matrix of Eq. 1; the role of LAPACK's DLAGTF: every row scaled by the 1-norm of its row of
+ * T - s_j I as given, rows k+1 and k interchanged when |c_k|/s_{k+1} > |a_k|/s_k for the current
+ * pivot entry a_k, ties kept) for every shift s[0..m).  Outputs are m x n arrays, row j
+ * (stride n) for shift j:
  *   l     : multipliers of the unit lower bidiagonal L;  u0 : diagonal of U;
  *   u1,u2 : first and second superdiagonals of U;  piv : 1 where rows k, k+1 were swapped.
  * Entries past the end of each factor (l, u1, u2 at k = n-1, u2 at n-2) are written as 0.
@@ -314,7 +317,9 @@ int tinv_lu(int64_t n, const double* d, const double* e, int64_t m, const double
 /*
  * tinv_solve -- step a5 alone: x_j <- (T - s_j I)^{-1} x_j for m right-hand sides X (n x m,
  * ldx), each scaled first as in DSTEIN when scale != 0 (x <- x n ||T||_1 max(eps,|u_nn|)/||x||_1).
- * Diagonal entries of U below tol = eps max|U| in magnitude are replaced by sign(u) tol.
+ * A diagonal entry u of U so small that a quotient of its row by it could overflow
+ * (|u| < DBL_MIN max(1, |u1|, |u2|), zero included) is replaced by sign(u) tol, tol = eps max|U|
+ * (DLAGTS's perturbation, made only to avoid overflow).
  */
 int tinv_solve(int64_t n, const double* d, const double* e, int64_t m, const double* s,
                double* X, int64_t ldx, int32_t scale, const tinv_opts* o);

@@ -32,8 +32,10 @@
  *   - After CWY the tested iterate is x = -c*q (q as printed, sign-flipped), which equals the
  *     MGS-orthogonalized iterate (I - Q Q^T) v; the next sweep starts from it.
  *   - Coincident shifts: if w_j - w'_{j-1} < 10*eps*|w_j| then w'_j = w'_{j-1} + 10*eps*|w_j|.
- *   - Tiny pivots in the solve: |u0_k| < tol = eps*max|U| is replaced by sign(u0_k)*tol,
- *     sign(0) = +.
+ *   - Tiny pivots in the solve (DLAGTS, job -1: U's diagonal is perturbed only to avoid
+ *     overflow, by at least tol = eps*max|U|): u0_k is replaced by sign(u0_k)*tol, sign(0) = +,
+ *     iff |u0_k| < DBL_MIN*max(1, |u1_k|, |u2_k|), i.e. iff a quotient of row k by u0_k could
+ *     overflow; the decision depends on U alone, not on the right-hand side.
  *   - Breakdown (remainder exactly zero): CWY/Householder complete the basis with the first
  *     free unit vector (u_hat := e_1); MGS restarts from a fresh random vector. Either way
  *     the sweep does not count as a success.
@@ -205,20 +207,22 @@ void orc_plan(int64_t n, const double* d, const double* e, int64_t m, const doub
 /* Factor T - lambda*I = P L U.  U has diagonal u0[0..n), first superdiagonal u1[0..n-1),
  * second superdiagonal u2[0..n-1) (nonzero only where rows were interchanged).  L is unit
  * lower bidiagonal with multipliers l[0..n-1).  piv[k] = 1 iff rows k and k+1 were
- * interchanged at step k.  Row k+1 becomes the pivot row when its scaled subdiagonal entry
- * |c_k| / (|c_k| + |a_{k+1}| + |b_{k+1}|) exceeds the scaled pivot |a_k| / (|a_k| + |b_k|)
- * of the current row (a tie keeps the current row). */
+ * interchanged at step k.  Partial pivoting with implicit row scaling (DLAGTF's role in Eq. 1):
+ * every row is scaled by the 1-norm of its row of T - lambda*I as given, s_0 = |a_0| + |b_0|
+ * and s_{k+1} = |c_k| + |a_{k+1}| + |b_{k+1}|; at step k row k+1 becomes the pivot row when
+ * |c_k| / s_{k+1} exceeds |a_k| / s_k, with a_k the current pivot entry (a tie keeps the
+ * current row; a zero numerator counts as 0). */
 void orc_lagtf(int64_t n, const double* d, const double* e, double lambda,
                double* u0, double* u1, double* u2, double* l, unsigned char* piv)
 {
     if (n <= 0) return;
     double ak = d[0] - lambda;           /* diagonal of the current pivot row      */
     double bk = (n > 1) ? e[0] : 0.0;    /* superdiagonal of the current pivot row */
+    double scale1 = fabs(ak) + fabs(bk); /* row scale of the pivot position k      */
     for (int64_t k = 0; k + 1 < n; ++k) {
         double ck = e[k];                            /* entry below the pivot        */
         double a1 = d[k + 1] - lambda;               /* diagonal of row k+1          */
         double b1 = (k + 2 < n) ? e[k + 1] : 0.0;    /* superdiagonal of row k+1     */
-        double scale1 = fabs(ak) + fabs(bk);
         double scale2 = (fabs(ck) + fabs(a1)) + fabs(b1);
         double piv1 = (ak == 0.0) ? 0.0 : fabs(ak) / scale1;
         double piv2 = (ck == 0.0) ? 0.0 : fabs(ck) / scale2;
@@ -241,13 +245,15 @@ void orc_lagtf(int64_t n, const double* d, const double* e, double lambda,
             ak = bk - lk * a1;
             bk = -(lk * b1);
         }
+        scale1 = scale2;
     }
     u0[n - 1] = ak;
 }
 
 /* Solve with the factors of orc_lagtf: first P and L, then U by back substitution.  A
- * diagonal entry of U smaller than tol = eps*max|U| in magnitude is replaced by
- * sign(u0_k)*tol (sign(0) = +).  Returns tol. */
+ * diagonal entry of U so small that a quotient of its row by it could overflow,
+ * |u0_k| < DBL_MIN*max(1, |u1_k|, |u2_k|) (zero included), is replaced by sign(u0_k)*tol with
+ * tol = eps*max|U| (sign(0) = +), the minimum perturbation of DLAGTS's job -1.  Returns tol. */
 double orc_lagts(int64_t n, const double* u0, const double* u1, const double* u2,
                  const double* l, const unsigned char* piv, double* y)
 {
@@ -274,7 +280,10 @@ double orc_lagts(int64_t n, const double* u0, const double* u1, const double* u2
         if (k + 1 < n) temp = temp - u1[k] * y[k + 1];
         if (k + 2 < n) temp = temp - u2[k] * y[k + 2];
         double ak = u0[k];
-        if (fabs(ak) < tol) ak = (ak >= 0.0) ? tol : -tol;
+        double big = 1.0;
+        if (k + 1 < n) big = dmax(big, fabs(u1[k]));
+        if (k + 1 < n) big = dmax(big, fabs(u2[k]));
+        if (fabs(ak) < DBL_MIN * big) ak = (ak >= 0.0) ? tol : -tol;
         y[k] = temp / ak;
     }
     return tol;

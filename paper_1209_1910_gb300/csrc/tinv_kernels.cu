@@ -442,12 +442,13 @@ __device__ __forceinline__ void lu_row(int64_t n, const double* __restrict__ d,
 {
     double ak = __dsub_rn(d[0], lam);
     double bk = (n > 1) ? e[0] : 0.0;
+    // implicit row scaling: each row is scaled by the 1-norm of its row of T - lam I as given
+    double scale1 = __dadd_rn(fabs(ak), fabs(bk));
     unsigned long long umax = 0;  // max |U entry| as the bit pattern of a non-negative double
     for (int64_t k = 0; k + 1 < n; ++k) {
         const double ck = e[k];
         const double a1 = __dsub_rn(d[k + 1], lam);
         const double b1 = (k + 2 < n) ? e[k + 1] : 0.0;
-        const double scale1 = __dadd_rn(fabs(ak), fabs(bk));
         const double scale2 = __dadd_rn(__dadd_rn(fabs(ck), fabs(a1)), fabs(b1));
         double lk, w0, w1, w2;
         uint8_t sw;
@@ -473,6 +474,7 @@ __device__ __forceinline__ void lu_row(int64_t n, const double* __restrict__ d,
         u1[k] = w1;
         u2[k] = w2;
         pv[k] = sw;
+        scale1 = scale2;
         umax = max(umax, max(abs_bits(w0), max(abs_bits(w1), abs_bits(w2))));
     }
     u0[n - 1] = ak;
@@ -514,14 +516,19 @@ __global__ void k_lu_seg(Problem p, Ws w)
            w.fu2 + base, w.fpiv + base, w.u0n + j, w.tolv + j);
 }
 
-// Solve-ready back-substitution factors, in place: r = 1/u0 with tiny pivots |u0| < tol
-// replaced by sign(u0) tol (sign(0) = +), a = -u1 r, b = -u2 r.
+// Solve-ready back-substitution factors, in place: r = 1/u0, a = -u1 r, b = -u2 r.  A pivot so
+// small that one of these quotients could overflow, |u0| < DBL_MIN max(1, |u1|, |u2|) (zero
+// included), is replaced by sign(u0) tol (sign(0) = +, tol = eps max|U|): the perturbation
+// DLAGTS makes only to avoid overflow, decided on U alone so that the back substitution stays a
+// fixed linear recurrence.
 __device__ __forceinline__ void recip_row(int64_t n, double* __restrict__ u0, double* __restrict__ u1,
                                           double* __restrict__ u2, double tol)
 {
+    constexpr double kDblMin = 2.2250738585072014e-308;
     for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
         double a = u0[k];
-        if (fabs(a) < tol) a = (a >= 0.0) ? tol : -tol;
+        const double big = fmax(1.0, fmax(fabs(u1[k]), fabs(u2[k])));
+        if (fabs(a) < __dmul_rn(kDblMin, big)) a = (a >= 0.0) ? tol : -tol;
         const double r = __drcp_rn(a);
         u0[k] = r;
         u1[k] = -u1[k] * r;

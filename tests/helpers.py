@@ -37,10 +37,14 @@ def orth_ratio(Z):
 
 
 def sin_angle(A, B):
-    """sin of the largest principal angle between span(A) and span(B) (orthonormal columns)."""
+    """sin of the largest principal angle between span(A) and span(B).  Both bases are
+    orthonormalized first (QR), so a basis whose columns are orthogonal only to O(eps kappa), as
+    MGS gives, is compared by the subspace it spans."""
     if A.shape[1] == 0:
         return 0.0
-    return float(np.linalg.norm(B - A @ (A.T @ B), 2))
+    Qa = np.linalg.qr(A)[0]
+    Qb = np.linalg.qr(B)[0]
+    return float(np.linalg.norm(Qb - Qa @ (Qa.T @ Qb), 2))
 
 
 def clusters_from_heads(head):

@@ -20,6 +20,20 @@ def test_pivot_choices_hand_computed_3x3(orc):
     assert piv[:2].tolist() == [0, 1]
 
 
+def test_pivot_rows_scaled_by_their_original_norms(orc):
+    # T = [[1,1,0],[1,1.5,1],[0,1,2]], lambda = 0; row scales s = 2, 3.5, 3 (1-norms of the rows
+    # of T as given).
+    # step 0: 1/2 > 1/3.5 -> keep row 0, l0 = 1, current pivot entry a1 = 1.5 - 1 = 0.5.
+    # step 1: 0.5/3.5 < 1/3 -> interchange (scaling the current row [0.5, 1] by its own norm
+    #         1.5 would give 1/3 = 1/3, a tie, and keep it), l1 = 0.5/1, u0[2] = 1 - 0.5*2 = 0.
+    u0, u1, u2, l, piv = orc.lagtf([1.0, 1.5, 2.0], [1.0, 1.0], 0.0)
+    assert piv[:2].tolist() == [0, 1]
+    assert u0.tolist() == [1.0, 1.0, 0.0]
+    assert u1[:2].tolist() == [1.0, 2.0]
+    assert u2[:2].tolist() == [0.0, 0.0]
+    assert l[:2].tolist() == [1.0, 0.5]
+
+
 def test_scaled_pivoting_differs_from_magnitude_pivoting(orc):
     # |c| = 2 > |a| = 1, but scaled: 1/3 > 2/12 -> no interchange
     u0, u1, u2, l, piv = orc.lagtf([1.0, 10.0], [2.0], 0.0)
@@ -30,13 +44,31 @@ def test_scaled_pivoting_differs_from_magnitude_pivoting(orc):
 
 
 def test_tiny_pivot_replaced_by_tolerance(orc):
-    # T = [[1,1],[1,1]] is singular: u0 = [1, 0]; tol = eps * max|U| = eps.
+    # DLAGTS, job -1: a diagonal entry of U is perturbed (by tol = eps max|U|) only where a
+    # quotient by it could overflow.  T = [[1,1],[1,1]] is singular: u0 = [1, 0].
     f = orc.lagtf([1.0, 1.0], [1.0], 0.0)
     x, tol = orc.lagts(f, [0.0, 1.0])
     assert tol == EPS
     assert x.tolist() == [-1.0 / EPS, 1.0 / EPS]
     x, _ = orc.lagts(f, [1.0, 1.0])
     assert x.tolist() == [1.0, 0.0]
+    # a subnormal pivot: its reciprocal overflows, so it is replaced by tol
+    f = orc.lagtf([1.0, 1e-310], [0.0], 0.0)
+    x, tol = orc.lagts(f, [0.0, 1.0])
+    assert tol == EPS and x.tolist() == [0.0, 1.0 / EPS]
+
+
+def test_small_normal_pivot_is_not_perturbed(orc):
+    # a pivot far below eps max|U| but in the normal range is used as it is (no overflow can
+    # occur): x_2 = 1 / 1e-20 exactly, as DLAGTS gives; the inverse iteration's amplification
+    # near an eigenvalue comes from exactly such pivots
+    f = orc.lagtf([1.0, 1e-20], [0.0], 0.0)
+    x, tol = orc.lagts(f, [0.0, 1.0])
+    assert tol == EPS and x.tolist() == [0.0, 1e20]
+    # the same at the threshold scale: a pivot just above DBL_MIN * max(1, |u1|) is kept
+    f = orc.lagtf([1.0, 1e-300], [0.0], 0.0)
+    x, _ = orc.lagts(f, [0.0, 1e-10])
+    assert x[1] == 1e-10 / 1e-300
 
 
 @pytest.mark.parametrize("seed", range(4))
