@@ -46,6 +46,7 @@ extern "C" {
 #define TINV_ENOTSUP (-106)   /* size beyond what this library supports                    */
 #define TINV_ENODEV (-107)    /* no CUDA device, or not an sm_103 device                   */
 #define TINV_EWORKSPACE (-108) /* caller-provided workspace is too small                   */
+#define TINV_EINTERNAL (-109) /* a device-side bounds check failed (TINV_DEBUG builds only)  */
 
 /* Reorthogonalization of eigenvectors inside a cluster. */
 #define TINV_CWY 0 /* compact-WY Householder orthogonalization (Sec. 3.3.2, Alg. 4)   */
@@ -78,7 +79,11 @@ typedef struct tinv_opts {
                          /*   the same n, off_de, off_z, seed and j0 wrote it); the call then   */
                          /*   makes no host-to-device copy and no allocation, so it can be      */
                          /*   captured into a CUDA graph and replayed (phase_ms must be NULL)   */
-    int32_t reserved[5];
+    int32_t spin_limit;  /* polls after which a bounded team-barrier wait of the cluster kernel  */
+                         /*   gives up (0 = the default: 4e8 polls or 20 s, whichever is first); */
+                         /*   a small value makes a launch end with TINV_ETIMEDOUT, which tests  */
+                         /*   the bounded-wait failure path without hanging the GPU              */
+    int32_t reserved[4];
 } tinv_opts;
 
 /* Fill *o with the defaults: CWY, host pointers, seed 0, j0 0, automatic scheduling. */
@@ -301,11 +306,10 @@ int tinv_plan(int64_t n, const double* d, const double* e, int64_t m, const doub
               double* wp, int32_t* head, double* scal, const tinv_opts* o);
 
 /*
- * tinv_lu -- step a3 alone: LU with partial pivoting and implicit row scaling of T - s_j I (the
- * matrix of Eq. 1; the role of LAPACK's DLAGTF: every row scaled by the 1-norm of its row of
- * T - s_j I as given, rows k+1 and k interchanged when |c_k|/s_{k+1} > |a_k|/s_k for the current
- * pivot entry a_k, ties kept) for every shift s[0..m).  Outputs are m x n arrays, row j
- * (stride n) for shift j:
+ * tinv_lu -- step a3 alone: LU with scaled partial pivoting of T - s_j I (the matrix of Eq. 1;
+ * rows k+1 and k are interchanged when |c_k|/(|c_k|+|a_{k+1}|+|b_{k+1}|) > |a_k|/(|a_k|+|b_k|)
+ * with the current pivot row's entries a_k, b_k; ties keep the row) for every shift s[0..m).
+ * Outputs are m x n arrays, row j (stride n) for shift j:
  *   l     : multipliers of the unit lower bidiagonal L;  u0 : diagonal of U;
  *   u1,u2 : first and second superdiagonals of U;  piv : 1 where rows k, k+1 were swapped.
  * Entries past the end of each factor (l, u1, u2 at k = n-1, u2 at n-2) are written as 0.

@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
                 ("iters", ctypes.c_void_p), ("info", ctypes.c_void_p),
                 ("max_team", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
                 ("phase_ms", ctypes.c_void_p), ("counters", ctypes.c_void_p),
-                ("table_ready", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("table_ready", ctypes.c_int32), ("spin_limit", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 def load(path: str | None = None) -> ctypes.CDLL:

@@ -10,6 +10,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -124,6 +125,19 @@ Ws bind_layout(void* base, const Layout& L, const Dims& D)
     }
     w.P = D.P;
     w.use_smem = chain_use_smem(D.nmax) ? 1 : 0;
+    w.nF = D.F;
+    w.nTT = D.TT;
+    w.nM = D.M;
+    w.nPN = (int64_t)D.P * D.nmax;
+#ifdef TINV_DEBUG
+    // test hook of the debug build: declare Y shorter than it is (by this many elements), so
+    // the bounds checks of the cluster kernel must fire on accesses that are still inside the
+    // real allocation (the check skips them)
+    if (const char* sh = getenv("TINV_DEBUG_SHRINK_F")) {
+        const long long k = atoll(sh);
+        if (k > 0) w.nF = w.nF > k ? w.nF - k : 0;
+    }
+#endif
     return w;
 }
 
@@ -133,10 +147,16 @@ using namespace tinvx;
 
 namespace {
 
+__device__ __forceinline__ int64_t dev_err_code(int64_t err)
+{
+    if (err & kErrBounds) return TINV_EINTERNAL;
+    return err ? (int64_t)TINV_ETIMEDOUT : 0;
+}
+
 __global__ void k_finish(const int64_t* ctr, int64_t* info)
 {
     const int64_t err = ctr[kCtrErr];
-    *info = err ? (int64_t)TINV_ETIMEDOUT : ctr[kCtrInfo];
+    *info = err ? dev_err_code(err) : ctr[kCtrInfo];
 }
 
 // tinv_opts.counters from the counter block.
@@ -162,7 +182,7 @@ __global__ void k_finish_batch(const int64_t* ctr, const int64_t* sinfo, int64_t
     const int64_t err = ctr[kCtrErr];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nprob;
          q += (int64_t)gridDim.x * blockDim.x)
-        info[q] = err ? (int64_t)TINV_ETIMEDOUT : sinfo[q];
+        info[q] = err ? dev_err_code(err) : sinfo[q];
 }
 
 struct Opts {
@@ -181,11 +201,13 @@ struct Opts {
 // must already be in the workspace (copied on `st`).
 // When phase_ms is given, CUDA events bracket each launch and the elapsed device times are
 // stored after synchronizing on the last event.
-int enqueue_tinv(const Problem& p, void* ws, const Dims& D, int32_t max_team, cudaStream_t st,
+int enqueue_tinv(const Problem& p0, void* ws, const Dims& D, int32_t max_team, cudaStream_t st,
                  float* phase_ms)
 {
     const Layout L = make_layout(D, true);
     const Ws w = bind_layout(ws, L, D);
+    Problem p = p0;
+    if (!p.seg_preset && p.zlen == 0 && p.m > 0) p.zlen = (p.m - 1) * p.ldz + p.n;
     cudaEvent_t ev[5] = {};
     cudaError_t e = cudaSuccess;
     if (phase_ms) {
@@ -269,9 +291,11 @@ int batch_enqueue_device(int64_t nprob, const int64_t* n, const int64_t* off_de,
     memset(&p, 0, sizeof(p));
     p.n = D.nmax;
     p.method = o.method;
+    p.spin_limit = (uint32_t)o.spin_limit;
     p.seg_preset = 1;
     p.nseg = nprob;
     p.M = D.M;
+    for (int64_t q = 0; q < nprob; ++q) p.zlen = std::max(p.zlen, off_z[q] + n[q] * n[q]);
     p.d = d;
     p.e = e;
     p.w = w;
@@ -342,6 +366,7 @@ const char* tinv_strerror(int code)
     case TINV_ENOMEM: return "device memory allocation failed";
     case TINV_ECUDA: return "CUDA runtime error";
     case TINV_ETIMEDOUT: return "a bounded device-side wait expired";
+    case TINV_EINTERNAL: return "a device-side bounds check failed (debug build)";
     case TINV_EAGAIN: return "no capacity right now; retry";
     case TINV_ECANCELED: return "request cancelled";
     case TINV_ENOTSUP: return "size not supported by this library";
@@ -384,6 +409,7 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
     p.m = m;
     p.ldz = ldz;
     p.method = op.o.method;
+    p.spin_limit = (uint32_t)op.o.spin_limit;
     p.seed = op.o.seed;
     p.j0 = op.o.j0;
     p.nseg = 1;
@@ -487,7 +513,7 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
         if (!rc) {
             if (op.o.counters) host_counters(ctr, op.o.counters);
             if (ctr[kCtrErr]) {
-                rc = TINV_ETIMEDOUT;
+                rc = (int)err_code(ctr[kCtrErr]);
             } else {
                 int64_t cnt = 0;
                 for (int64_t j = 0; j < m; ++j) {
@@ -564,9 +590,11 @@ int tinv_batch(int64_t nprob, const int64_t* n, const int64_t* off_de, const int
     memset(&p, 0, sizeof(p));
     p.n = D.nmax;
     p.method = op.o.method;
+    p.spin_limit = (uint32_t)op.o.spin_limit;
     p.seg_preset = 1;
     p.nseg = nprob;
     p.M = D.M;
+    for (int64_t q = 0; q < nprob; ++q) p.zlen = std::max(p.zlen, off_z[q] + n[q] * n[q]);
     const Layout L = make_layout(D, true);
 
     // ---- host pointers: validate values, copy in, run, copy out ----
@@ -631,9 +659,9 @@ int tinv_batch(int64_t nprob, const int64_t* n, const int64_t* off_de, const int
         if (!rc) {
             if (op.o.counters) host_counters(ctr, op.o.counters);
             if (ctr[kCtrErr]) {
-                rc = TINV_ETIMEDOUT;
+                rc = (int)err_code(ctr[kCtrErr]);
                 if (info)
-                    for (int64_t q = 0; q < nprob; ++q) info[q] = TINV_ETIMEDOUT;
+                    for (int64_t q = 0; q < nprob; ++q) info[q] = rc;
             } else {
                 int64_t cnt = 0;
                 for (int64_t q = 0; q < nprob; ++q) {
@@ -874,6 +902,7 @@ int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int
     p.n = n;
     p.m = m;
     p.method = op.o.method;
+    p.spin_limit = (uint32_t)op.o.spin_limit;
     p.nseg = 1;
     p.M = m;
     cudaStream_t st = op.o.device_ptrs ? (cudaStream_t)op.o.stream : nullptr;
@@ -902,6 +931,7 @@ int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int
             p.Z = Q;
             p.ldz = ldq;
         }
+        p.zlen = (m - 1) * p.ldz + n;
         rc = cuda_code(ce);
         Ws wsb = bind_layout(ws.p, L, D);
         // team size for one cluster of m columns: at most n/16 CTAs and kTeamMax
@@ -931,7 +961,7 @@ int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int
             ce = cudaMemcpyAsync(ctr, wsb.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, st);
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
             rc = cuda_code(ce);
-            if (!rc && ctr[kCtrErr]) rc = TINV_ETIMEDOUT;
+            if (!rc && ctr[kCtrErr]) rc = (int)err_code(ctr[kCtrErr]);
         }
     }
     if (own_stream) {

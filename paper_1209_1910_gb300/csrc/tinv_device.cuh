@@ -43,6 +43,17 @@ __device__ __forceinline__ double start_value(uint64_t key, int64_t i)
 
 __device__ __forceinline__ double sgn(double a) { return a < 0.0 ? -1.0 : 1.0; }
 
+// Bounds check of TINV_DEBUG builds (see TINV_IN): false, with kErrBounds set, on failure.
+__device__ __forceinline__ bool dbg_ok(bool cond, int* err)
+{
+    if (!cond) atomicOr(err, kErrBounds);
+    return cond;
+}
+__device__ __forceinline__ bool dbg_range(int64_t lo, int64_t hi, int64_t cap)
+{
+    return 0 <= lo && lo <= hi && hi <= cap;
+}
+
 // ------------------------------------------------------------------------------------------
 // Reductions (fixed shapes, so results do not depend on scheduling)
 // ------------------------------------------------------------------------------------------
@@ -110,8 +121,8 @@ __device__ __forceinline__ double block_max(double v, double* sred)
 // ------------------------------------------------------------------------------------------
 // Bounded team barrier among G co-resident CTAs (a cooperative launch guarantees residency).
 // `ctr` counts arrivals monotonically; the caller's `target` advances by G per barrier.  A
-// wait gives up after kSpinTimeoutNs or kSpinLimit polls, sets the error word and returns
-// false; callers unwind on false.  G == 1 is a plain CTA barrier.
+// wait gives up after kSpinTimeoutNs or `limit` polls (0 = kSpinLimit), sets the error word and
+// returns false; callers unwind on false.  G == 1 is a plain CTA barrier.
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t globaltimer_ns()
 {
@@ -142,7 +153,8 @@ __device__ __forceinline__ void red_release_add_u32(uint32_t* p, uint32_t v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __noinline__ bool team_sync(uint32_t* ctr, uint32_t& target, int G, int* err)
+__device__ __noinline__ bool team_sync(uint32_t* ctr, uint32_t& target, int G, int* err,
+                                       uint32_t limit = 0)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -153,15 +165,17 @@ __device__ __noinline__ bool team_sync(uint32_t* ctr, uint32_t& target, int G, i
         int ok = 1;
         uint64_t t0 = 0;
         uint32_t spins = 0;
+        const uint32_t lim = limit ? limit : kSpinLimit;
         while ((int32_t)(ld_acquire_u32(ctr) - target) < 0) {
-            if ((++spins & 63u) == 0) {
+            ++spins;
+            if ((spins & 63u) == 0 || spins >= lim) {
                 if (ld_volatile_i32(err) != 0) {
                     ok = 0;
                     break;
                 }
                 const uint64_t now = globaltimer_ns();
                 if (t0 == 0) t0 = now;
-                if (spins > kSpinLimit || now - t0 > kSpinTimeoutNs) {
+                if (spins >= lim || now - t0 > kSpinTimeoutNs) {
                     atomicOr(err, kErrTimeout);
                     ok = 0;
                     break;
@@ -181,7 +195,9 @@ __device__ __noinline__ bool team_sync(uint32_t* ctr, uint32_t& target, int G, i
 // substitutions are linear recurrences with fixed coefficients, so each chunk first computes
 // its affine map (carry in -> carry out) in parallel, then one thread propagates the boundary
 // values across the P chunks in order, then every chunk re-runs its rows from its boundary
-// value.  The forward maps have multipliers |l| <= 1.  The back-substitution maps grow by
+// value.  The forward maps compose the multipliers l (scaled pivoting lets |l| exceed 1; on the
+// workloads measured their folds stay accurate, and they are not checked).  The
+// back-substitution maps grow by
 // 1/|u0| at every small pivot, and near-singular shifts of clustered spectra can put several
 // small pivots into one chunk; the boundary value folded from such a map then carries an error
 // far above the rounding of the true solution.  Every chunk therefore re-checks the rows next to
@@ -220,7 +236,6 @@ struct CtaSync {
 
 // Sequential back substitution by the calling thread alone of rows [0, top), from the forward
 // results y and the already final x[top], x[top + 1] (rows at or past n count as 0).  The
-// forward elimination is stable in parallel (its multipliers are at most 1 in magnitude).  The
 // parallel solves fall back to it when their consistency check fails, from the lowest failing
 // chunk boundary: the rows below it passed every check, so they are already backward stable.
 __device__ __noinline__ void seq_back(int64_t n, const Fac& f, const double* y, double* x, int64_t top)
@@ -513,6 +528,7 @@ struct TeamRef {
     unsigned long long stamp;  // increasing per solve of the team
     unsigned long long* nfall; // counter of sequential fallbacks (may be null)
     double tol;                // accepted backward error of a row, in eps
+    uint32_t limit;            // polls of a barrier wait (0 = default)
 };
 
 __device__ __forceinline__ void compose2(double& m00, double& m01, double& m10, double& m11,
@@ -538,6 +554,8 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
 {
     constexpr int NW = 4, PT = 32 * NW;
     const int t = threadIdx.x, B = blockDim.x, lane = t & 31, wid = t >> 5;
+    if (!TINV_IN(dbg_range(r0, r1, n) && r1 > r0 && tr.rank < tr.G && tr.G <= kTeamMax, tr.err))
+        return false;
     const int64_t R = r1 - r0;
     const int Pn = (int)min((int64_t)PT, max((int64_t)1, R / 2));
     const int64_t L = (R + Pn - 1) / Pn;
@@ -600,7 +618,7 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
         pubf[2 * tr.rank] = CA;
         pubf[2 * tr.rank + 1] = CB;
     }
-    if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+    if (!team_sync(tr.bar, *tr.target, tr.G, tr.err, tr.limit)) return false;
     double* pf = sh + 128;  // the published forward maps of the CTAs before this one
     for (int q = t; q < tr.rank; q += B) {
         pf[2 * q] = __ldcg(&pubf[2 * q]);
@@ -722,7 +740,7 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
         o[4] = c0;
         o[5] = c1;
     }
-    if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+    if (!team_sync(tr.bar, *tr.target, tr.G, tr.err, tr.limit)) return false;
     double* pb = sh + 128;  // the published back maps of the CTAs after this one
     for (int q = tr.rank + 1 + t; q < tr.G; q += B)
         for (int u = 0; u < 6; ++u) pb[6 * q + u] = __ldcg(&pubb[6 * q + u]);
@@ -782,7 +800,7 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
 
     // ---------------- consistency at the chunk boundaries ----------------
     // The rows below a CTA's last chunk belong to the next CTA: read them once all are written.
-    if (tr.G > 1 && !team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+    if (tr.G > 1 && !team_sync(tr.bar, *tr.target, tr.G, tr.err, tr.limit)) return false;
     bool bad = false;
     if (act && hi < n) {
         const double x1 = (hi < r1) ? vsm[hi] : __ldcg(&vout[hi]);
@@ -809,7 +827,7 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
 #endif
     if (tr.G > 1) {
         if (fallback && t == 0) atomicMax(tr.flag, (tr.stamp << 32) | s_top);
-        if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+        if (!team_sync(tr.bar, *tr.target, tr.G, tr.err, tr.limit)) return false;
         const unsigned long long v = ld_volatile_u64(tr.flag);
         fallback = (v >> 32) == tr.stamp;
         top = (int64_t)(v & 0xffffffffull);
@@ -825,7 +843,7 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
 #endif
         }
         if (tr.G > 1) {
-            if (!team_sync(tr.bar, *tr.target, tr.G, tr.err)) return false;
+            if (!team_sync(tr.bar, *tr.target, tr.G, tr.err, tr.limit)) return false;
             for (int64_t k = r0 + t; k < r1; k += B) vsm[k] = __ldcg(&vout[k]);
         } else {
             __syncthreads();

@@ -92,6 +92,11 @@ struct Problem {
     uint64_t seed;
     int64_t j0;
     int64_t nseg, M;
+    int64_t zlen;         // elements of the packed Z array the launch may touch (0 = unknown;
+                          // used by the device bounds checks of TINV_DEBUG builds)
+    uint32_t spin_limit;  // polls of a bounded team-barrier wait before it gives up (0 = the
+                          // default kSpinLimit; tinv_opts.spin_limit, for testing the timeout path)
+    uint32_t pad32;
 };
 
 // All device pointers derived from one workspace (see Layout).
@@ -125,7 +130,21 @@ struct Ws {
     double* gvec;     // [P*2*nmax] global fallback for the per-CTA vectors (large n)
     int32_t P;        // persistent grid size the schedule was made for
     int32_t use_smem; // per-CTA vectors live in shared memory
+    // extents in elements, for the device bounds checks of TINV_DEBUG builds
+    int64_t nF;       // factor rows / Y columns (fl, fu1, fu2, fr, fpiv, Y, rhs)
+    int64_t nTT;      // T
+    int64_t nM;       // per-eigenvalue arrays
+    int64_t nPN;      // per-CTA vectors and partials: P x nmax
 };
+
+// Device bounds checks (TINV_DEBUG builds): a failed check sets kErrBounds in the error word
+// and the caller skips the access and unwinds (no trap, no assert); team barriers see the error
+// word and give up, so a whole launch ends and the host reports TINV_EINTERNAL.
+#ifdef TINV_DEBUG
+#define TINV_IN(cond, err) ::tinvx::dbg_ok((cond), (err))
+#else
+#define TINV_IN(cond, err) true
+#endif
 
 // need_chain: the cluster kernel's arrays; need_rhs: a copy of the right-hand sides (tinv_solve).
 Layout make_layout(const Dims& D, bool need_chain, bool need_rhs = false);
@@ -168,6 +187,13 @@ int batch_enqueue_device(int64_t nprob, const int64_t* n, const int64_t* off_de,
                          const double* e, const double* w, double* Z, int64_t* info,
                          const tinv_opts& o);
 size_t batch_workspace_bytes(int64_t nprob, const int64_t* n, const tinv_opts& o);
+
+// Library status code of a device error word (kErrBounds before kErrTimeout).
+inline int64_t err_code(int64_t err)
+{
+    if (err & kErrBounds) return TINV_EINTERNAL;
+    return err ? (int64_t)TINV_ETIMEDOUT : 0;
+}
 
 // Library status code (include/tinv.h) of a CUDA runtime error.
 inline int cuda_code(cudaError_t e)

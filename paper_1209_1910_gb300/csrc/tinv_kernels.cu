@@ -442,13 +442,12 @@ __device__ __forceinline__ void lu_row(int64_t n, const double* __restrict__ d,
 {
     double ak = __dsub_rn(d[0], lam);
     double bk = (n > 1) ? e[0] : 0.0;
-    // implicit row scaling: each row is scaled by the 1-norm of its row of T - lam I as given
-    double scale1 = __dadd_rn(fabs(ak), fabs(bk));
     unsigned long long umax = 0;  // max |U entry| as the bit pattern of a non-negative double
     for (int64_t k = 0; k + 1 < n; ++k) {
         const double ck = e[k];
         const double a1 = __dsub_rn(d[k + 1], lam);
         const double b1 = (k + 2 < n) ? e[k + 1] : 0.0;
+        const double scale1 = __dadd_rn(fabs(ak), fabs(bk));
         const double scale2 = __dadd_rn(__dadd_rn(fabs(ck), fabs(a1)), fabs(b1));
         double lk, w0, w1, w2;
         uint8_t sw;
@@ -474,7 +473,6 @@ __device__ __forceinline__ void lu_row(int64_t n, const double* __restrict__ d,
         u1[k] = w1;
         u2[k] = w2;
         pv[k] = sw;
-        scale1 = scale2;
         umax = max(umax, max(abs_bits(w0), max(abs_bits(w1), abs_bits(w2))));
     }
     u0[n - 1] = ak;
@@ -512,6 +510,8 @@ __global__ void k_lu_seg(Problem p, Ws w)
     const Seg* g = w.segs + w.segj[j];
     const int64_t n = g->n;
     const size_t base = (size_t)(g->foff + (j - g->j0) * n);
+    if (!TINV_IN(j < w.nM && dbg_range((int64_t)base, (int64_t)base + n, w.nF), (int*)&w.ctr[kCtrErr]))
+        return;
     lu_row(n, p.d + g->de, p.e + g->de, w.wp[j], w.fl + base, w.fr + base, w.fu1 + base,
            w.fu2 + base, w.fpiv + base, w.u0n + j, w.tolv + j);
 }
@@ -550,6 +550,7 @@ __global__ void k_recip_seg(Problem p, Ws w)
     for (int64_t j = blockIdx.x; j < p.M; j += gridDim.x) {
         const Seg* g = w.segs + w.segj[j];
         const size_t o = (size_t)(g->foff + (j - g->j0) * g->n);
+        if (!TINV_IN(dbg_range((int64_t)o, (int64_t)o + g->n, w.nF), (int*)&w.ctr[kCtrErr])) return;
         recip_row(g->n, w.fr + o, w.fu1 + o, w.fu2 + o, w.tolv[j]);
     }
 }
@@ -619,6 +620,10 @@ __global__ void __launch_bounds__(kFirstWarps * 32) k_first(Problem p, Ws w)
     const Seg& g = *jr.g;
     const int64_t n = g.n;
     double* x = p.Z + g.z + jr.jl * g.ldz;
+    if (!TINV_IN(dbg_range((int64_t)jr.off, (int64_t)jr.off + n, w.nF) &&
+                     (p.zlen == 0 || dbg_range(g.z + jr.jl * g.ldz, g.z + jr.jl * g.ldz + n, p.zlen)),
+                 (int*)&w.ctr[kCtrErr]))
+        return;
     const Fac f = fac_at(w, jr.off);
     const double onenrm = g.onenrm, dtpcrt = g.dtpcrt, u0n = w.u0n[j];
     const bool is_head = (w.head[j] == (int32_t)j);
@@ -688,6 +693,10 @@ __global__ void __launch_bounds__(kFirstWarps * 32) k_finalize(Problem p, Ws w)
     const JRef jr = jref(w, j);
     double* x = p.Z + jr.g->z + jr.jl * jr.g->ldz;
     const int64_t n = jr.g->n;
+    if (!TINV_IN(p.zlen == 0 || dbg_range(jr.g->z + jr.jl * jr.g->ldz, jr.g->z + jr.jl * jr.g->ldz + n,
+                                          p.zlen),
+                 (int*)&w.ctr[kCtrErr]))
+        return;
     double ss = 0.0, am = -1.0;
     int64_t ai = 0;
     for (int64_t i = lane; i < n; i += 32) {
@@ -914,6 +923,14 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
     const double onenrm = sg.onenrm, dtpcrt = sg.dtpcrt;
     const bool orth = (cx.mode == kModeOrth);
     __shared__ double s_b[8];
+    // the cluster's ranges of Y, T, Z and of the team's buffers (TINV_DEBUG builds)
+    if (!TINV_IN(s0 >= 0 && mc >= 1 && s0 + mc <= w.nM && n <= p.n && rank < G && leader + G <= w.P &&
+                     dbg_range((int64_t)jr.off, (int64_t)jr.off + mc * n, w.nF) &&
+                     dbg_range(w.cltoff[c], w.cltoff[c] + mc * mc, w.nTT) &&
+                     dbg_range((int64_t)leader * p.n, (int64_t)(leader + G) * p.n, w.nPN) &&
+                     (p.zlen == 0 || dbg_range(sg.z + jr.jl * ldz, sg.z + (jr.jl + mc - 1) * ldz + n, p.zlen)),
+                 cx.err))
+        return false;
 
     // rows of passes A and C and of the head step
     const int64_t ra0 = part_lo(0, n, rank, G), ra1 = part_lo(0, n, rank + 1, G);
@@ -930,7 +947,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
         for (int64_t r = ra0 + t; r < ra1; r += B) ss = fma(z[r], z[r], ss);
         ss = block_sum(ss, red);
         if (t == 0) scal_t[rank * kScalTeam + 6] = ss;
-        if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+        if (!team_sync(tm.bar, tm.target, G, cx.err, cx.p.spin_limit)) return false;
         if (t < 32) {
             const double tot = team_sum_slot(scal_t, G, 6);
             const double nrm = sqrt(tot);
@@ -955,7 +972,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
         if (rank == 0 && t == 0) Tc[0] = s_b[1];
         kstart = 1;
         // Y[:,0] and T[0,0] must be complete before members stage rows of Y
-        if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+        if (!team_sync(tm.bar, tm.target, G, cx.err, cx.p.spin_limit)) return false;
     }
 
     for (int64_t kk = kstart; kk < mc; ++kk) {
@@ -980,6 +997,11 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
         __syncthreads();
         const int64_t c0 = s_tb[0], c1 = s_tb[1], i0 = s_tb[2], i1 = s_tb[3];
         const int64_t rc0 = s_tb[4], rc1 = s_tb[5];
+        // slices of the passes and T products: columns of Y_k / T_k and rows of Y
+        if (!TINV_IN(dbg_range(c0, c1, k) && dbg_range(i0, i1, k) && dbg_range(rc0, rc1, n) &&
+                         dbg_range(part_lo(k, n, rank, G), part_lo(k, n, rank + 1, G), n) && k < mc,
+                     cx.err))
+            return false;
         int nrmchk = 0, its = 0;
         bool conv = false;
         double fac_next = 0.0;
@@ -997,7 +1019,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 TeamRef tr{tm.bar, &tm.target, G, rank, cx.err,
                            (unsigned long long*)(scal_t + 15), ++cx.nsolve,
                            (unsigned long long*)&w.ctr[kCtrFallback],
-                           may_end ? kSolveTol : kSolveTolLoose};
+                           may_end ? kSolveTol : kSolveTolLoose, cx.p.spin_limit};
                 if (!team_solve(n, f, qbuf, fac_next, vsm, vbuf, vecS, ra0, ra1, pubf, pubb, tr, red))
                     return false;
                 PROF_MARK(cx.prof, kPhSolve);
@@ -1014,7 +1036,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 cta_coldots<kLower>(Yc, n, 0, k, rc0, rc1, vsm, red,
                                     [&](int64_t i, double s) { myS[i] = s; });
                 PROF_MARK(cx.prof, kPhA);
-                if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+                if (!team_sync(tm.bar, tm.target, G, cx.err, cx.p.spin_limit)) return false;
                 PROF_MARK(cx.prof, kPhB1);
                 // ---- s' = T_k^T s, columns [c0, c1) of this CTA ----
                 PROF_MARK(cx.prof, kPhB1);
@@ -1024,7 +1046,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                     const int64_t l0 = part_lo(0, k, rank, G), l1 = part_lo(0, k, rank + 1, G);
                     for (int64_t l = l0 + t; l < l1; l += B)
                         vecX[l] = sum_partials(w.partS + (size_t)leader * ns + l, ns, G);
-                    if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+                    if (!team_sync(tm.bar, tm.target, G, cx.err, cx.p.spin_limit)) return false;
                     for (int64_t l = t; l < c1; l += B) s1[l] = __ldcg(&vecX[l]);
                 } else {
                     for (int64_t l = t; l < c1; l += B)
@@ -1035,7 +1057,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 cta_coldots<kUpper>(Tc, ldt, c0, c1, 0, k, s1, red,
                                     [&](int64_t i, double s) { vecS[i] = s; });
                 PROF_MARK(cx.prof, kPhT1);
-                if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+                if (!team_sync(tm.bar, tm.target, G, cx.err, cx.p.spin_limit)) return false;
                 PROF_MARK(cx.prof, kPhB2);
                 for (int64_t l = t; l < k; l += B) s1[l] = __ldcg(&vecS[l]);
                 __syncthreads();
@@ -1063,7 +1085,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 scal_t[rank * kScalTeam + 1] = (rb0 <= k && k < rb1) ? vsm[k] : 0.0;
             }
             PROF_MARK(cx.prof, kPhB);
-            if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+            if (!team_sync(tm.bar, tm.target, G, cx.err, cx.p.spin_limit)) return false;
             PROF_MARK(cx.prof, kPhB3);
             // ---- g = Yhat_k^T u_hat from the team partials (all warps but the first), while
             //      warp 0 forms the reflector (Eq. yt with t = 1/(c^2 - u_kk c), Sec. 3.3.2) ----
@@ -1095,7 +1117,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                     s1[l] = sum_partials(w.partG + (size_t)leader * ns + l, ns, G);
             }
             if (sliced) {
-                if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+                if (!team_sync(tm.bar, tm.target, G, cx.err, cx.p.spin_limit)) return false;
                 for (int64_t l = i0 + t; l < k; l += B) s1[l] = __ldcg(&vecS[l]);
             }
             __syncthreads();
@@ -1128,7 +1150,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 Yc[r + kk * n] = y;
             }
             PROF_MARK(cx.prof, kPhT2);
-            if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+            if (!team_sync(tm.bar, tm.target, G, cx.err, cx.p.spin_limit)) return false;
             PROF_MARK(cx.prof, kPhB4);
             // ---- pass C: q = (Y_{k+1} T_{k+1} Y_{k+1}^T - I) e_k = Y_{k+1} x_T - e_k ----
             for (int64_t l = t; l <= k; l += B) s1[l] = __ldcg(&vecX[l]);
@@ -1150,7 +1172,7 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
                 scal_t[rank * kScalTeam + 3] = am;
             }
             PROF_MARK(cx.prof, kPhC);
-            if (!team_sync(tm.bar, tm.target, G, cx.err)) return false;
+            if (!team_sync(tm.bar, tm.target, G, cx.err, cx.p.spin_limit)) return false;
             PROF_MARK(cx.prof, kPhB5);
             if (orth) {
                 for (int64_t r = ra0 + t; r < ra1; r += B)
@@ -1210,6 +1232,11 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
     const bool orth = (cx.mode == kModeOrth);
     const double onenrm = sg.onenrm, dtpcrt = sg.dtpcrt;
     const int64_t kstart = orth ? 0 : 1;
+    if (!TINV_IN(s0 >= 0 && mc >= 1 && s0 + mc <= w.nM && n <= p.n &&
+                     (orth || dbg_range((int64_t)jr.off, (int64_t)jr.off + mc * n, w.nF)) &&
+                     (p.zlen == 0 || dbg_range(sg.z + jr.jl * ldz, sg.z + (jr.jl + mc - 1) * ldz + n, p.zlen)),
+                 cx.err))
+        return false;
     for (int64_t kk = kstart; kk < mc; ++kk) {
         const int64_t j = s0 + kk;
         const Fac f = orth ? Fac{} : fac_at(w, jr.off + (size_t)kk * (size_t)n);
@@ -1237,7 +1264,7 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
                 const bool may_end = nrmchk >= kExtra || its == maxits;
                 TeamRef tr{nullptr, &tgt, 1, 0, cx.err, nullptr, 0ull,
                            (unsigned long long*)&w.ctr[kCtrFallback],
-                           may_end ? kSolveTol : kSolveTolLoose};
+                           may_end ? kSolveTol : kSolveTolLoose, 0u};
                 if (!team_solve(n, f, v, scl, v, nullptr, cx.s1, 0, n, nullptr, nullptr, tr, red))
                     return false;
             }
@@ -1348,6 +1375,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t
 
     const int32_t tf = w.sched[4 * b + 0], tg = w.sched[4 * b + 1], tr = w.sched[4 * b + 2],
                   tc = w.sched[4 * b + 3];
+    if (!TINV_IN(tf >= 0 && tg >= 1 && tf + tg <= w.P && tr >= 0 && tr < tg && tc < (int32_t)w.nM,
+                 (int*)&w.ctr[kCtrErr]))
+        return;
     if (tc >= 0) {
         Team tm{tf, tg, tr, w.bar + tf, 0u};
         const bool ok = (METHOD == 0) ? cwy_cluster(cx, tc, tm) : mgs_cluster(cx, tc);
@@ -1364,6 +1394,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t
         const int32_t c = s_c;
         __syncthreads();
         if (c < 0) break;
+        if (!TINV_IN(c < (int32_t)w.nM, cx.err)) return;
         Team tm{b, 1, 0, w.bar + b, 0u};
         const bool ok = (METHOD == 0) ? cwy_cluster(cx, c, tm) : mgs_cluster(cx, c);
         if (!ok) return;
