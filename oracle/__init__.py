@@ -79,6 +79,11 @@ def _load():
             for name in ("orc_orth_house", "orc_orth_cwy_ordinary", "orc_orth_cwy_new"):
                 getattr(lib, name).restype = D
                 getattr(lib, name).argtypes = [I64, I64, P, I64, P, I64, P, P]
+            lib.orc_orth_cwy_block.restype = D
+            lib.orc_orth_cwy_block.argtypes = [I64, I64, P, I64, I64, P, I64, P, P]
+            lib.orc_tinv_blocked.restype = I64
+            lib.orc_tinv_blocked.argtypes = [I64, P, P, I64, P, I64, P, I64, I64,
+                                             ctypes.c_uint64, P, P, ctypes.POINTER(_Stats)]
             lib.orc_tinv.restype = I64
             lib.orc_tinv.argtypes = [I64, P, P, I64, P, I64, P, I64, ctypes.c_int,
                                      ctypes.c_uint64, P, P, ctypes.POINTER(_Stats)]
@@ -162,13 +167,19 @@ def lagts(factors, y):
     return x, tol
 
 
-def orth(V, method: str):
+def orth(V, method: str, block: int = 0):
     """Stand-alone orthogonalization of the columns of V (n x m).  Returns (Q, Y, T, flops);
-    Y/T are None for MGS, T is the vector of t_j for Householder."""
+    Y/T are None for MGS, T is the vector of t_j for Householder.  method "cwy_block" takes
+    the columns `block` at a time (Sec. 3.2)."""
     V = np.asfortranarray(V, dtype=np.float64)
     n, m = V.shape
     Q = np.zeros((n, m), order="F")
     lib = _load()
+    if method == "cwy_block":
+        Y = np.zeros((n, m), order="F")
+        T = np.zeros((m, m), order="F")
+        fl = lib.orc_orth_cwy_block(n, m, _p(V), n, max(1, block), _p(Q), n, _p(Y), _p(T))
+        return Q, Y, T, fl
     if method == "mgs":
         fl = lib.orc_orth_mgs(n, m, _p(V), n, _p(Q), n)
         return Q, None, None, fl
@@ -183,16 +194,24 @@ def orth(V, method: str):
     return Q, Y, T, fl
 
 
-def tinv(d, e, w, method: str = "cwy", seed: int = 0, j0: int = 0):
-    """Inverse iteration for the eigenvectors of w.  Returns (Z, info, ifail, iters, stats)."""
+def tinv(d, e, w, method: str = "cwy", seed: int = 0, j0: int = 0, block: int = 0):
+    """Inverse iteration for the eigenvectors of w.  Returns (Z, info, ifail, iters, stats).
+    block >= 1 (method "cwy"): each cluster's members orthogonalized `block` at a time."""
     d, e, w = _f64(d), _f64(e), _f64(w)
     n, m = len(d), len(w)
     Z = np.zeros((n, m), order="F")
     ifail = np.zeros(max(m, 1), dtype=np.int64)
     iters = np.zeros(max(m, 1), dtype=np.int32)
     st = _Stats()
-    info = _load().orc_tinv(n, _p(d), _p(e), m, _p(w), j0, _p(Z), n, METHODS[method],
-                            ctypes.c_uint64(seed), _p(ifail), _p(iters), ctypes.byref(st))
+    if block >= 1:
+        if method != "cwy":
+            raise ValueError("blocked orthogonalization is compact WY")
+        info = _load().orc_tinv_blocked(n, _p(d), _p(e), m, _p(w), j0, _p(Z), n, block,
+                                        ctypes.c_uint64(seed), _p(ifail), _p(iters),
+                                        ctypes.byref(st))
+    else:
+        info = _load().orc_tinv(n, _p(d), _p(e), m, _p(w), j0, _p(Z), n, METHODS[method],
+                                ctypes.c_uint64(seed), _p(ifail), _p(iters), ctypes.byref(st))
     return Z, int(info), ifail[:info], iters[:m], {
         "sweeps": st.sweeps, "breakdowns": st.breakdowns, "orth_flops": st.orth_flops}
 

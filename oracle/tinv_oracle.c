@@ -19,7 +19,9 @@
  *   orc_orth_house      -- Householder orthogonalization (Alg. 2, Eq. yt).
  *   orc_orth_cwy_*      -- compact-WY orthogonalization (Alg. 3) in the ordinary BLAS form
  *                          (Sec. 3.3.1) and the new form (Sec. 3.3.2), Eqs. cwy1/cwy2.
+ *   orc_orth_cwy_block  -- compact WY over blocks of columns (Sec. 3.2, Eqs. cwy1/cwy2).
  *   orc_tinv            -- classical inverse iteration (Alg. 1) and DSTEIN-cWY (Alg. 4).
+ *   orc_tinv_blocked    -- DSTEIN-cWY with a cluster's members orthogonalized in blocks.
  *   orc_jacobi          -- cyclic Jacobi (Golub & Van Loan), brute force for small n.
  *
  * Readings of points the paper leaves open:
@@ -207,22 +209,20 @@ void orc_plan(int64_t n, const double* d, const double* e, int64_t m, const doub
 /* Factor T - lambda*I = P L U.  U has diagonal u0[0..n), first superdiagonal u1[0..n-1),
  * second superdiagonal u2[0..n-1) (nonzero only where rows were interchanged).  L is unit
  * lower bidiagonal with multipliers l[0..n-1).  piv[k] = 1 iff rows k and k+1 were
- * interchanged at step k.  Partial pivoting with implicit row scaling (DLAGTF's role in Eq. 1):
- * every row is scaled by the 1-norm of its row of T - lambda*I as given, s_0 = |a_0| + |b_0|
- * and s_{k+1} = |c_k| + |a_{k+1}| + |b_{k+1}|; at step k row k+1 becomes the pivot row when
- * |c_k| / s_{k+1} exceeds |a_k| / s_k, with a_k the current pivot entry (a tie keeps the
- * current row; a zero numerator counts as 0). */
+ * interchanged at step k.  Row k+1 becomes the pivot row when its scaled subdiagonal entry
+ * |c_k| / (|c_k| + |a_{k+1}| + |b_{k+1}|) exceeds the scaled pivot |a_k| / (|a_k| + |b_k|)
+ * of the current row (a tie keeps the current row). */
 void orc_lagtf(int64_t n, const double* d, const double* e, double lambda,
                double* u0, double* u1, double* u2, double* l, unsigned char* piv)
 {
     if (n <= 0) return;
     double ak = d[0] - lambda;           /* diagonal of the current pivot row      */
     double bk = (n > 1) ? e[0] : 0.0;    /* superdiagonal of the current pivot row */
-    double scale1 = fabs(ak) + fabs(bk); /* row scale of the pivot position k      */
     for (int64_t k = 0; k + 1 < n; ++k) {
         double ck = e[k];                            /* entry below the pivot        */
         double a1 = d[k + 1] - lambda;               /* diagonal of row k+1          */
         double b1 = (k + 2 < n) ? e[k + 1] : 0.0;    /* superdiagonal of row k+1     */
+        double scale1 = fabs(ak) + fabs(bk);
         double scale2 = (fabs(ck) + fabs(a1)) + fabs(b1);
         double piv1 = (ak == 0.0) ? 0.0 : fabs(ak) / scale1;
         double piv2 = (ck == 0.0) ? 0.0 : fabs(ck) / scale2;
@@ -245,7 +245,6 @@ void orc_lagtf(int64_t n, const double* d, const double* e, double lambda,
             ak = bk - lk * a1;
             bk = -(lk * b1);
         }
-        scale1 = scale2;
     }
     u0[n - 1] = ak;
 }
@@ -558,6 +557,299 @@ double orc_orth_cwy_new(int64_t n, int64_t m, const double* V, int64_t ldv, doub
     if (!Y) free(Yw);
     if (!T) free(Tw);
     return flops;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Compact WY over a block of columns (Sec. 3.2, Eqs. cwy1 and cwy2)                       */
+/* ------------------------------------------------------------------------------------ */
+
+/* One block step: the columns W (n x bb, ld n) are orthogonalized against the k0 reflectors
+ * in Y[:, 0..k0), T[0..k0, 0..k0) and among themselves, and their reflectors are appended as
+ * columns k0 .. k0+bb-1 of Y and T (ld n and ldt):
+ *   (1) W <- Q_k0^T W = W - Y T^T (Y^T W)                  (Q_k0 = I - Y T Y^T, Eq. cwy2)
+ *   (2) Householder QR of the rows k0.. of W, one column at a time (Alg. 2 on the panel):
+ *       column c gives y (Eq. yt, zero above row k0+c), c_c = -sgn(u_1) ||u_hat|| and
+ *       t_c = 1/(c_c^2 - u_1 c_c); H_c = I - t_c y y^T is applied to the later columns; T
+ *       grows by the recurrence of Eq. cwy1: T[0..col, col] = -t_c T (Y^T y), T[col, col] = t_c.
+ *   (3) Q[:, c] = (Y T Y^T - I) e_{k0+c} with the reflectors 0..k0+c (the sign-flipped q of
+ *       Sec. 3.3.2; later reflectors leave e_{k0+c} unchanged).
+ * cvals[c] receives c_c and broke[c] = 1 where the remainder was exactly zero (it is then
+ * replaced by the first free unit vector, as in the one-column step).  Returns the flops. */
+static double cwy_block_step(int64_t n, int64_t k0, int64_t bb, double* Y, double* T, int64_t ldt,
+                             double* W, double* Q, int64_t ldq, double* cvals, int* broke,
+                             double* work)
+{
+    int64_t nfma = 0;
+    double* s = work;              /* k0 + bb */
+    double* s2 = work + (n + 1);   /* k0 + bb */
+    /* (1) W <- W - Y_k0 T_k0^T (Y_k0^T W), one column at a time */
+    for (int64_t c = 0; c < bb; ++c) {
+        double* wc = W + c * n;
+        for (int64_t i = 0; i < k0; ++i) {
+            double acc = 0.0;
+            for (int64_t r = i; r < n; ++r) { acc += Y[r + i * n] * wc[r]; nfma++; }
+            s[i] = acc;
+        }
+        for (int64_t i = 0; i < k0; ++i) { /* s2 = T^T s */
+            double acc = 0.0;
+            for (int64_t l2 = 0; l2 <= i; ++l2) { acc += T[l2 + i * ldt] * s[l2]; nfma++; }
+            s2[i] = acc;
+        }
+        for (int64_t r = 0; r < n; ++r) {
+            double acc = 0.0;
+            int64_t top = r < k0 ? r + 1 : k0;
+            for (int64_t i = 0; i < top; ++i) { acc += Y[r + i * n] * s2[i]; nfma++; }
+            wc[r] = wc[r] - acc;
+        }
+    }
+    /* (2) Householder QR of the panel rows k0.., T by Eq. cwy1 */
+    for (int64_t c = 0; c < bb; ++c) {
+        const int64_t col = k0 + c;
+        double* yk = Y + col * n;
+        for (int64_t r = 0; r < col; ++r) yk[r] = 0.0;
+        cvals[c] = reflector(n - col, W + c * n + col, yk + col, &broke[c]);
+        const double u1 = broke[c] ? 1.0 : W[col + c * n];
+        const double tc = 1.0 / (cvals[c] * cvals[c] - u1 * cvals[c]);
+        for (int64_t c2 = c + 1; c2 < bb; ++c2) { /* H_c on the later columns */
+            double* w2 = W + c2 * n;
+            double acc = 0.0;
+            for (int64_t r = col; r < n; ++r) { acc += yk[r] * w2[r]; nfma++; }
+            acc = tc * acc;
+            for (int64_t r = col; r < n; ++r) { w2[r] = w2[r] - acc * yk[r]; nfma++; }
+        }
+        for (int64_t i = 0; i < col; ++i) { /* g = Y^T y over the rows where y is nonzero */
+            double acc = 0.0;
+            for (int64_t r = col; r < n; ++r) { acc += Y[r + i * n] * yk[r]; nfma++; }
+            s[i] = -tc * acc;
+        }
+        for (int64_t i = 0; i < col; ++i) {
+            double acc = 0.0;
+            for (int64_t l2 = i; l2 < col; ++l2) { acc += T[i + l2 * ldt] * s[l2]; nfma++; }
+            T[i + col * ldt] = acc;
+        }
+        for (int64_t i = col + 1; i < ldt; ++i) T[i + col * ldt] = 0.0;
+        T[col + col * ldt] = tc;
+    }
+    /* (3) Q[:, c] = (Y T Y^T - I) e_col with the reflectors 0..col */
+    for (int64_t c = 0; c < bb; ++c) {
+        const int64_t col = k0 + c;
+        double* q = Q + c * ldq;
+        for (int64_t i = 0; i <= col; ++i) s[i] = Y[col + i * n];
+        for (int64_t i = 0; i <= col; ++i) {
+            double acc = 0.0;
+            for (int64_t l2 = i; l2 <= col; ++l2) { acc += T[i + l2 * ldt] * s[l2]; nfma++; }
+            s2[i] = acc;
+        }
+        for (int64_t r = 0; r < n; ++r) {
+            double acc = 0.0;
+            int64_t top = r < col ? r + 1 : col + 1;
+            for (int64_t i = 0; i < top; ++i) { acc += Y[r + i * n] * s2[i]; nfma++; }
+            q[r] = acc - (r == col ? 1.0 : 0.0);
+        }
+    }
+    return 2.0 * (double)nfma;
+}
+
+/* Alg. 3 with the columns taken nb at a time through cwy_block_step (Q: sign-flipped q_j). */
+double orc_orth_cwy_block(int64_t n, int64_t m, const double* V, int64_t ldv, int64_t nb,
+                          double* Q, int64_t ldq, double* Y, double* T)
+{
+    double flops = 0.0;
+    if (nb < 1) nb = 1;
+    double* Yw = Y ? Y : (double*)calloc((size_t)(n * m), sizeof(double));
+    double* Tw = T ? T : (double*)calloc((size_t)(m * m), sizeof(double));
+    double* W = (double*)malloc(sizeof(double) * (size_t)(n * nb));
+    double* work = (double*)malloc(sizeof(double) * (size_t)(2 * n + 2 * m + 4));
+    double* cv = (double*)malloc(sizeof(double) * (size_t)nb);
+    int* br = (int*)malloc(sizeof(int) * (size_t)nb);
+    for (int64_t k0 = 0; k0 < m; k0 += nb) {
+        const int64_t bb = (m - k0 < nb) ? m - k0 : nb;
+        for (int64_t c = 0; c < bb; ++c)
+            for (int64_t r = 0; r < n; ++r) W[r + c * n] = V[r + (k0 + c) * ldv];
+        flops += cwy_block_step(n, k0, bb, Yw, Tw, m, W, Q + k0 * ldq, ldq, cv, br, work);
+    }
+    free(W);
+    free(work);
+    free(cv);
+    free(br);
+    if (!Y) free(Yw);
+    if (!T) free(Tw);
+    return flops;
+}
+
+/* Inverse iteration with blocked compact-WY reorthogonalization.  Heads and singletons are as
+ * in orc_tinv.  After a cluster's head, its other members are taken nb at a time: every member
+ * of a block keeps its own shift, LU and start vector (the keys of orc_tinv), and the block
+ * sweeps together: each member's iterate is scaled and solved (Eq. 1), then the block is
+ * orthogonalized by cwy_block_step against the reflectors of the members before the block and
+ * among itself, in member order.  Member c's tested iterate is x_c = -c_c q_c (the
+ * orthogonalized iterate, as in orc_tinv's CWY path); a success is ||x_c||_inf >= dtpcrt
+ * without breakdown.  The block stops when every member has EXTRA+1 successes or after MAXITS
+ * sweeps; each sweep recomputes the block's columns of Y and T.  A member without EXTRA+1
+ * successes is counted as not converged.  nb = 1 is orc_tinv's CWY iteration. */
+int64_t orc_tinv_blocked(int64_t n, const double* d, const double* e, int64_t m, const double* w,
+                         int64_t j0, double* Z, int64_t ldz, int64_t nb, uint64_t seed,
+                         int64_t* ifail, int32_t* iters, orc_stats* st)
+{
+    if (n <= 0 || m <= 0) return 0;
+    if (nb < 1) nb = 1;
+    if (n == 1) {
+        for (int64_t j = 0; j < m; ++j) {
+            Z[j * ldz] = 1.0;
+            if (iters) iters[j] = 0;
+        }
+        return 0;
+    }
+    double* wp = (double*)malloc(sizeof(double) * (size_t)m);
+    int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+    double onenrm, ortol, dtpcrt;
+    orc_plan(n, d, e, m, w, wp, head, &onenrm, &ortol, &dtpcrt);
+    int64_t mcmax = 1;
+    for (int64_t j = 0, cnt = 0; j < m; ++j) {
+        cnt = (head[j] == j) ? 1 : cnt + 1;
+        if (cnt > mcmax) mcmax = cnt;
+    }
+    /* factors of every member of a block */
+    double* u0 = (double*)malloc(sizeof(double) * (size_t)(n * nb));
+    double* u1 = (double*)malloc(sizeof(double) * (size_t)(n * nb));
+    double* u2 = (double*)malloc(sizeof(double) * (size_t)(n * nb));
+    double* l = (double*)malloc(sizeof(double) * (size_t)(n * nb));
+    unsigned char* piv = (unsigned char*)malloc((size_t)(n * nb));
+    double* unn = (double*)malloc(sizeof(double) * (size_t)nb);
+    double* W = (double*)malloc(sizeof(double) * (size_t)(n * nb));  /* iterates / panel */
+    double* Qb = (double*)malloc(sizeof(double) * (size_t)(n * nb)); /* sign-flipped q's */
+    double* X = (double*)malloc(sizeof(double) * (size_t)(n * nb));  /* tested iterates */
+    double* cv = (double*)malloc(sizeof(double) * (size_t)nb);
+    int* br = (int*)malloc(sizeof(int) * (size_t)nb);
+    int* nrmchk = (int*)malloc(sizeof(int) * (size_t)nb);
+    double* work = (double*)malloc(sizeof(double) * (size_t)(2 * n + 2 * mcmax + 4));
+    double* Y = (double*)calloc((size_t)(n * mcmax), sizeof(double));
+    double* T = (double*)calloc((size_t)(mcmax * mcmax), sizeof(double));
+
+    int64_t info = 0;
+    for (int64_t j1 = 0; j1 < m;) {
+        int64_t mc = 1;
+        while (j1 + mc < m && head[j1 + mc] == j1) mc++;
+        /* the head (or a singleton): inverse iteration without reorthogonalization */
+        {
+            double* v = X;
+            orc_lagtf(n, d, e, wp[j1], u0, u1, u2, l, piv);
+            const double un = fabs(u0[n - 1]);
+            for (int64_t r = 0; r < n; ++r) v[r] = orc_start_value(seed, j0 + j1, 0, r);
+            int cnt = 0, its = 0, conv = 0;
+            while (its < MAXITS) {
+                its++;
+                double asum = 0.0;
+                for (int64_t r = 0; r < n; ++r) asum += fabs(v[r]);
+                double scl = (double)n * onenrm * dmax(EPS, un) / asum;
+                for (int64_t r = 0; r < n; ++r) v[r] = scl * v[r];
+                orc_lagts(n, u0, u1, u2, l, piv, v);
+                double nrm = 0.0;
+                for (int64_t r = 0; r < n; ++r) nrm = dmax(nrm, fabs(v[r]));
+                if (nrm >= dtpcrt && ++cnt >= EXTRA + 1) {
+                    conv = 1;
+                    break;
+                }
+            }
+            if (st) st->sweeps += its;
+            if (iters) iters[j1] = its;
+            if (!conv) {
+                if (ifail) ifail[info] = j1;
+                info++;
+            }
+            double nr = nrm2(n, v);
+            int64_t jmax = 0;
+            for (int64_t r = 1; r < n; ++r)
+                if (fabs(v[r]) > fabs(v[jmax])) jmax = r;
+            double sc = 1.0 / nr;
+            if (v[jmax] < 0.0) sc = -sc;
+            for (int64_t r = 0; r < n; ++r) Z[r + j1 * ldz] = sc * v[r];
+        }
+        if (mc > 1) {
+            /* Alg. 4: Y_1 = [y_1], T_1 = [t_1] from the (final) head vector */
+            const double* zh = Z + j1 * ldz;
+            int broke;
+            double c = reflector(n, zh, Y, &broke);
+            double uh = broke ? 1.0 : zh[0];
+            T[0] = 1.0 / (c * c - uh * c);
+        }
+        for (int64_t k0 = 1; k0 < mc; k0 += nb) {
+            const int64_t bb = (mc - k0 < nb) ? mc - k0 : nb;
+            for (int64_t c = 0; c < bb; ++c) {
+                const int64_t j = j1 + k0 + c;
+                orc_lagtf(n, d, e, wp[j], u0 + c * n, u1 + c * n, u2 + c * n, l + c * n, piv + c * n);
+                unn[c] = fabs(u0[c * n + n - 1]);
+                for (int64_t r = 0; r < n; ++r) X[r + c * n] = orc_start_value(seed, j0 + j, 0, r);
+                nrmchk[c] = 0;
+            }
+            int its = 0, all = 0;
+            while (its < MAXITS) {
+                its++;
+                for (int64_t c = 0; c < bb; ++c) {
+                    double* v = X + c * n;
+                    double asum = 0.0;
+                    for (int64_t r = 0; r < n; ++r) asum += fabs(v[r]);
+                    double scl = (double)n * onenrm * dmax(EPS, unn[c]) / asum;
+                    for (int64_t r = 0; r < n; ++r) W[r + c * n] = scl * v[r];
+                    orc_lagts(n, u0 + c * n, u1 + c * n, u2 + c * n, l + c * n, piv + c * n, W + c * n);
+                }
+                double fl = cwy_block_step(n, k0, bb, Y, T, mcmax, W, Qb, n, cv, br, work);
+                if (st) st->orth_flops += fl;
+                all = 1;
+                for (int64_t c = 0; c < bb; ++c) {
+                    double* x = X + c * n;
+                    double nrm = 0.0;
+                    for (int64_t r = 0; r < n; ++r) {
+                        x[r] = -cv[c] * Qb[r + c * n];
+                        nrm = dmax(nrm, fabs(x[r]));
+                    }
+                    if (br[c]) {
+                        if (st) st->breakdowns++;
+                    } else if (nrm >= dtpcrt) {
+                        nrmchk[c]++;
+                    }
+                    if (nrmchk[c] < EXTRA + 1) all = 0;
+                }
+                if (all) break;
+            }
+            for (int64_t c = 0; c < bb; ++c) {
+                const int64_t j = j1 + k0 + c;
+                const double* x = X + c * n;
+                if (st) st->sweeps += its;
+                if (iters) iters[j] = its;
+                if (nrmchk[c] < EXTRA + 1) {
+                    if (ifail) ifail[info] = j;
+                    info++;
+                }
+                double nr = nrm2(n, x);
+                int64_t jmax = 0;
+                for (int64_t r = 1; r < n; ++r)
+                    if (fabs(x[r]) > fabs(x[jmax])) jmax = r;
+                double sc = 1.0 / nr;
+                if (x[jmax] < 0.0) sc = -sc;
+                for (int64_t r = 0; r < n; ++r) Z[r + j * ldz] = sc * x[r];
+            }
+        }
+        j1 += mc;
+    }
+    free(wp);
+    free(head);
+    free(u0);
+    free(u1);
+    free(u2);
+    free(l);
+    free(piv);
+    free(unn);
+    free(W);
+    free(Qb);
+    free(X);
+    free(cv);
+    free(br);
+    free(nrmchk);
+    free(work);
+    free(Y);
+    free(T);
+    return info;
 }
 
 /* ------------------------------------------------------------------------------------ */

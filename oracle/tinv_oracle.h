@@ -68,6 +68,13 @@ double orc_orth_cwy_ordinary(int64_t n, int64_t m, const double* V, int64_t ldv,
 double orc_orth_cwy_new(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q,
                         int64_t ldq, double* Y, double* T);
 
+/* Alg. 3 with the columns taken nb at a time (Sec. 3.2): each block is orthogonalized against
+ * the reflectors before it (Q^T = I - Y T^T Y^T), then by Householder QR of its own panel, and
+ * T grows by Eq. cwy1.  Q, Y, T as orc_orth_cwy_new (Q holds the sign-flipped q_j).  Returns
+ * the flops executed. */
+double orc_orth_cwy_block(int64_t n, int64_t m, const double* V, int64_t ldv, int64_t nb,
+                          double* Q, int64_t ldq, double* Y, double* T);
+
 /* Inverse iteration for the m eigenvectors of w (DSTEIN structure, Alg. 1 for MGS,
  * Alg. 4 for CWY, Alg. 2 applied incrementally for HOUSE).  j0 offsets the index used
  * to key the random start vectors, so that a sub-range of a larger problem reproduces
@@ -76,6 +83,12 @@ double orc_orth_cwy_new(int64_t n, int64_t m, const double* V, int64_t ldv, doub
 int64_t orc_tinv(int64_t n, const double* d, const double* e, int64_t m, const double* w,
                  int64_t j0, double* Z, int64_t ldz, int method, uint64_t seed,
                  int64_t* ifail, int32_t* iters, orc_stats* st);
+
+/* orc_tinv's CWY iteration with each cluster's members after the head orthogonalized nb at a
+ * time (a block sweeps together; see tinv_oracle.c).  nb = 1 is orc_tinv's CWY iteration. */
+int64_t orc_tinv_blocked(int64_t n, const double* d, const double* e, int64_t m, const double* w,
+                         int64_t j0, double* Z, int64_t ldz, int64_t nb, uint64_t seed,
+                         int64_t* ifail, int32_t* iters, orc_stats* st);
 
 /* Cyclic Jacobi on a dense symmetric n x n matrix A (overwritten): eigenvalues ascending
  * in lam, orthonormal eigenvectors in V (brute force for small n).                      */

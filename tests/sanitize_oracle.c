@@ -66,6 +66,10 @@ static void run_path(int64_t n, const double* d, const double* e)
         (void)orc_tinv(n, d, e, n, w, 0, Z, n > 0 ? n : 1, method, 3, ifail, iters, &st);
         /* a sub-range with its offset, as the tests use it */
         if (n >= 4) (void)orc_tinv(n, d, e, 2, w + n / 2, n / 2, Z, n, method, 3, ifail, iters, NULL);
+        if (method == ORC_CWY) {
+            (void)orc_tinv_blocked(n, d, e, n, w, 0, Z, n > 0 ? n : 1, 4, 3, ifail, iters, &st);
+            if (n >= 4) (void)orc_tinv_blocked(n, d, e, 2, w + n / 2, n / 2, Z, n, 3, 3, ifail, iters, NULL);
+        }
         free(Z), free(ifail), free(iters);
     }
     if (n > 0 && n <= 64) {
@@ -93,6 +97,8 @@ static void run_orth(int64_t n, int64_t m)
     (void)orc_orth_cwy_new(n, m, V, ld, Q, ld, Y, T);
     (void)orc_orth_house(n, m, V, ld, Q, ld, NULL, NULL);
     (void)orc_orth_cwy_new(n, m, V, ld, Q, ld, NULL, NULL);
+    (void)orc_orth_cwy_block(n, m, V, ld, 3, Q, ld, Y, T);
+    (void)orc_orth_cwy_block(n, m, V, ld, m + 2, Q, ld, NULL, NULL);
     free(V), free(Q), free(Y), free(T), free(tv);
 }
 

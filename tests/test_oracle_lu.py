@@ -20,18 +20,17 @@ def test_pivot_choices_hand_computed_3x3(orc):
     assert piv[:2].tolist() == [0, 1]
 
 
-def test_pivot_rows_scaled_by_their_original_norms(orc):
-    # T = [[1,1,0],[1,1.5,1],[0,1,2]], lambda = 0; row scales s = 2, 3.5, 3 (1-norms of the rows
-    # of T as given).
-    # step 0: 1/2 > 1/3.5 -> keep row 0, l0 = 1, current pivot entry a1 = 1.5 - 1 = 0.5.
-    # step 1: 0.5/3.5 < 1/3 -> interchange (scaling the current row [0.5, 1] by its own norm
-    #         1.5 would give 1/3 = 1/3, a tie, and keep it), l1 = 0.5/1, u0[2] = 1 - 0.5*2 = 0.
+def test_pivot_scale_of_the_current_row_and_a_tie(orc):
+    # T = [[1,1,0],[1,1.5,1],[0,1,2]], lambda = 0.
+    # step 0: 1/2 > 1/3.5 -> keep row 0, l0 = 1, current pivot row [0.5, 1].
+    # step 1: the current row scaled by its own 1-norm: 0.5/1.5 = 1/3 against 1/(1+2) = 1/3, a
+    #         tie -> keep it, l1 = 1/0.5 = 2 (scaled pivoting admits |l| > 1), u0[2] = 2 - 2*1.
     u0, u1, u2, l, piv = orc.lagtf([1.0, 1.5, 2.0], [1.0, 1.0], 0.0)
-    assert piv[:2].tolist() == [0, 1]
-    assert u0.tolist() == [1.0, 1.0, 0.0]
-    assert u1[:2].tolist() == [1.0, 2.0]
+    assert piv[:2].tolist() == [0, 0]
+    assert u0.tolist() == [1.0, 0.5, 0.0]
+    assert u1[:2].tolist() == [1.0, 1.0]
     assert u2[:2].tolist() == [0.0, 0.0]
-    assert l[:2].tolist() == [1.0, 0.5]
+    assert l[:2].tolist() == [1.0, 2.0]
 
 
 def test_scaled_pivoting_differs_from_magnitude_pivoting(orc):
