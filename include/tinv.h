@@ -83,7 +83,14 @@ typedef struct tinv_opts {
                          /*   gives up (0 = the default: 4e8 polls or 20 s, whichever is first); */
                          /*   a small value makes a launch end with TINV_ETIMEDOUT, which tests  */
                          /*   the bounded-wait failure path without hanging the GPU              */
-    int32_t reserved[4];
+    int32_t block;       /* compact WY only: 0 or 1 = each cluster member orthogonalized on its  */
+                         /*   own (Alg. 4); b = 2..8 = a cluster's members after its head in    */
+                         /*   blocks of up to b that sweep together and are orthogonalized by   */
+                         /*   the compact-WY block form of Sec. 3.2 (Eqs. cwy1/cwy2).  Applies  */
+                         /*   to clusters on CTA teams whose block staging fits the shared      */
+                         /*   memory (the block shrinks to fit: b <= team size, 2 b m_c <= a    */
+                         /*   per-order capacity); other clusters take b = 1                    */
+    int32_t reserved[3];
 } tinv_opts;
 
 /* Fill *o with the defaults: CWY, host pointers, seed 0, j0 0, automatic scheduling. */
@@ -157,25 +164,64 @@ size_t tinv_workspace_size(int64_t n, int64_t m, const tinv_opts* o);
 int tinv_tune(int64_t n, const double* d, const double* e, int64_t m, const double* w,
               const tinv_opts* o, int32_t reps, int32_t* max_team, float* ms, int32_t* cached);
 
-/* Empty the tune cache of tinv_tune. */
+/* Result of tinv_tune_auto / tinv_tune_batch. */
+typedef struct tinv_tuning {
+    int32_t max_team; /* chosen team cap (tinv_opts.max_team; 0 = the automatic rule)            */
+    int32_t block;    /* chosen block (tinv_opts.block; 0 = one member at a time)                */
+    float ms;         /* mean device milliseconds of one call with the choice                    */
+    int32_t cached;   /* 1 when the choice came from the tune cache and nothing was run           */
+    int32_t reserved[4];
+} tinv_tuning;
+
+/*
+ * tinv_tune_auto -- tinv_tune over both launch parameters of the cluster kernel: the switch
+ * between one member at a time (Sec. 3.3.2, GEMV passes) and the blocked compact-WY form of
+ * Sec. 3.2 (tinv_opts.block 4 or 8, passes over Y for several members at once), then the team
+ * cap with the chosen block.  Each stage keeps the current choice unless a candidate is at least
+ * 1% faster; MGS and problems without multi-member clusters take (0, 0).  Arguments as
+ * tinv_tune (o->block and o->max_team are not used); *out receives the choice.  Cached like
+ * tinv_tune under a key of its own.  Returns as tinv_tune, with -8 for out == NULL.
+ */
+int tinv_tune_auto(int64_t n, const double* d, const double* e, int64_t m, const double* w,
+                   const tinv_opts* o, int32_t reps, tinv_tuning* out);
+
+/*
+ * tinv_tune_batch -- the same two-stage search for a batch (tinv_batch), timing tinv_batch on the
+ * caller's problems.  Arguments as tinv_batch (d, e, w host or device memory per o->device_ptrs;
+ * n, off_de, off_z host arrays); reps timed calls per candidate.  The tune cache key is the
+ * batch's size profile: device, SM count, method, grid cap, the total order, the number of
+ * problems, a 62-bit hash of the count of problems in each power-of-two order class, and the
+ * largest order.  The call allocates its own Z, info and workspace and synchronizes.  Returns 0;
+ * -1 nprob < 0; -2 n; -3 off_de; -4 off_z (NULL or negative); -5 d; -6 e; -7 w (NULL; with
+ * host pointers also non-finite or not ascending); -8 method; -9 reps < 1; -10 out NULL; or a
+ * runtime code.
+ */
+int tinv_tune_batch(int64_t nprob, const int64_t* n, const int64_t* off_de, const int64_t* off_z,
+                    const double* d, const double* e, const double* w, const tinv_opts* o,
+                    int32_t reps, tinv_tuning* out);
+
+/* Empty the tune cache of tinv_tune, tinv_tune_auto and tinv_tune_batch. */
 void tinv_tune_clear(void);
 
 /*
  * tinv_tune_save -- write the tune cache to `path` (created or truncated): a tag line
- * "# tinv tune cache v1", then one entry per line with tab-separated fields: device name, SM
- * count, method, grid cap, n, m, clusters with >= 2 members, largest cluster, chosen cap,
- * milliseconds.  Returns 0, -1 (path NULL) or -2 (the file cannot be written).
+ * "# tinv tune cache v2", then one entry per line with tab-separated fields: kind (0 tinv_tune,
+ * 1 tinv_tune_auto, 2 tinv_tune_batch), device name, SM count, method, grid cap, the options'
+ * block, n, m, clusters with >= 2 members (batch: size-profile hash), largest cluster (batch:
+ * largest order), chosen cap, chosen block, milliseconds.  Returns 0, -1 (path NULL) or -2 (the
+ * file cannot be written).
  */
 int tinv_tune_save(const char* path);
 
 /*
  * tinv_tune_load -- merge the entries of a file written by tinv_tune_save into the tune cache
- * (an entry with the same key is replaced).  Returns the number of entries read (>= 0), -1 (path
- * NULL), -2 (the file cannot be read or lacks the tag line) or -3 (a malformed entry -- a
+ * (an entry with the same key is replaced); files with the v1 tag (no kind and no block fields)
+ * are read as tinv_tune entries with block 0.  Returns the number of entries read (>= 0), -1
+ * (path NULL), -2 (the file cannot be read or lacks a tag line) or -3 (a malformed entry -- a
  * missing or non-numeric field, trailing text, a line longer than 1023 bytes, or a value out of
- * range: SM count <= 0, m > n, largest cluster > m, cap outside [0, 192], time negative or not
- * finite, unknown method; the entries before it are kept, the rest of the file is not read).
- * No device is needed.
+ * range: unknown kind, SM count <= 0, m > n or largest cluster > m (kinds 0 and 1), cap outside
+ * [0, 192], block outside [0, 8], time negative or not finite, unknown method; the entries before
+ * it are kept, the rest of the file is not read).  No device is needed.
  */
 int tinv_tune_load(const char* path);
 

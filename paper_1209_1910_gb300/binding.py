@@ -27,7 +27,8 @@ ERRORS = {-101: "ENOMEM", -102: "ECUDA", -103: "ETIMEDOUT", -104: "EAGAIN", -105
 EXPORTS = ["tinv_opts_default", "tinv_strerror", "tinv_version", "tinv", "tinv_ex",
            "tinv_workspace_size", "tinv_batch", "tinv_batch_workspace_size", "tinv_bisect",
            "tinv_bisect_batch", "tinv_split", "tinv_eig", "tinv_bdsvd",
-           "tinv_plan", "tinv_tune", "tinv_tune_clear", "tinv_tune_save", "tinv_tune_load",
+           "tinv_plan", "tinv_tune", "tinv_tune_auto", "tinv_tune_batch", "tinv_tune_clear",
+           "tinv_tune_save", "tinv_tune_load",
            "tinv_lu", "tinv_solve", "tinv_solve_noalloc", "tinv_orth",
            "tinv_server_cfg_default", "tinv_server_create", "tinv_submit", "tinv_poll",
            "tinv_wait", "tinv_cancel", "tinv_server_stats", "tinv_server_destroy"]
@@ -48,7 +49,12 @@ class Opts(ctypes.Structure):
                 ("max_team", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
                 ("phase_ms", ctypes.c_void_p), ("counters", ctypes.c_void_p),
                 ("table_ready", ctypes.c_int32), ("spin_limit", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("block", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("max_team", ctypes.c_int32), ("block", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("cached", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 def load(path: str | None = None) -> ctypes.CDLL:
@@ -119,6 +125,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_int32)]
             lib.tinv_tune.restype = ctypes.c_int
+            lib.tinv_tune_auto.argtypes = [I64, P, P, I64, P, ctypes.POINTER(Opts), I32,
+                                           ctypes.POINTER(Tuning)]
+            lib.tinv_tune_auto.restype = ctypes.c_int
+            lib.tinv_tune_batch.argtypes = [I64, P, P, P, P, P, P, ctypes.POINTER(Opts), I32,
+                                            ctypes.POINTER(Tuning)]
+            lib.tinv_tune_batch.restype = ctypes.c_int
             lib.tinv_tune_clear.argtypes = []
             lib.tinv_tune_clear.restype = None
             lib.tinv_tune_save.argtypes = [ctypes.c_char_p]
@@ -210,6 +222,31 @@ def tune(d, e, w, reps=2, **kw):
     _check(load().tinv_tune(n, _ptr(d), _ptr(e), m, _ptr(w), ctypes.byref(o), reps,
                             ctypes.byref(mt), ctypes.byref(ms), ctypes.byref(cached)), "tinv_tune")
     return int(mt.value), float(ms.value), bool(cached.value)
+
+
+def tune_auto(d, e, w, reps=2, **kw):
+    """tinv_tune_auto: (max_team, block, ms, cached) for this problem."""
+    d, e, w = _f64(d), _f64(e), _f64(w)
+    t = Tuning()
+    _check(load().tinv_tune_auto(len(d), _ptr(d), _ptr(e), len(w), _ptr(w), ctypes.byref(_opts(**kw)),
+                                 reps, ctypes.byref(t)), "tinv_tune_auto")
+    return int(t.max_team), int(t.block), float(t.ms), bool(t.cached)
+
+
+def tune_batch(ds, es, ws, reps=1, **kw):
+    """tinv_tune_batch on host arrays of the problems: (max_team, block, ms, cached)."""
+    ns, off_de, off_z = pack_offsets([len(d) for d in ds])
+    M = int(ns.sum())
+    D, E, W = np.zeros(max(M, 1)), np.zeros(max(M, 1)), np.zeros(max(M, 1))
+    for q, (d, e, w) in enumerate(zip(ds, es, ws)):
+        a, n = int(off_de[q]), int(ns[q])
+        D[a:a + n], W[a:a + n] = d, w
+        if n > 1:
+            E[a:a + n - 1] = e
+    t = Tuning()
+    _check(load().tinv_tune_batch(len(ns), _ptr(ns), _ptr(off_de), _ptr(off_z), _ptr(D), _ptr(E), _ptr(W),
+                                  ctypes.byref(_opts(**kw)), reps, ctypes.byref(t)), "tinv_tune_batch")
+    return int(t.max_team), int(t.block), float(t.ms), bool(t.cached)
 
 
 def tune_clear():

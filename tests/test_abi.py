@@ -206,22 +206,30 @@ def test_tune_argument_checks(lib):
 
 def test_tune_cache_file_round_trip(lib, tmp_path):
     # the tune cache's file form needs no device: load, save, reload give the same entries
-    tag = "# tinv tune cache v1\n"
-    rows = ["NVIDIA GB300\t152\t0\t0\t4200\t4200\t14\t400\t0\t171.894\n",
-            "NVIDIA GB300\t152\t0\t0\t2100\t2100\t14\t200\t16\t43.15\n",
-            "NVIDIA GB300\t152\t1\t0\t210\t210\t14\t20\t0\t3.5\n"]
+    tag = "# tinv tune cache v2\n"
+    rows = ["0\tNVIDIA GB300\t152\t0\t0\t0\t4200\t4200\t14\t400\t0\t0\t171.894\n",
+            "1\tNVIDIA GB300\t152\t0\t0\t0\t2100\t2100\t14\t200\t16\t8\t43.15\n",
+            "0\tNVIDIA GB300\t152\t1\t0\t0\t210\t210\t14\t20\t0\t0\t3.5\n",
+            "2\tNVIDIA GB300\t152\t0\t0\t0\t560000\t512\t123456789\t4096\t0\t8\t2100.5\n"]
     src, out, out2 = tmp_path / "a.txt", tmp_path / "b.txt", tmp_path / "c.txt"
     src.write_text(tag + "".join(rows))
     lib.tinv_tune_clear()
-    assert lib.tinv_tune_load(str(src).encode()) == 3
+    assert lib.tinv_tune_load(str(src).encode()) == 4
     assert lib.tinv_tune_save(str(out).encode()) == 0
     text = out.read_text()
     assert text.startswith(tag) and sorted(text[len(tag):].splitlines()) == sorted(
         r.rstrip("\n") for r in rows)
     # the same entries again replace, they do not duplicate
-    assert binding.tune_load(str(out)) == 3
+    assert binding.tune_load(str(out)) == 4
     binding.tune_save(str(out2))
     assert out2.read_text() == text
+    # a v1 file (no kind, no blocks) reads as tinv_tune entries with block 0
+    v1 = tmp_path / "v1.txt"
+    v1.write_text("# tinv tune cache v1\nNVIDIA GB300\t152\t0\t0\t4200\t4200\t14\t400\t4\t160.5\n")
+    lib.tinv_tune_clear()
+    assert lib.tinv_tune_load(str(v1).encode()) == 1
+    assert lib.tinv_tune_save(str(out).encode()) == 0
+    assert out.read_text() == tag + "0\tNVIDIA GB300\t152\t0\t0\t0\t4200\t4200\t14\t400\t4\t0\t160.5\n"
     # errors: NULL path, missing file, no tag line, a malformed entry (earlier entries kept)
     assert lib.tinv_tune_save(None) == -1 and lib.tinv_tune_load(None) == -1
     assert lib.tinv_tune_load(str(tmp_path / "missing.txt").encode()) == -2
@@ -229,13 +237,48 @@ def test_tune_cache_file_round_trip(lib, tmp_path):
     assert lib.tinv_tune_load(str(tmp_path / "notag.txt").encode()) == -2
     lib.tinv_tune_clear()
     bad = tmp_path / "bad.txt"
-    bad.write_text(tag + rows[0] + "NVIDIA GB300\t152\t0\t0\t10\t20\t1\t2\t0\t1.0\n" + rows[1])
-    assert lib.tinv_tune_load(str(bad).encode()) == -3  # m > n
-    assert lib.tinv_tune_save(str(out).encode()) == 0
-    assert out.read_text() == tag + rows[0]
+    for wrong in ("0\tNVIDIA GB300\t152\t0\t0\t0\t10\t20\t1\t2\t0\t0\t1.0\n",   # m > n
+                  "0\tNVIDIA GB300\t152\t0\t0\t0\t10\t10\t1\t2\t0\t9\t1.0\n",   # block > 8
+                  "3\tNVIDIA GB300\t152\t0\t0\t0\t10\t10\t1\t2\t0\t0\t1.0\n",   # unknown kind
+                  "0\tNVIDIA GB300\t152\t0\t0\t0\t10\t10\t1\t2\t0\t0\n"):         # a field short
+        bad.write_text(tag + rows[0] + wrong + rows[1])
+        lib.tinv_tune_clear()
+        assert lib.tinv_tune_load(str(bad).encode()) == -3, wrong
+        assert lib.tinv_tune_save(str(out).encode()) == 0
+        assert out.read_text() == tag + rows[0]
     lib.tinv_tune_clear()
     assert lib.tinv_tune_save(str(out).encode()) == 0 and out.read_text() == tag
     assert lib.tinv_tune_save(str(tmp_path / "no" / "such" / "dir.txt").encode()) == -2
+
+
+def test_tune_auto_and_batch_argument_checks(lib):
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    t = binding.Tuning()
+    d, e, w = np.zeros(4), np.ones(3), np.arange(4.0)
+    T = ctypes.byref(t)
+    assert lib.tinv_tune_auto(-1, None, None, 0, None, None, 1, T) == -1
+    assert lib.tinv_tune_auto(4, None, P(e), 4, P(w), None, 1, T) == -2
+    assert lib.tinv_tune_auto(4, P(d), P(e), 5, P(w), None, 1, T) == -4
+    assert lib.tinv_tune_auto(4, P(d), P(e), 4, P(w[::-1].copy()), None, 1, T) == -5
+    assert lib.tinv_tune_auto(4, P(d), P(e), 4, P(w), None, 0, T) == -7
+    assert lib.tinv_tune_auto(4, P(d), P(e), 4, P(w), None, 1, None) == -8
+    assert lib.tinv_tune_auto(0, None, None, 0, None, None, 1, T) == 0 and t.max_team == 0 and t.block == 0
+    ns, off_de, off_z = binding.pack_offsets([4, 3])
+    D, E, W = np.zeros(7), np.ones(7), np.r_[np.arange(4.0), np.arange(3.0)]
+    args = lambda: [2, P(ns), P(off_de), P(off_z), P(D), P(E), P(W), None, 1, T]
+    assert lib.tinv_tune_batch(-1, *args()[1:]) == -1
+    a = args(); a[1] = None
+    assert lib.tinv_tune_batch(*a) == -2
+    a = args(); a[4] = None
+    assert lib.tinv_tune_batch(*a) == -5
+    W2 = W.copy(); W2[1] = -1.0  # problem 0 not ascending
+    a = args(); a[6] = P(W2)
+    assert lib.tinv_tune_batch(*a) == -7
+    a = args(); a[8] = 0
+    assert lib.tinv_tune_batch(*a) == -9
+    a = args(); a[9] = None
+    assert lib.tinv_tune_batch(*a) == -10
+    assert lib.tinv_tune_batch(0, None, None, None, None, None, None, None, 1, T) == 0
 
 
 def test_server_config_and_null_checks(lib):

@@ -45,7 +45,7 @@ def test_tune_choice_cache_and_bounds(gpu, orc, tmp_path):
     path = str(tmp_path / "tune.txt")
     gpu.tune_save(path)
     lines = open(path).read().splitlines()
-    assert lines[0] == "# tinv tune cache v1" and len(lines) == 3
+    assert lines[0] == "# tinv tune cache v2" and len(lines) == 3
     gpu.tune_clear()
     _, _, cached4 = gpu.tune(d, e, w, reps=1)
     assert not cached4
@@ -61,3 +61,37 @@ def test_tune_mgs_keeps_the_automatic_rule(gpu, orc):
     w = orc.bisect(d, e)
     mt, ms, _ = gpu.tune(d, e, w, method="mgs", reps=1)
     assert mt == 0 and ms > 0.0
+
+
+def test_tune_auto_picks_block_and_cap(gpu, orc):
+    # the switch between one member at a time and the blocked compact-WY form, then the cap
+    d, e = inputs.glued_wilkinson(100, 1e-10)
+    w = orc.bisect(d, e)
+    gpu.tune_clear()
+    mt, blk, ms, cached = gpu.tune_auto(d, e, w, reps=1)
+    assert not cached and ms > 0.0
+    assert blk in (0, 4, 8)
+    assert mt == 0 or (2 <= mt <= 128 and mt & (mt - 1) == 0)
+    assert gpu.tune_auto(d, e, w, reps=1) == (mt, blk, ms, True)
+    Z = gpu.tinv(d, e, w, max_team=mt, block=blk)
+    assert residual_ratio(d, e, w, Z) <= 10 and orth_ratio(Z) <= 10
+    # MGS has neither teams nor blocks
+    mt2, blk2, _, _ = gpu.tune_auto(d, e, w, method="mgs", reps=1)
+    assert (mt2, blk2) == (0, 0)
+    gpu.tune_clear()
+
+
+def test_tune_batch_is_keyed_by_the_size_profile(gpu, orc):
+    probs = [inputs.glued_wilkinson(40, 1e-10), inputs.uniform(300, seed=2), inputs.uniform(97, seed=3)]
+    ds, es = [p[0] for p in probs], [p[1] for p in probs]
+    ws = [orc.bisect(d, e) for d, e in probs]
+    gpu.tune_clear()
+    mt, blk, ms, cached = gpu.tune_batch(ds, es, ws, reps=1)
+    assert not cached and ms > 0.0 and blk in (0, 4, 8)
+    assert gpu.tune_batch(ds, es, ws, reps=1)[3]  # the same profile: served from the cache
+    # another size profile is another key
+    assert not gpu.tune_batch(ds[:2], es[:2], ws[:2], reps=1)[3]
+    Zs = gpu.tinv_batch(ds, es, ws, max_team=mt, block=blk)
+    for d, e, w, Z in zip(ds, es, ws, Zs):
+        assert residual_ratio(d, e, w, Z) <= 10 and orth_ratio(Z) <= 10
+    gpu.tune_clear()

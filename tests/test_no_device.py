@@ -64,6 +64,11 @@ def test_every_compute_entry_point_reports_no_device(lib):
                                            None),
         "tinv_tune": lambda: lib.tinv_tune(n, P(d), P(e), n, P(w), None, 1, ctypes.byref(mt),
                                            None, None),
+        "tinv_tune_auto": lambda: lib.tinv_tune_auto(n, P(d), P(e), n, P(w), None, 1,
+                                                     ctypes.byref(binding.Tuning())),
+        "tinv_tune_batch": lambda: lib.tinv_tune_batch(
+            1, P(np.array([n], dtype=np.int64)), P(np.zeros(1, dtype=np.int64)),
+            P(np.zeros(1, dtype=np.int64)), P(d), P(e), P(w), None, 1, ctypes.byref(binding.Tuning())),
     }
     for name, call in calls.items():
         assert call() == ENODEV, name
