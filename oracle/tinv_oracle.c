@@ -678,11 +678,13 @@ double orc_orth_cwy_block(int64_t n, int64_t m, const double* V, int64_t ldv, in
 }
 
 /* Inverse iteration with blocked compact-WY reorthogonalization.  Heads and singletons are as
- * in orc_tinv.  After a cluster's head, its other members are taken nb at a time: every member
- * of a block keeps its own shift, LU and start vector (the keys of orc_tinv), and the block
- * sweeps together: each member's iterate is scaled and solved (Eq. 1), then the block is
- * orthogonalized by cwy_block_step against the reflectors of the members before the block and
- * among itself, in member order.  Member c's tested iterate is x_c = -c_c q_c (the
+ * in orc_tinv.  After a cluster's head, its other mc-1 members are split into nblk =
+ * ceil((mc-1)/nb) blocks, block b holding the members 1 + b + nblk c (evenly spread over the
+ * cluster), processed b = 0, 1, ...; the reflectors are appended to Y and T in that order.
+ * Every member of a block keeps its own shift, LU and start vector (the keys of orc_tinv), and
+ * the block sweeps together: each member's iterate is scaled and solved (Eq. 1), then the block
+ * is orthogonalized by cwy_block_step against the reflectors of the blocks before it and among
+ * itself, in member order.  Member c's tested iterate is x_c = -c_c q_c (the
  * orthogonalized iterate, as in orc_tinv's CWY path); a success is ||x_c||_inf >= dtpcrt
  * without breakdown.  The block stops when every member has EXTRA+1 successes or after MAXITS
  * sweeps; each sweep recomputes the block's columns of Y and T.  A member without EXTRA+1
@@ -773,10 +775,17 @@ int64_t orc_tinv_blocked(int64_t n, const double* d, const double* e, int64_t m,
             double uh = broke ? 1.0 : zh[0];
             T[0] = 1.0 / (c * c - uh * c);
         }
-        for (int64_t k0 = 1; k0 < mc; k0 += nb) {
-            const int64_t bb = (mc - k0 < nb) ? mc - k0 : nb;
+        /* the members 1..mc-1 go to nblk blocks of at most nb, block b holding the members
+           1 + b + nblk*c: the members that sweep together are spread evenly over the cluster,
+           so near neighbours in the spectrum are orthogonalized against finished vectors */
+        const int64_t nblk = (mc - 1 + nb - 1) / nb;
+        int64_t kpos = 1;
+        for (int64_t bi = 0; bi < nblk; ++bi) {
+            const int64_t k0 = kpos; /* Y and T columns of this block: k0 .. k0+bb-1 */
+            const int64_t bb = (mc - 1 - bi + nblk - 1) / nblk;
+            kpos += bb;
             for (int64_t c = 0; c < bb; ++c) {
-                const int64_t j = j1 + k0 + c;
+                const int64_t j = j1 + 1 + bi + nblk * c;
                 orc_lagtf(n, d, e, wp[j], u0 + c * n, u1 + c * n, u2 + c * n, l + c * n, piv + c * n);
                 unn[c] = fabs(u0[c * n + n - 1]);
                 for (int64_t r = 0; r < n; ++r) X[r + c * n] = orc_start_value(seed, j0 + j, 0, r);
@@ -813,7 +822,7 @@ int64_t orc_tinv_blocked(int64_t n, const double* d, const double* e, int64_t m,
                 if (all) break;
             }
             for (int64_t c = 0; c < bb; ++c) {
-                const int64_t j = j1 + k0 + c;
+                const int64_t j = j1 + 1 + bi + nblk * c;
                 const double* x = X + c * n;
                 if (st) st->sweeps += its;
                 if (iters) iters[j] = its;

@@ -84,8 +84,9 @@ int64_t orc_tinv(int64_t n, const double* d, const double* e, int64_t m, const d
                  int64_t j0, double* Z, int64_t ldz, int method, uint64_t seed,
                  int64_t* ifail, int32_t* iters, orc_stats* st);
 
-/* orc_tinv's CWY iteration with each cluster's members after the head orthogonalized nb at a
- * time (a block sweeps together; see tinv_oracle.c).  nb = 1 is orc_tinv's CWY iteration. */
+/* orc_tinv's CWY iteration with each cluster's members after the head orthogonalized in blocks
+ * of at most nb members spread evenly over the cluster (a block sweeps together; see
+ * tinv_oracle.c).  nb = 1 is orc_tinv's CWY iteration. */
 int64_t orc_tinv_blocked(int64_t n, const double* d, const double* e, int64_t m, const double* w,
                          int64_t j0, double* Z, int64_t ldz, int64_t nb, uint64_t seed,
                          int64_t* ifail, int32_t* iters, orc_stats* st);

@@ -21,7 +21,7 @@ namespace tinvx {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-Dims single_dims(int64_t n, int64_t m, int32_t P)
+Dims single_dims(int64_t n, int64_t m, int32_t P, int32_t block)
 {
     Dims D;
     D.nmax = n;
@@ -30,7 +30,14 @@ Dims single_dims(int64_t n, int64_t m, int32_t P)
     D.TT = m * m;
     D.nseg = 1;
     D.P = P;
+    D.block = block;
     return D;
+}
+
+int32_t opts_block(const tinv_opts& o)
+{
+    if (o.method != TINV_CWY || o.block <= 1) return 0;
+    return o.block < kBlockMax ? o.block : kBlockMax;
 }
 
 Layout make_layout(const Dims& D, bool need_chain, bool need_rhs)
@@ -78,6 +85,13 @@ Layout make_layout(const Dims& D, bool need_chain, bool need_rhs)
         L.vbuf = take(pp * nn * sizeof(double));
         L.tpub = take(pp * 8 * sizeof(double));
         if (!chain_use_smem(D.nmax)) L.gvec = take(pp * 2 * nn * sizeof(double));
+        if (D.block >= 2 && block_xcap(D.nmax) > 0) {
+            const size_t bv = pp * (size_t)kBlockMax * nn * sizeof(double);
+            L.vblk = take(bv);
+            L.qblk = take(bv);
+            L.pblk = take(3 * bv);
+            L.tblk = take(3 * bv);
+        }
     }
     L.total = off;
     return L;
@@ -122,6 +136,14 @@ Ws bind_layout(void* base, const Layout& L, const Dims& D)
         w.vbuf = (double*)(b + L.vbuf);
         w.tpub = (double*)(b + L.tpub);
         w.gvec = L.gvec ? (double*)(b + L.gvec) : nullptr;
+        if (L.vblk) {
+            w.vblk = (double*)(b + L.vblk);
+            w.qblk = (double*)(b + L.qblk);
+            w.pblk = (double*)(b + L.pblk);
+            w.tblk = (double*)(b + L.tblk);
+            w.block = D.block;
+            w.xcap = block_xcap(D.nmax);
+        }
     }
     w.P = D.P;
     w.use_smem = chain_use_smem(D.nmax) ? 1 : 0;
@@ -242,6 +264,7 @@ int batch_tables(int64_t nprob, const int64_t* n, const int64_t* off_de, const i
     memset(&d, 0, sizeof(d));
     d.nseg = nprob;
     d.P = P;
+    d.block = opts_block(o);
     segs->assign((size_t)nprob, Seg{});
     for (int64_t q = 0; q < nprob; ++q) {
         const int64_t nq = n[q];
@@ -385,7 +408,7 @@ size_t tinv_workspace_size(int64_t n, int64_t m, const tinv_opts* o)
     if (n < 0 || m < 0) return 0;
     const Opts op(o);
     const int32_t P = chain_grid(op.o.grid_ctas, n);
-    return make_layout(single_dims(n, m, P), true).total;
+    return make_layout(single_dims(n, m, P, opts_block(op.o)), true).total;
 }
 
 int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double* w, double* Z,
@@ -415,7 +438,7 @@ int tinv_ex(int64_t n, const double* d, const double* e, int64_t m, const double
     p.nseg = 1;
     p.M = m;
     const int32_t P = chain_grid(op.o.grid_ctas, n);
-    const Dims D = single_dims(n, m, P);
+    const Dims D = single_dims(n, m, P, opts_block(op.o));
 
     if (op.o.device_ptrs) {
         cudaStream_t st = (cudaStream_t)op.o.stream;
@@ -895,7 +918,7 @@ int tinv_orth(int64_t n, int64_t m, const double* V, int64_t ldv, double* Q, int
     if (op.o.method != TINV_CWY && op.o.method != TINV_MGS) return -9;
     if (m == 0) return 0;
     int32_t P = chain_grid(op.o.grid_ctas, n);
-    const Dims D = single_dims(n, m, P);
+    const Dims D = single_dims(n, m, P, opts_block(op.o));
     const Layout L = make_layout(D, true);
     Problem p;
     memset(&p, 0, sizeof(p));

@@ -1,0 +1,684 @@
+// tinv_block.cuh -- blocked compact-WY reorthogonalization of a cluster by a CTA team
+// (tinv_opts.block >= 2): the members after the cluster's head are split into blocks of at most
+// nb that sweep together, block b holding the members 1 + b + nblk c (nblk blocks): the members
+// of a block are spread evenly over the cluster, and near neighbours in the spectrum, in
+// different blocks, are orthogonalized against finished vectors.  Per block sweep, each member's iterate is solved on its own CTA of the team
+// (no team barrier inside a solve), then the whole block is orthogonalized by the compact-WY
+// block form of Sec. 3.2 (Eqs. cwy1/cwy2): W = (I - Y T^T Y^T) V with one pass over Y for all
+// bb iterates, a Householder QR of the block's panel (one team barrier per column), T extended
+// by Eq. cwy1 with one triangular product over T for all columns, and the bb vectors
+// q = (Y T Y^T - I) e_col with one more pass over Y.  A sweep takes bb + 6 team barriers, where
+// one member at a time takes about 9 per member.  Included by tinv_kernels.cu inside its
+// namespace (it uses the cluster kernel's context and the helpers defined there).
+#pragma once
+
+// Row-major staged vectors in shared memory: x_c[idx] = p[idx * ld + c].
+struct XRow {
+    const double* p;
+    int ld;
+    __device__ __forceinline__ double operator()(int64_t idx, int c) const { return p[idx * ld + c]; }
+};
+// Column vectors in shared memory holding rows [off, off + ld): x_c[idx] = p[c * ld + idx - off].
+struct XCol {
+    const double* p;
+    int64_t ld, off;
+    __device__ __forceinline__ double operator()(int64_t idx, int c) const { return p[c * ld + idx - off]; }
+};
+// Column vectors in global memory written by other CTAs (read through L2): base + c * ld + idx.
+struct XGlob {
+    const double* base;
+    int64_t ld;
+    __device__ __forceinline__ double operator()(int64_t idx, int c) const { return __ldcg(base + c * ld + idx); }
+};
+
+// Multi-vector column products: out(i, c, sum_{r in R(i)} A[r + i lda] x_c[r]) for columns i in
+// [c0, c1) and vectors c < nv (nv <= NV), R(i) as cta_coldots (LOWER: [max(rlo, i), rhi),
+// UPPER: [rlo, min(rhi, i + 1))).  A warp takes 8 columns x 4 row phases; every load of A feeds
+// nv FMAs.  Rows are split into segments when the columns alone do not fill the warps; the
+// segment partials are added by a fixed-shape tree, so results do not depend on scheduling.
+template <int KIND, int NV, class XF, class Out>
+__device__ __noinline__ void mv_coldots(const double* __restrict__ A, int64_t lda, int64_t c0, int64_t c1,
+                                        int64_t rlo, int64_t rhi, XF xf, int nv, double* red, Out out)
+{
+    const int nW = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cl = lane >> 2, ph = lane & 3;
+    const int64_t nc = c1 - c0;
+    if (nc <= 0 || nv <= 0) return;
+    if (KIND == kLower)
+        rlo = max(rlo, c0);
+    else
+        rhi = min(rhi, c1);
+    const int64_t groups = (nc + 7) / 8;
+    const int64_t rows = rhi > rlo ? rhi - rlo : 0;
+    int lmax = 0;
+    while (lmax < 4 && ((int64_t)nc * nv << (lmax + 1)) <= 2048 && rows >= ((int64_t)32 << (lmax + 1))) ++lmax;
+    const int lS = pick_segments(groups, (rows + 3) / 4 * nv, nW, lmax);
+    const int S = 1 << lS;
+    const int64_t seglen = (rows + S - 1) >> lS;
+    const int64_t units = groups << lS;
+    for (int64_t u = wid; u < units; u += nW) {
+        const int64_t g = u >> lS;
+        const int sg = (int)(u & (S - 1));
+        const int64_t i = c0 + g * 8 + cl;
+        const bool act = i < c1;
+        const int64_t s_lo = rlo + sg * seglen, s_hi = min(rhi, s_lo + seglen);
+        int64_t a = 0, b = 0;
+        if (act) {
+            a = max(s_lo, (KIND == kLower) ? max(rlo, i) : rlo);
+            b = min(s_hi, (KIND == kLower) ? rhi : min(rhi, i + 1));
+        }
+        double acc[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) acc[c] = 0.0;
+        if (act && a < b) {
+            const double* col = A + i * lda;
+            int64_t r = a + ((ph - a) & 3);
+            for (; r + 4 < b; r += 8) {
+                const double y0 = col[r], y1 = col[r + 4];
+#pragma unroll
+                for (int c = 0; c < NV; ++c)
+                    if (c < nv) acc[c] = fma(y1, xf(r + 4, c), fma(y0, xf(r, c), acc[c]));
+            }
+            if (r < b) {
+                const double y0 = col[r];
+#pragma unroll
+                for (int c = 0; c < NV; ++c)
+                    if (c < nv) acc[c] = fma(y0, xf(r, c), acc[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NV; ++c) {
+            acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
+            acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 2);
+        }
+        if (act && ph == 0) {
+#pragma unroll
+            for (int c = 0; c < NV; ++c) {
+                if (c >= nv) break;
+                if (S == 1)
+                    out(i, c, acc[c]);
+                else
+                    red[((int64_t)sg * nc + (i - c0)) * nv + c] = acc[c];
+            }
+        }
+    }
+    if (S > 1) {
+        tree_segments(red, S, nc, nv);
+        for (int64_t q = threadIdx.x; q < nc * nv; q += blockDim.x) out(c0 + q / nv, (int)(q % nv), red[q]);
+    }
+    __syncthreads();
+}
+
+// Multi-vector row products: out(rho, c, sum_{i in C(rho)} A[rho + i lda] x_c[i]) for rows rho in
+// [r0, r1) and vectors c < nv, C(rho) as cta_rowdots (LOWERCOL: [0, min(ccap, rho + 1)),
+// UPPERCOL: [rho, ccap), ALL: [0, ccap)).  A warp takes RL consecutive rows x 32/RL column
+// phases; column ranges are split into segments when the rows alone do not fill the warps.
+template <int RL, int KIND, int NV, class XF, class Out>
+__device__ __noinline__ void mv_rowdots_rl(const double* __restrict__ A, int64_t lda, int64_t r0, int64_t r1,
+                                           int64_t ccap, XF xf, int nv, double* red, Out out)
+{
+    constexpr int CL = 32 / RL;
+    const int nW = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rr = lane % RL, ph = lane / RL;
+    const int64_t nr = r1 - r0;
+    const int64_t rgroups = (nr + RL - 1) / RL;
+    const int64_t gb = (KIND == kUpperCol) ? r0 : 0;
+    const int64_t ge = (KIND == kLowerCol) ? min(ccap, r1) : ccap;
+    const int64_t glen = ge > gb ? ge - gb : 0;
+    int lmax = 0;
+    while (lmax < 5 && ((int64_t)nr * nv << (lmax + 1)) <= 2048 && glen >= ((int64_t)8 * CL << (lmax + 1))) ++lmax;
+    const int lS = pick_segments(rgroups, (glen + CL - 1) / CL * nv, nW, lmax);
+    const int S = 1 << lS;
+    const int64_t seglen = (glen + S - 1) >> lS;
+    const int64_t units = rgroups << lS;
+    for (int64_t u = wid; u < units; u += nW) {
+        const int64_t g = u >> lS;
+        const int sg = (int)(u & (S - 1));
+        const int64_t rho = r0 + g * RL + rr;
+        const bool act = rho < r1;
+        int64_t a = 0, b = 0;
+        if (act) {
+            const int64_t s0 = gb + sg * seglen, s1 = min(ge, s0 + seglen);
+            const int64_t cb = (KIND == kUpperCol) ? rho : 0;
+            const int64_t ce = (KIND == kLowerCol) ? min(ccap, rho + 1) : ccap;
+            a = max(s0, cb);
+            b = min(s1, ce);
+        }
+        double acc[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) acc[c] = 0.0;
+        if (act && a < b) {
+            const double* row = A + rho;
+            int64_t i = a + (((int64_t)ph - a) % CL + CL) % CL;
+            for (; i + CL < b; i += 2 * CL) {
+                const double y0 = row[i * lda], y1 = row[(i + CL) * lda];
+#pragma unroll
+                for (int c = 0; c < NV; ++c)
+                    if (c < nv) acc[c] = fma(y1, xf(i + CL, c), fma(y0, xf(i, c), acc[c]));
+            }
+            if (i < b) {
+                const double y0 = row[i * lda];
+#pragma unroll
+                for (int c = 0; c < NV; ++c)
+                    if (c < nv) acc[c] = fma(y0, xf(i, c), acc[c]);
+            }
+        }
+#pragma unroll
+        for (int o = RL; o < 32; o <<= 1) {
+#pragma unroll
+            for (int c = 0; c < NV; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+        }
+        if (act && ph == 0) {
+#pragma unroll
+            for (int c = 0; c < NV; ++c) {
+                if (c >= nv) break;
+                if (S == 1)
+                    out(rho, c, acc[c]);
+                else
+                    red[((int64_t)sg * nr + (rho - r0)) * nv + c] = acc[c];
+            }
+        }
+    }
+    if (S > 1) {
+        tree_segments(red, S, nr, nv);
+        for (int64_t q = threadIdx.x; q < nr * nv; q += blockDim.x) out(r0 + q / nv, (int)(q % nv), red[q]);
+    }
+    __syncthreads();
+}
+
+template <int KIND, int NV, class XF, class Out>
+__device__ __forceinline__ void mv_rowdots_nv(const double* __restrict__ A, int64_t lda, int64_t r0, int64_t r1,
+                                              int64_t ccap, XF xf, int nv, double* red, Out out)
+{
+    if (r1 - r0 > 64)
+        mv_rowdots_rl<32, KIND, NV>(A, lda, r0, r1, ccap, xf, nv, red, out);
+    else
+        mv_rowdots_rl<8, KIND, NV>(A, lda, r0, r1, ccap, xf, nv, red, out);
+}
+
+// The products with the accumulator count fitted to nv (<= NVMAX): predicated-off FP64
+// instructions would still take the FP64 pipe's issue slots.
+template <int KIND, int NVMAX, class XF, class Out>
+__device__ __forceinline__ void mv_rowdots(const double* __restrict__ A, int64_t lda, int64_t r0, int64_t r1,
+                                           int64_t ccap, XF xf, int nv, double* red, Out out)
+{
+    if (r1 <= r0 || nv <= 0) return;
+    if (nv <= NVMAX / 4)
+        mv_rowdots_nv<KIND, NVMAX / 4>(A, lda, r0, r1, ccap, xf, nv, red, out);
+    else if (nv <= NVMAX / 2)
+        mv_rowdots_nv<KIND, NVMAX / 2>(A, lda, r0, r1, ccap, xf, nv, red, out);
+    else
+        mv_rowdots_nv<KIND, NVMAX>(A, lda, r0, r1, ccap, xf, nv, red, out);
+}
+
+template <int KIND, int NVMAX, class XF, class Out>
+__device__ __forceinline__ void mv_coldots_fit(const double* __restrict__ A, int64_t lda, int64_t c0, int64_t c1,
+                                               int64_t rlo, int64_t rhi, XF xf, int nv, double* red, Out out)
+{
+    if (nv <= NVMAX / 4)
+        mv_coldots<KIND, NVMAX / 4>(A, lda, c0, c1, rlo, rhi, xf, nv, red, out);
+    else if (nv <= NVMAX / 2)
+        mv_coldots<KIND, NVMAX / 2>(A, lda, c0, c1, rlo, rhi, xf, nv, red, out);
+    else
+        mv_coldots<KIND, NVMAX>(A, lda, c0, c1, rlo, rhi, xf, nv, red, out);
+}
+
+// Sum over the team's ranks, in rank order, of the partial `idx` of each rank's block
+// (ranks `stride` doubles apart); lane-strided, then a fixed xor tree.  Whole warp; every lane
+// receives the result.
+__device__ __forceinline__ double team_sum_at(const double* base, size_t stride, int G, size_t idx)
+{
+    const int lane = threadIdx.x & 31;
+    double a = 0.0;
+    for (int r = lane; r < G; r += 32) a += __ldcg(base + (size_t)r * stride + idx);
+    return warp_sum(a);
+}
+
+// Members per block the blocked path uses for a cluster of mc members on a team of G CTAs
+// (1: the cluster takes the one-member path).
+__device__ __forceinline__ int block_members(const Ws& w, int64_t mc, int G)
+{
+    if (w.block < 2 || G < 2 || mc < 3 || !w.vblk) return 1;
+    // up to 2 members per CTA (each CTA solves its members one after the other); the panel
+    // buffer holds bb (n/G + 1) <= 2 n + 64 doubles
+    int nb = min(w.block, 2 * G);
+    // staged vectors in shared memory: 2 NB (mc) doubles for the T products, NB (mc + NB) for
+    // pass C (NB = kBlockMax, the staging stride)
+    if ((int64_t)2 * kBlockMax * mc > w.xcap || (int64_t)kBlockMax * (mc + kBlockMax) > w.xcap) return 1;
+    return nb;
+}
+
+// ---- one cluster by the blocked compact-WY path (Sec. 3.2; Alg. 4's sweeps per block) -----
+__device__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int nb)
+{
+    const Problem& p = cx.p;
+    const Ws& w = cx.w;
+    const int t = threadIdx.x, B = blockDim.x, wid = t >> 5, lane = t & 31, nW = B >> 5;
+    const int G = tm.G, rank = tm.rank, leader = tm.leader;
+    constexpr int NB = kBlockMax;
+    const int64_t s0 = w.clstart[c];
+    const int64_t mc = w.clsize[c];
+    const JRef jr = jref(w, s0);
+    const Seg& sg = *jr.g;
+    const int64_t n = sg.n;
+    double* Zc = p.Z + sg.z + jr.jl * sg.ldz;
+    const int64_t ldz = sg.ldz;
+    double* Tc = w.T + w.cltoff[c];
+    const int64_t ldt = mc;
+    double* Yc = w.Y + jr.off;
+    const size_t ns = (size_t)p.n;
+    const bool orth = (cx.mode == kModeOrth);
+    const double onenrm = sg.onenrm, dtpcrt = sg.dtpcrt;
+    const size_t pstride = 3 * (size_t)NB * ns;   // doubles of one CTA's partial block
+    double* vb = w.vblk + (size_t)leader * NB * ns;  // member c's iterate at + c ns (all rows)
+    double* qb = w.qblk + (size_t)leader * NB * ns;  // member c's q at + c ns (all rows)
+    double* teamP = w.pblk + (size_t)leader * pstride;
+    double* myP = teamP + (size_t)rank * pstride;
+    double* pA = myP;                          // pass A partials [i NB + c]
+    double* pG = myP + (size_t)NB * ns;        // Gram partials [i NB + c], rows k0.. hold Y_b^T Y_b
+    double* pQ = myP + 2 * (size_t)NB * ns;    // panel and statistics partials (small)
+    double* tb = w.tblk + (size_t)leader * pstride;
+    double* sP = tb;                           // S' = T^T Y^T V  [i NB + c]
+    double* tP = tb + (size_t)NB * ns;         // T_k (Y_k^T Y_b)  [i NB + c]
+    double* xT = tb + 2 * (size_t)NB * ns;     // X_T, then T_k R1 before it  [i NB + c]
+    double* ybr = tb + 3 * (size_t)NB * ns;    // rows k0.. of Y_b  [r NB + c] (rank 1's slot; G >= 2)
+    double* W = cx.vsm;                        // this CTA's panel rows, column c at + c Rb
+    double* xs = cx.xs;
+    double* red = cx.red;
+    double* scal_t = w.partScal + (size_t)leader * kScalTeam;
+    __shared__ double s_cv[NB], s_tv[NB], s_yh[NB], s_fac[NB], s_coef[NB];
+    __shared__ double s_g22[NB * NB], s_t22[NB * NB], s_yb[NB * NB], s_stat[2 * NB];
+    __shared__ int s_broke[NB], s_chk[NB];
+    __shared__ int64_t s_rows[8];
+    __shared__ double s_b[4];
+
+    if (!TINV_IN(s0 >= 0 && mc >= 1 && s0 + mc <= w.nM && n <= p.n && rank < G && leader + G <= w.P &&
+                     dbg_range((int64_t)jr.off, (int64_t)jr.off + mc * n, w.nF) &&
+                     dbg_range(w.cltoff[c], w.cltoff[c] + mc * mc, w.nTT) &&
+                     nb >= 2 && nb <= NB && nb <= 2 * G && (int64_t)2 * NB * mc <= w.xcap &&
+                     (p.zlen == 0 || dbg_range(sg.z + jr.jl * ldz, sg.z + (jr.jl + mc - 1) * ldz + n, p.zlen)),
+                 cx.err))
+        return false;
+
+    const int64_t ra0 = part_lo(0, n, rank, G), ra1 = part_lo(0, n, rank + 1, G);
+    int64_t kstart = 0;
+    if (!orth) {
+        // Alg. 4: Y_1 = [y_1], T_1 = [t_1] from the final head vector z
+        const double* z = Zc;
+        double ss = 0.0;
+        for (int64_t r = ra0 + t; r < ra1; r += B) ss = fma(z[r], z[r], ss);
+        ss = block_sum(ss, red);
+        if (t == 0) scal_t[rank * kScalTeam + 6] = ss;
+        if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
+        if (t < 32) {
+            const double tot = team_sum_slot(scal_t, G, 6);
+            const double nrm = sqrt(tot);
+            const double z0 = z[0];
+            const bool broke = !(nrm > 0.0) || !isfinite(nrm);
+            const double cc = broke ? -1.0 : -sgn(z0) * nrm;
+            const double u11 = broke ? 1.0 : z0;
+            if (t == 0) {
+                s_b[0] = cc;
+                s_b[1] = 1.0 / (cc * cc - u11 * cc);
+                s_b[2] = broke ? 1.0 : 0.0;
+            }
+        }
+        __syncthreads();
+        const double cc = s_b[0];
+        const bool broke = s_b[2] != 0.0;
+        for (int64_t r = ra0 + t; r < ra1; r += B) {
+            double y = broke ? 0.0 : z[r];
+            if (r == 0) y = broke ? 2.0 : z[0] - cc;
+            Yc[r] = y;
+        }
+        if (rank == 0 && t == 0) Tc[0] = s_b[1];
+        kstart = 1;
+        if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
+    }
+
+    // blocks: stand-alone orthogonalization takes V's columns in order, nb at a time; inverse
+    // iteration takes the members 1 + b + nblk c of block b
+    const int64_t nblk = orth ? (mc + nb - 1) / nb : (mc - 1 + nb - 1) / nb;
+    int64_t kpos = kstart;
+    for (int64_t bi = 0; bi < nblk; ++bi) {
+        const int64_t k0 = kpos;  // Y and T columns k0 .. k0 + bb - 1
+        const int bb = (int)(orth ? min((int64_t)nb, mc - k0) : (mc - 1 - bi + nblk - 1) / nblk);
+        kpos += bb;
+        const int64_t kb = k0 + bb;
+        const int64_t mem0 = orth ? k0 : 1 + bi;           // member of the block's column cc:
+        const int64_t mstride = orth ? 1 : nblk;           //   mem0 + mstride cc
+        if (t == 0) {
+            s_rows[0] = part_lo(k0, n, rank, G);       // panel rows
+            s_rows[1] = part_lo(k0, n, rank + 1, G);
+            s_rows[2] = trap_row_lo(n, kb, rank, G);   // rows of passes A and C
+            s_rows[3] = trap_row_lo(n, kb, rank + 1, G);
+            s_rows[4] = tri_col_lo(k0, rank, G);       // columns of T^T s
+            s_rows[5] = tri_col_lo(k0, rank + 1, G);
+            s_rows[6] = tri_row_lo(k0, rank, G);       // rows of the T products
+            s_rows[7] = tri_row_lo(k0, rank + 1, G);
+        }
+        if (t < NB) s_chk[t] = 0;
+        __syncthreads();
+        const int64_t rb0 = s_rows[0], rb1 = s_rows[1], Rb = rb1 - rb0;
+        const int64_t rc0 = s_rows[2], rc1 = s_rows[3];
+        const int64_t c0 = s_rows[4], c1 = s_rows[5], i0 = s_rows[6], i1 = s_rows[7];
+        if (!TINV_IN(dbg_range(rb0, rb1, n) && rb0 >= k0 && dbg_range(rc0, rc1, n) && dbg_range(c0, c1, k0) &&
+                         dbg_range(i0, i1, k0) && (int64_t)bb * Rb <= 2 * n + 64 && kb <= mc,
+                     cx.err))
+            return false;
+        const int maxits = orth ? 1 : kMaxIts;
+        int its = 0;
+        while (its < maxits) {
+            ++its;
+            // ---- (S) the block's iterates: CTA-local solves, member cc on rank cc mod G ----
+            XGlob vsrc{orth ? cx.V + k0 * cx.ldv : (its == 1 ? Zc + mem0 * ldz : vb),
+                       orth ? cx.ldv : (its == 1 ? mstride * ldz : (int64_t)ns)};
+            PROF_MARK(cx.prof, kPhEnd);
+            if (!orth && its > 1) {
+                for (int cc = rank; cc < bb; cc += G) {
+                    const int64_t kk = mem0 + mstride * cc;
+                    const Fac f = fac_at(w, jr.off + (size_t)kk * (size_t)n);
+                    const bool may_end = s_chk[cc] >= kExtra || its == maxits;
+                    uint32_t tgt = 0;
+                    TeamRef tr{nullptr, &tgt, 1, 0, cx.err, nullptr, 0ull,
+                               (unsigned long long*)&w.ctr[kCtrFallback],
+                               may_end ? kSolveTol : kSolveTolLoose, 0u};
+                    if (!team_solve(n, f, qb + cc * ns, s_fac[cc], cx.vsm, vb + cc * ns, pG, 0, n,
+                                    nullptr, nullptr, tr, red))
+                        return false;
+                }
+                PROF_MARK(cx.prof, kPhSolve);
+                if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
+                PROF_MARK(cx.prof, kPhLoad);
+            }
+            // ---- (A) partial S = Y_k^T V over this CTA's rows (V staged in shared memory when
+            //      its rows fit the panel buffer) ----
+            if (k0 > 0) {
+                const int64_t Ra = rc1 - rc0;
+                auto outA = [&](int64_t i, int cc, double v) { pA[i * NB + cc] = v; };
+                if ((int64_t)bb * Ra <= 2 * n) {
+                    for (int64_t q = t; q < (int64_t)bb * Ra; q += B) {
+                        const int cc = (int)(q / Ra);
+                        W[q] = vsrc(rc0 + q % Ra, cc);
+                    }
+                    __syncthreads();
+                    mv_coldots_fit<kLower, NB>(Yc, n, 0, k0, rc0, rc1, XCol{W, Ra, rc0}, bb, red, outA);
+                } else {
+                    mv_coldots_fit<kLower, NB>(Yc, n, 0, k0, rc0, rc1, vsrc, bb, red, outA);
+                }
+            }
+            PROF_MARK(cx.prof, kPhA);
+            if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
+            PROF_MARK(cx.prof, kPhB1);
+            // ---- (T1) S' = T_k^T S for the columns [c0, c1) of this CTA ----
+            if (k0 > 0) {
+                for (int64_t q = t; q < c1 * bb; q += B) {
+                    const int64_t l = q / bb;
+                    const int cc = (int)(q % bb);
+                    xs[l * NB + cc] = sum_partials(teamP + l * NB + cc, pstride, G);
+                }
+                __syncthreads();
+                mv_coldots_fit<kUpper, NB>(Tc, ldt, c0, c1, 0, k0, XRow{xs, NB}, bb, red,
+                                       [&](int64_t i, int cc, double v) { sP[i * NB + cc] = v; });
+            }
+            PROF_MARK(cx.prof, kPhT1);
+            if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
+            PROF_MARK(cx.prof, kPhB2);
+            // ---- (B) panel rows of W = V - Y_k S' (this CTA's rows [rb0, rb1) of [k0, n)) ----
+            if (k0 > 0)
+                for (int64_t q = t; q < k0 * bb; q += B) {
+                    const int64_t l = q / bb;
+                    const int cc = (int)(q % bb);
+                    xs[l * NB + cc] = __ldcg(&sP[l * NB + cc]);
+                }
+            for (int64_t q = t; q < (int64_t)bb * Rb; q += B) {
+                const int cc = (int)(q / Rb);
+                const int64_t r = rb0 + q % Rb;
+                W[cc * Rb + (r - rb0)] = vsrc(r, cc);
+            }
+            __syncthreads();
+            if (k0 > 0)
+                mv_rowdots<kAllCols, NB>(Yc, n, rb0, rb1, k0, XRow{xs, NB}, bb, red,
+                                         [&](int64_t r, int cc, double v) { W[cc * Rb + (r - rb0)] -= v; });
+            PROF_MARK(cx.prof, kPhBb);
+            // ---- (QR) Householder QR of the panel, one column (and team barrier) at a time ----
+            for (int cc = 0; cc < bb; ++cc) {
+                const int64_t col = k0 + cc;
+                double* slot = pQ + (cc & 1) * 32;
+                const int64_t lo = max(rb0, col);
+                const double* wc = W + cc * Rb;
+                // warp v: v = 0 the norm^2 of column cc, v > 0 its dot with column cc + v
+                for (int v = wid; v < bb - cc; v += nW) {
+                    const double* wv = W + (cc + v) * Rb;
+                    double a = 0.0;
+                    for (int64_t r = lo + lane; r < rb1; r += 32) a = fma(wc[r - rb0], wv[r - rb0], a);
+                    a = warp_sum(a);
+                    if (lane == 0) slot[v] = a;
+                }
+                // the head row's entries of columns cc.. (zero unless this CTA owns row col)
+                if (t < bb - cc) slot[16 + t] = (col >= rb0 && col < rb1) ? W[(cc + t) * Rb + (col - rb0)] : 0.0;
+                PROF_MARK(cx.prof, kPhB);
+                if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
+                PROF_MARK(cx.prof, kPhB3);
+                // every CTA reduces the team's partials in rank order: identical decisions
+                const size_t soff = 2 * (size_t)NB * ns + (cc & 1) * 32;
+                for (int v = wid; v < 2 * (bb - cc); v += nW) {
+                    const size_t idx = soff + (v < bb - cc ? v : 16 + (v - (bb - cc)));
+                    const double s = team_sum_at(teamP, pstride, G, idx);
+                    if (lane == 0) red[v] = s;
+                }
+                __syncthreads();
+                if (t == 0) {
+                    const double nrm = sqrt(red[0]);
+                    const bool broke = !(nrm > 0.0) || !isfinite(nrm);
+                    const double u1 = red[bb - cc];
+                    const double cv = broke ? -1.0 : -sgn(u1) * nrm;
+                    const double ue = broke ? 1.0 : u1;
+                    const double tv = 1.0 / (cv * cv - ue * cv);
+                    s_cv[cc] = cv;
+                    s_tv[cc] = tv;
+                    s_yh[cc] = ue - cv;
+                    s_broke[cc] = broke ? 1 : 0;
+                    // y^T w_{cc+v} = (w_cc - c e_col)^T w_{cc+v}, or 2 w_{cc+v}[col] after a breakdown
+                    for (int v = 1; v < bb - cc; ++v) {
+                        const double hv = red[bb - cc + v];
+                        s_coef[cc + v] = tv * (broke ? 2.0 * hv : red[v] - cv * hv);
+                    }
+                }
+                __syncthreads();
+                const bool broke = s_broke[cc] != 0;
+                const double yh = s_yh[cc];
+                // apply H_cc to the later columns of this CTA's rows, then make column cc the
+                // reflector y (zero above row col) and store it as column col of Y
+                for (int64_t q = t; q < Rb; q += B) {
+                    const int64_t r = rb0 + q;
+                    double yr = 0.0;
+                    if (r >= col) yr = (r == col) ? yh : (broke ? 0.0 : W[cc * Rb + q]);
+                    if (yr != 0.0)
+                        for (int v = cc + 1; v < bb; ++v) W[v * Rb + q] = fma(-s_coef[v], yr, W[v * Rb + q]);
+                    W[cc * Rb + q] = yr;
+                    if (r >= col) Yc[r + col * n] = yr;
+                }
+                __syncthreads();
+                PROF_MARK(cx.prof, kPhT2a);
+            }
+            // ---- (Gram) Y_k^T Y_b and Y_b^T Y_b over this CTA's panel rows; Y_b's rows k0.. ----
+            if (k0 > 0)
+                mv_coldots_fit<kLower, NB>(Yc, n, 0, k0, rb0, rb1, XCol{W, Rb, rb0}, bb, red,
+                                       [&](int64_t i, int cc, double v) { pG[i * NB + cc] = v; });
+            for (int v = wid; v < bb * bb; v += nW) {
+                const int ca = v / bb, cb = v % bb;
+                if (ca > cb) continue;  // upper triangle only
+                double a = 0.0;
+                for (int64_t q = lane; q < Rb; q += 32) a = fma(W[ca * Rb + q], W[cb * Rb + q], a);
+                a = warp_sum(a);
+                if (lane == 0) pG[(k0 + ca) * NB + cb] = a;
+            }
+            for (int64_t q = t; q < (int64_t)bb * bb; q += B) {
+                const int64_t r = k0 + q / bb;
+                const int cc = (int)(q % bb);
+                if (r >= rb0 && r < rb1) ybr[(r - k0) * NB + cc] = W[cc * Rb + (r - rb0)];
+            }
+            PROF_MARK(cx.prof, kPhBc);
+            if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
+            PROF_MARK(cx.prof, kPhBa);
+            // ---- (T2) T columns k0.. by Eq. cwy1 and X_T = T (rows col of Y) for pass C ----
+            for (int v = wid; v < bb * bb; v += nW) {
+                const int ca = v / bb, cb = v % bb;
+                const double g = (ca <= cb) ? team_sum_at(teamP, pstride, G, NB * ns + (size_t)(k0 + ca) * NB + cb) : 0.0;
+                if (lane == 0) {
+                    s_g22[ca * NB + cb] = g;
+                    s_yb[ca * NB + cb] = __ldcg(&ybr[ca * NB + cb]);  // y_cb at row k0 + ca
+                }
+            }
+            // staged [G12 | R1] for the rows [i0, k0) of T_k (vector v < bb: G12[l, v] =
+            // (Y_k^T Y_b)[l, v]; v = bb + c: R1[l, c] = Y[k0 + c, l], row k0 + c of Y_k)
+            for (int64_t q = t; q < (k0 - i0) * bb; q += B) {
+                const int64_t l = i0 + q / bb;
+                const int cc = (int)(q % bb);
+                xs[(l - i0) * 2 * NB + cc] = sum_partials(teamP + NB * ns + l * NB + cc, pstride, G);
+                xs[(l - i0) * 2 * NB + bb + cc] = __ldcg(&Yc[(k0 + cc) + l * n]);
+            }
+            __syncthreads();
+            if (t == 0) {  // T_22 by the recurrence of Eq. cwy1 inside the block
+                for (int cb = 0; cb < bb; ++cb) {
+                    s_t22[cb * NB + cb] = s_tv[cb];
+                    for (int ca = cb - 1; ca >= 0; --ca) {
+                        double a = 0.0;
+                        for (int l = ca; l < cb; ++l) a = fma(s_t22[ca * NB + l], s_g22[l * NB + cb], a);
+                        s_t22[ca * NB + cb] = -s_tv[cb] * a;
+                    }
+                    for (int ca = cb + 1; ca < NB; ++ca) s_t22[ca * NB + cb] = 0.0;
+                }
+            }
+            // rows [i0, i1) of T_k times [G12 | R1]: into tP (first bb) and xT (last bb)
+            if (k0 > 0 && i1 > i0)
+                mv_rowdots<kUpperCol, 2 * NB>(Tc, ldt, i0, i1, k0, XRow{xs - i0 * 2 * NB, 2 * NB}, 2 * bb, red,
+                                              [&](int64_t i, int v, double a) {
+                                                  if (v < bb)
+                                                      tP[i * NB + v] = a;
+                                                  else
+                                                      xT[i * NB + (v - bb)] = a;
+                                              });
+            __syncthreads();
+            // per row i of T_k: T[i, k0 + c] = -t_c (P[i, c] + sum_{c2 < c} T[i, k0 + c2] G22[c2, c]),
+            // X_T[i, c] = (T_k R1)[i, c] + sum_{c2 <= c} T[i, k0 + c2] y_c2[k0 + c]
+            for (int64_t i = i0 + t; i < i1; i += B) {
+                double t12[NB], pr[NB];
+#pragma unroll
+                for (int cc = 0; cc < NB; ++cc) {
+                    t12[cc] = 0.0;
+                    pr[cc] = (cc < bb) ? xT[i * NB + cc] : 0.0;
+                }
+#pragma unroll
+                for (int cc = 0; cc < NB; ++cc) {
+                    if (cc >= bb) break;
+                    double a = tP[i * NB + cc];
+                    for (int c2 = 0; c2 < cc; ++c2) a = fma(t12[c2], s_g22[c2 * NB + cc], a);
+                    t12[cc] = -s_tv[cc] * a;
+                    Tc[i + (k0 + cc) * ldt] = t12[cc];
+                }
+#pragma unroll
+                for (int cc = 0; cc < NB; ++cc) {
+                    if (cc >= bb) break;
+                    double a = pr[cc];
+                    for (int c2 = 0; c2 <= cc; ++c2) a = fma(t12[c2], s_yb[cc * NB + c2], a);
+                    xT[i * NB + cc] = a;
+                }
+            }
+            if (rank == 0 && t < bb * bb) {
+                // the block's own rows: T_22 into T, X_T[k0 + ca, cb] = sum_{ca <= l <= cb} T_22[ca, l] y_l[k0 + cb]
+                const int ca = t / bb, cb = t % bb;
+                double a = 0.0;
+                if (ca <= cb)
+                    for (int l = ca; l <= cb; ++l) a = fma(s_t22[ca * NB + l], s_yb[cb * NB + l], a);
+                xT[(k0 + ca) * NB + cb] = a;
+                if (ca <= cb) Tc[(k0 + ca) + (k0 + cb) * ldt] = s_t22[ca * NB + cb];
+            }
+            PROF_MARK(cx.prof, kPhT2);
+            if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
+            PROF_MARK(cx.prof, kPhB4);
+            // ---- (C) q_c = (Y T Y^T - I) e_{k0+c} = Y_{kb} X_T[:, c] - e_{k0+c}, rows [rc0, rc1) ----
+            for (int64_t q = t; q < kb * bb; q += B) {
+                const int64_t l = q / bb;
+                const int cc = (int)(q % bb);
+                xs[l * NB + cc] = __ldcg(&xT[l * NB + cc]);
+            }
+            __syncthreads();
+            mv_rowdots<kLowerCol, NB>(Yc, n, rc0, rc1, kb, XRow{xs, NB}, bb, red,
+                                      [&](int64_t r, int cc, double a) {
+                                          qb[cc * ns + r] = (r == k0 + cc) ? a - 1.0 : a;
+                                      });
+            // statistics of this CTA's rows: sum |q_c| (next scaling) and max |q_c| (the test)
+            for (int cc = wid; cc < bb; cc += nW) {
+                double as = 0.0;
+                unsigned long long mb = 0;
+                for (int64_t r = rc0 + lane; r < rc1; r += 32) {
+                    const double x = qb[cc * ns + r];
+                    as += fabs(x);
+                    mb = max(mb, (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull);
+                }
+                as = warp_sum(as);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+                if (lane == 0) {
+                    pQ[64 + cc] = as;
+                    pQ[64 + NB + cc] = __longlong_as_double((long long)mb);
+                }
+            }
+            PROF_MARK(cx.prof, kPhC);
+            if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
+            PROF_MARK(cx.prof, kPhB5);
+            if (orth) {
+                for (int cc = 0; cc < bb; ++cc)
+                    for (int64_t r = ra0 + t; r < ra1; r += B) Zc[r + (k0 + cc) * ldz] = __ldcg(&qb[cc * ns + r]);
+                break;
+            }
+            for (int v = wid; v < 2 * bb; v += nW) {
+                const int cc = v % bb;
+                const size_t idx = 2 * (size_t)NB * ns + 64 + (v < bb ? cc : NB + cc);
+                double s;
+                if (v < bb) {
+                    s = team_sum_at(teamP, pstride, G, idx);
+                } else {
+                    unsigned long long mb = 0;
+                    for (int r = lane; r < G; r += 32)
+                        mb = max(mb, (unsigned long long)__double_as_longlong(__ldcg(teamP + (size_t)r * pstride + idx)));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+                    s = __longlong_as_double((long long)mb);
+                }
+                if (lane == 0) s_stat[v < bb ? cc : NB + cc] = s;
+            }
+            __syncthreads();
+            // convergence test on x_c = -c_c q_c (||x||_inf = |c_c| max|q_c|), per member
+            if (t == 0) {
+                int all = 1;
+                for (int cc = 0; cc < bb; ++cc) {
+                    if (!s_broke[cc] && fabs(s_cv[cc]) * s_stat[NB + cc] >= dtpcrt) ++s_chk[cc];
+                    if (s_chk[cc] < kExtra + 1) all = 0;
+                    const int64_t j = s0 + mem0 + mstride * cc;
+                    s_fac[cc] = -sgn(s_cv[cc]) * (((double)n * onenrm) * fmax(kEps, w.u0n[j])) / s_stat[cc];
+                }
+                s_b[3] = all ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            if (s_b[3] != 0.0 || its == maxits) {
+                // Alg. 4's normalization and sign are applied by k_finalize
+                for (int cc = 0; cc < bb; ++cc)
+                    for (int64_t r = ra0 + t; r < ra1; r += B)
+                        Zc[r + (mem0 + mstride * cc) * ldz] = __ldcg(&qb[cc * ns + r]);
+                if (rank == 0 && t < bb) {
+                    const int64_t j = s0 + mem0 + mstride * t;
+                    const bool conv = s_chk[t] >= kExtra + 1;
+                    if (p.iters) p.iters[j] = conv ? its : -its;
+                    if (!conv) count_nonconverged(w, j);
+                }
+                break;
+            }
+        }
+        // Y's block columns and T are complete (last barrier); Z rows are written per CTA
+        __syncthreads();
+    }
+    return true;
+}

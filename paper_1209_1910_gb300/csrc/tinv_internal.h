@@ -18,6 +18,8 @@ constexpr int kScalTeam = 16;       // doubles of per-CTA scalar partials
 // scratch, 128 doubles of warp maps, 6 per rank of the maps published by the team and 6 x 128 of
 // chunk maps: (2048 - 128 - 768) / 6 = 192 ranks.
 constexpr int kTeamMax = 192;
+// Largest block of the blocked compact-WY path (tinv_opts.block).
+constexpr int kBlockMax = 8;
 
 // Device error word bits.
 constexpr int kErrTimeout = 1;   // a bounded spin wait expired
@@ -52,8 +54,11 @@ struct Dims {
     int64_t TT;     // elements reserved for T: sum over problems of m^2
     int64_t nseg;   // problems
     int32_t P;      // persistent grid size
+    int32_t block;  // block size of the blocked compact-WY path (<= 1: none)
 };
-Dims single_dims(int64_t n, int64_t m, int32_t P);
+Dims single_dims(int64_t n, int64_t m, int32_t P, int32_t block = 0);
+// tinv_opts.block as the layout uses it: 0 for MGS or b <= 1, else min(b, kBlockMax).
+int32_t opts_block(const tinv_opts& o);
 
 // Byte offsets of every device array inside one workspace allocation.
 struct Layout {
@@ -61,6 +66,7 @@ struct Layout {
     size_t scal, wp, head, clstart, clsize, cltoff, sched, queue, ctr, bar;
     size_t fl, fu1, fu2, fr, fpiv, u0n, tolv, rhs;
     size_t Y, T, partS, partG, partScal, vecS, vecX, vecR, qbuf, vbuf, tpub, gvec;
+    size_t vblk, qblk, pblk, tblk;
     size_t total;
 };
 
@@ -135,6 +141,13 @@ struct Ws {
     int64_t nTT;      // T
     int64_t nM;       // per-eigenvalue arrays
     int64_t nPN;      // per-CTA vectors and partials: P x nmax
+    // blocked compact WY (block >= 2): per team slot (leader) kBlockMax vectors of nmax
+    double* vblk;     // [P*kBlockMax*nmax] the block's iterates (solve outputs)
+    double* qblk;     // [P*kBlockMax*nmax] the block's q vectors (next right-hand sides)
+    double* pblk;     // [P*3*kBlockMax*nmax] per-CTA partial sums
+    double* tblk;     // [P*3*kBlockMax*nmax] team vectors (G slots of a team)
+    int32_t block;    // largest block (0: blocked path off)
+    int32_t xcap;     // doubles of the block path's shared staging area
 };
 
 // Device bounds checks (TINV_DEBUG builds): a failed check sets kErrBounds in the error word
@@ -176,8 +189,10 @@ cudaError_t launch_finish_info(const Problem& p, const Ws& w, int64_t* info_out,
 // threads per CTA it runs with.
 int32_t chain_grid(int32_t cap, int64_t n);
 int32_t chain_threads(int64_t n);
-size_t chain_smem_bytes(int64_t n, bool use_smem);
+size_t chain_smem_bytes(int64_t n, bool use_smem, int32_t xcap = 0);
 bool chain_use_smem(int64_t n);
+// Shared staging capacity (doubles) of the blocked path for order n (0: blocking off).
+int32_t block_xcap(int64_t n);
 
 // Batched path on device arrays (tinv_api.cu): the device-pointer form of tinv_batch, with an
 // optional per-problem seed array (host; null = o.seed for every problem).  Enqueues on

@@ -773,6 +773,7 @@ struct ChainCtx {
     double* vsm;   // [n] working vector (shared or global)
     double* s1;    // [n] staging vector (shared or global)
     double* red;   // [2048] reduction / solve scratch (shared)
+    double* xs;    // staging area of the blocked path (shared, Ws.xcap doubles) or null
     int* err;
     unsigned long long nsolve;  // solves so far (the team's stamps: equal in all its CTAs)
     Prof prof;
@@ -1214,6 +1215,8 @@ __device__ bool cwy_cluster(ChainCtx& cx, int32_t c, Team& tm)
     return true;
 }
 
+#include "tinv_block.cuh"
+
 // ---- MGS processing of one cluster by one CTA (Alg. 1) -----------------------------------
 __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
 {
@@ -1343,6 +1346,8 @@ __device__ bool mgs_cluster(ChainCtx& cx, int32_t c)
     return true;
 }
 
+// METHOD 0: compact WY, one member at a time; 1: MGS; 2: compact WY with blocks of members on
+// CTA teams (tinv_opts.block), one member at a time elsewhere.
 template <int METHOD, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t mode,
                                                            const double* V, int64_t ldv)
@@ -1357,9 +1362,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t
     cx.V = V;
     cx.ldv = ldv;
     cx.red = smem;  // 2048 doubles
+    cx.xs = nullptr;
     if (w.use_smem) {
         cx.vsm = smem + 2048;
         cx.s1 = smem + 2048 + n;
+        if (w.block >= 2 && w.xcap > 0) cx.xs = smem + 2048 + 2 * n + 64;  // 64: panel slack
     } else {
         cx.vsm = w.gvec + (size_t)b * 2 * (size_t)n;
         cx.s1 = cx.vsm + n;
@@ -1380,7 +1387,15 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t
         return;
     if (tc >= 0) {
         Team tm{tf, tg, tr, w.bar + tf, 0u};
-        const bool ok = (METHOD == 0) ? cwy_cluster(cx, tc, tm) : mgs_cluster(cx, tc);
+        bool ok;
+        if (METHOD == 2) {  // compact WY with blocks of members where the team's cluster allows
+            const int nbk = cx.xs ? block_members(w, w.clsize[tc], tg) : 1;
+            ok = (nbk >= 2) ? bcwy_cluster(cx, tc, tm, nbk) : cwy_cluster(cx, tc, tm);
+        } else if (METHOD == 0) {
+            ok = cwy_cluster(cx, tc, tm);
+        } else {
+            ok = mgs_cluster(cx, tc);
+        }
         if (!ok) return;
     }
     const int64_t nq = w.ctr[kCtrNQueue];
@@ -1396,7 +1411,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t
         if (c < 0) break;
         if (!TINV_IN(c < (int32_t)w.nM, cx.err)) return;
         Team tm{b, 1, 0, w.bar + b, 0u};
-        const bool ok = (METHOD == 0) ? cwy_cluster(cx, c, tm) : mgs_cluster(cx, c);
+        const bool ok = (METHOD != 1) ? cwy_cluster(cx, c, tm) : mgs_cluster(cx, c);
         if (!ok) return;
     }
 #ifdef TINV_PHASE_PROFILE
@@ -1429,9 +1444,17 @@ bool chain_use_smem(int64_t n)
     return (size_t)(2048 + 2 * n) * sizeof(double) + 4096 <= 220u * 1024u;
 }
 
-size_t chain_smem_bytes(int64_t n, bool use_smem)
+size_t chain_smem_bytes(int64_t n, bool use_smem, int32_t xcap)
 {
-    return (size_t)(2048 + (use_smem ? 2 * n : 0)) * sizeof(double);
+    return (size_t)(2048 + (use_smem ? 2 * n : 0) + (use_smem && xcap > 0 ? xcap + 64 : 0)) * sizeof(double);
+}
+
+int32_t block_xcap(int64_t n)
+{
+    if (!chain_use_smem(n)) return 0;
+    // 220 KB of dynamic shared memory, 4 KB of it left for the kernel's static arrays
+    const int64_t avail = (int64_t)(220 * 1024) / 8 - 2048 - 2 * n - 64 - 512;
+    return (int32_t)max((int64_t)0, min((int64_t)16384, avail));
 }
 
 int32_t chain_grid(int32_t cap, int64_t)
@@ -1532,11 +1555,11 @@ cudaError_t launch_solve_rhs(int64_t n, int64_t m, const Ws& w, double* X, int64
 cudaError_t launch_chain(const Problem& p, const Ws& w, int32_t mode, const double* V, int64_t ldv,
                          cudaStream_t st)
 {
-    const size_t smem = chain_smem_bytes(p.n, w.use_smem != 0);
+    const size_t smem = chain_smem_bytes(p.n, w.use_smem != 0, w.block >= 2 ? w.xcap : 0);
     const int nt = chain_threads(p.n);
     void* fn;
     if (p.method == 0)
-        fn = (void*)k_chain<0, 512>;
+        fn = (w.block >= 2 && w.xcap > 0) ? (void*)k_chain<2, 512> : (void*)k_chain<0, 512>;
     else
         fn = (void*)k_chain<1, 512>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

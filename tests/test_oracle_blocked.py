@@ -16,7 +16,7 @@ import scipy.linalg.lapack as lapack
 from helpers import EPS, clusters_from_heads, dense, orth_ratio, residual_ratio, sin_angle
 from paper_1209_1910_gb300 import inputs
 
-BLOCKS = [1, 2, 4, 8, 16]
+BLOCKS = [1, 2, 4, 8]  # the library's blocks hold at most 8 members
 
 
 def _graded(n, m, kappa, seed=0):
