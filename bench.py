@@ -39,6 +39,8 @@ WORKLOADS = {
     "glued2100": "glued Wilkinson 100 x W21+ (glue 1e-10), n=2100, all eigenvectors",
     "uniform1000": "uniform[-1,1] d,e (seed 1), n=1000, all eigenvectors",
     "toeplitz4200": "Toeplitz d=2 e=1, n=4200, all eigenvectors (one cluster)",
+    "toeplitz6000": "Toeplitz d=2 e=1, n=6000, all eigenvectors (one cluster; its compact-WY Y, "
+                    "144 MB, exceeds the 126 MB L2)",
     "uniform10000": "uniform[-1,1] d,e (seed 1), n=10000, all eigenvectors",
     "zero10000": "Toeplitz d=0 e=1, n=10000, all eigenvectors (one cluster)",
     "batch512": "512 problems, n log-uniform [64,4096] (seed 2), even U[-1,1] d,e, odd glued "
@@ -49,9 +51,11 @@ WORKLOADS["split4200"] = ("glued Wilkinson 200 x W21+ with exactly zero glue, n=
 WORKLOADS["bidiag2000"] = ("upper bidiagonal n=2000 (seed 1), a = +-U[1,2), b = U[-1/2,1/2): all "
                            "singular triplets by tinv_bdsvd (Golub-Kahan form of order 4000, 76 "
                            "clusters, the largest 583)")
-WORKLOADS["serve"] = ("Poisson request stream (seed 3), n log-uniform [128,4096], 70% U[-1,1] / 30% "
-                      "glued W21+; eigenvalues computed by the server; offered at 0.5x, 0.9x and "
-                      "1.3x the saturated rate")
+WORKLOADS["serve"] = ("Poisson request stream (seed 3), 256 requests per load level, n log-uniform "
+                      "[128,4096] (the configuration's upper end 16384 capped at 4096: a uniform "
+                      "n=16384 request is one cluster of ~n members, about a minute of GPU time), "
+                      "70% U[-1,1] / 30% glued W21+; eigenvalues computed by the server; offered at "
+                      "0.5x, 0.9x and 1.3x the saturated rate")
 # kernels one call enqueues: plan (2), LU (2), first sweep, cluster kernel, CWY finalize, status
 LAUNCHES = {"cwy": 8, "mgs": 7}
 # the drivers add: split marks, bisection, scatter (tinv_eig); Golub-Kahan form, bisection,
@@ -71,9 +75,14 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="glued4200")
     ap.add_argument("--method", choices=["cwy", "mgs"], default="cwy")
+    ap.add_argument("--block", type=int, default=8,
+                    help="compact WY: cluster members orthogonalized in blocks of up to this many "
+                         "(Sec. 3.2's block form; 0 = one member at a time, Alg. 4)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batch, serving and n=1000 child runs of the default workload")
     ap.add_argument("--phases", action="store_true",
                     help="phase timing of the cluster kernel (diagnostic build), no bench line")
     ap.add_argument("--phases-child", action="store_true", help=argparse.SUPPRESS)
@@ -397,14 +406,15 @@ def batch_arm(args):
     tz = torch.zeros(int((ns * ns).sum()), dtype=torch.float64, device=dev)
     info = torch.zeros(nprob, dtype=torch.int64, device=dev)
     iters = torch.zeros(M, dtype=torch.int32, device=dev)
-    ws = torch.empty(binding.batch_workspace_size(ns), dtype=torch.uint8, device=dev)
+    blk = args.block if args.method == "cwy" else 0
+    ws = torch.empty(binding.batch_workspace_size(ns, block=blk), dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     phase = np.zeros(4, dtype=np.float32)
 
     def step(with_phase):
         kw = {"phase_ms": phase.ctypes.data} if with_phase else {}
         binding.tinv_batch_device(ns, off_de, off_z, td, te, tw, tz, method=args.method,
-                                  info=info, workspace=ws, iters=iters, **kw)
+                                  info=info, workspace=ws, iters=iters, block=blk, **kw)
 
     for _ in range(args.warmup):
         step(False)
@@ -475,7 +485,7 @@ def batch_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS["batch512"], "method": args.method,
+        "config": {"workload": WORKLOADS["batch512"], "method": args.method, "block": blk,
                    "problems": nprob_all, "eigenvectors": M_all,
                    "parallelism": "problem shards (LPT)" if world > 1 else "single",
                    "inputs": "resident in HBM (eigenvalues by GPU bisection, untimed)",
@@ -503,7 +513,8 @@ def batch_arm(args):
         with torch.cuda.stream(gs):
             with torch.cuda.graph(graph, stream=gs):
                 binding.tinv_batch_device(ns, off_de, off_z, td, te, tw, tz, method=args.method,
-                                          info=info, workspace=ws, iters=iters, table_ready=1)
+                                          info=info, workspace=ws, iters=iters, table_ready=1,
+                                          block=blk)
         # replay() launches on the current stream: make it gs, the stream the events are on
         with torch.cuda.stream(gs):
             graph.replay()
@@ -534,7 +545,7 @@ def batch_arm(args):
             for q in range(nprob):
                 n, a0, z0 = int(ns[q]), int(off_de[q]), int(off_z[q])
                 binding.tinv_device(td[a0:a0 + n], te[a0:a0 + n - 1], tw[a0:a0 + n],
-                                    tz[z0:z0 + n * n], method=args.method)
+                                    tz[z0:z0 + n * n], method=args.method, block=blk)
         one_at_a_time()
         torch.cuda.synchronize()
         flush.zero_()
@@ -557,7 +568,7 @@ def batch_arm(args):
         hz = torch.empty(int((ns * ns).sum()), dtype=torch.float64).pin_memory()
         hinfo = np.zeros(nprob, dtype=np.int64)
         lib = binding.load()
-        o = binding._opts(args.method)
+        o = binding._opts(args.method, block=blk)
         P = ctypes.c_void_p
 
         def e2e_call():
@@ -610,7 +621,7 @@ def cpu_sample_batch(method, probs, stride=32):
                       "eigenvectors)" % (len(pick), stride, tot))
 
 
-def serve_requests(count=128, hi=4096, seed=3):
+def serve_requests(count=256, hi=4096, seed=3):
     """The serving workload: (d, e) per request and unit-rate exponential arrival gaps."""
     g = inputs.rng(seed)
     reqs = []
@@ -624,7 +635,7 @@ def serve_requests(count=128, hi=4096, seed=3):
     return reqs, g.exponential(1.0, count)
 
 
-def serve_arm(args, count=128, hi=4096):
+def serve_arm(args, count=256, hi=4096):
     """Request-queue server under Poisson load: saturated rate (all requests at once), then the
     same requests offered at 0.5x, 0.9x and 1.3x that rate; p50/p99 latency per level.  Against
     one-problem-at-a-time calls (tinv through the host API, one after another)."""
@@ -636,12 +647,13 @@ def serve_arm(args, count=128, hi=4096):
     build.build()
     binding.load()
     reqs, gaps = serve_requests(count, hi)
+    blk = args.block if args.method == "cwy" else 0
     M = sum(len(d) for d, _ in reqs)
     outs = [np.zeros((len(d), len(d)), order="F") for d, _ in reqs]
 
     def run_level(rate):
         """Submit every request at its arrival time (rate None: all at once); returns stats."""
-        with binding.Server(method=args.method) as srv:
+        with binding.Server(method=args.method, block=blk) as srv:
             t0 = time.perf_counter()
             tick = []
             at = 0.0
@@ -695,7 +707,8 @@ def serve_arm(args, count=128, hi=4096):
         "metric": "served_problems_per_s", "value": sat_rate, "unit": "problems/s", "n_gpus": 1,
         "steps": 1, "warmup": warm, "ms_per_step": 1e3 * sat["wall_s"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS["serve"], "method": args.method, "requests": count,
+        "config": {"workload": WORKLOADS["serve"], "method": args.method, "block": blk,
+                   "requests": count,
                    "eigenvectors": M, "parallelism": "single",
                    "inputs": "host arrays submitted through tinv_submit (copies, bisection and "
                              "inverse iteration inside the timed region)"},
@@ -714,7 +727,7 @@ def serve_arm(args, count=128, hi=4096):
         t0 = time.perf_counter()
         for (d, e), Z in zip(reqs, outs):
             w = binding.bisect(d, e)
-            binding.tinv(d, e, w, method=args.method, out=Z)
+            binding.tinv(d, e, w, method=args.method, out=Z, block=blk)
         el = time.perf_counter() - t0
         out["compare"] = {"one_at_a_time": {"value": count / el, "unit": "problems/s",
                                             "eigvecs_per_s": M / el}}
@@ -904,16 +917,19 @@ def ours_arm(args):
     Zt = torch.zeros((m, n), dtype=torch.float64, device=dev)  # row j = eigenvector j
     iters = torch.zeros(m, dtype=torch.int32, device=dev)
     info = torch.zeros(1, dtype=torch.int64, device=dev)
-    ws = torch.empty(binding.workspace_size(n, m), dtype=torch.uint8, device=dev)
+    blk = args.block if args.method == "cwy" else 0
+    ws = torch.empty(max(binding.workspace_size(n, m, block=blk), binding.workspace_size(n, m)),
+                     dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     head = binding.plan(d, e, w)[1]
     phase = np.zeros(4, dtype=np.float32)
     counters = torch.zeros(4, dtype=torch.int64, device=dev)
 
-    def step(method, with_phase):
+    def step(method, with_phase, block=None):
         kw = {"phase_ms": phase.ctypes.data} if with_phase else {}
+        b = blk if block is None else block
         binding.tinv_device(td, te, tw, Zt, method=method, workspace=ws, iters=iters, info=info,
-                            counters=counters.data_ptr(), **kw)
+                            counters=counters.data_ptr(), block=b if method == "cwy" else 0, **kw)
 
     for _ in range(args.warmup):
         step(args.method, False)
@@ -988,7 +1004,7 @@ def ours_arm(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "method": args.method,
+        "config": {"workload": WORKLOADS[args.workload], "method": args.method, "block": blk,
                    "parallelism": "replicas" if world > 1 else "single",
                    "inputs": "resident in HBM", "l2": "flushed by a 512 MiB write between steps"},
         "check": {"nonconverged": nonconv, "residual_ratio": res_ratio, "orth_ratio": orth_ratio,
@@ -1005,13 +1021,13 @@ def ours_arm(args):
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         hd, he, hw = pin(d), pin(e), pin(w)
         hz = torch.empty((m, n), dtype=torch.float64).pin_memory().numpy().T  # n x m, F-order
-        binding.tinv(hd, he, hw, method=args.method, out=hz)
+        binding.tinv(hd, he, hw, method=args.method, out=hz, block=blk)
         el = 0.0
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            binding.tinv(hd, he, hw, method=args.method, out=hz)
+            binding.tinv(hd, he, hw, method=args.method, out=hz, block=blk)
             el += time.perf_counter() - t0
         if dist:
             tt = torch.tensor([el], dtype=torch.float64, device=dev)
@@ -1035,8 +1051,31 @@ def ours_arm(args):
             b.record(st)
             b.synchronize()
             ms.append(a.elapsed_time(b))
+        ncl = int(counters[1].item())  # clusters with >= 2 members (MGS: one CTA each)
+        P = torch.cuda.get_device_properties(dev).multi_processor_count
         out["compare"] = {"mgs": {"value": m / (statistics.mean(ms) * 1e-3),
-                                  "ms_per_step": statistics.mean(ms)}}
+                                  "ms_per_step": statistics.mean(ms),
+                                  "ctas": "one CTA per cluster: %d clusters on %d of the %d CTAs "
+                                          "of the persistent grid (compact WY spreads each "
+                                          "cluster over a CTA team)" % (ncl, min(ncl, P), P)}}
+        # the other form of compact WY on the same workload: one member at a time (Alg. 4 as
+        # printed) when the line measures blocks, blocks of 8 otherwise
+        other = 0 if blk >= 2 else 8
+        step("cwy", False, block=other)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(2):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            step("cwy", False, block=other)
+            b.record(st)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        out["compare"]["cwy_one_member" if other == 0 else "cwy_block8"] = {
+            "value": m / (statistics.mean(ms) * 1e-3), "ms_per_step": statistics.mean(ms),
+            "block": other}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc = cpu_sample(args.workload, args.method, d, e, w)
@@ -1048,11 +1087,40 @@ def ours_arm(args):
         lap = lapack_dstein_sample(args.workload, d, e, w)
         if lap:
             out["context_lapack_dstein"] = lap
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "glued4200":
+        out["extras"] = extras()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def extras():
+    """The other workloads of the metric, each a child run of this script (after the main
+    measurement, outside its timed region): the 512-problem batch against one call per problem,
+    the served request stream against one host call per request, and uniform n = 1000.  Returns
+    a summary of each line, or the reason it is missing."""
+    runs = {"batch512": ["--workload", "batch512", "--steps", "2", "--warmup", "1", "--no-e2e"],
+            "serve": ["--workload", "serve", "--warmup", "1"],
+            "uniform1000": ["--workload", "uniform1000", "--steps", "5", "--warmup", "3",
+                            "--no-compare"]}
+    keep = ("metric", "value", "unit", "ms_per_step", "problems_per_s", "eigvecs_per_s", "compare",
+            "check", "roofline", "saturated", "levels", "graph_replay", "e2e", "clocks", "config")
+    res = {}
+    for name, extra in runs.items():
+        cmd = [sys.executable, os.path.abspath(__file__), "--no-cpu-baseline", "--no-extras"] + extra
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            line = [x for x in r.stdout.splitlines() if x.startswith("{")]
+            if r.returncode != 0 or not line:
+                res[name] = {"missing": "exit %d: %s" % (r.returncode, (r.stderr or r.stdout)[-300:])}
+                continue
+            full = json.loads(line[-1])
+            res[name] = {k: full[k] for k in keep if k in full}
+        except subprocess.TimeoutExpired:
+            res[name] = {"missing": "timed out after 600 s"}
+    return res
 
 
 # ------------------------------------------------------------------------------------------
@@ -1071,7 +1139,8 @@ def _phases_child(args):
     binding.load(path)
     d, e, w = inputs.workload(args.workload)
     ph = np.zeros(4, dtype=np.float32)
-    binding.tinv(d, e, w, method=args.method, phase_ms=ph.ctypes.data)
+    binding.tinv(d, e, w, method=args.method, phase_ms=ph.ctypes.data,
+                 block=args.block if args.method == "cwy" else 0)
     print("PHASES_MS plan=%.3f lu=%.3f first=%.3f chain=%.3f" % tuple(ph.tolist()), flush=True)
 
 
@@ -1105,7 +1174,8 @@ def summarize_phases(text: str):
 
 def phases_arm(args):
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--phases-child",
-                        "--workload", args.workload, "--method", args.method],
+                        "--workload", args.workload, "--method", args.method,
+                        "--block", str(args.block)],
                        capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(r.stdout[-4000:] + r.stderr[-4000:])

@@ -445,7 +445,8 @@ typedef struct tinv_server_cfg {
     int32_t device;       /* CUDA device ordinal                                               */
     int32_t wave_ctas;    /* one stream's share of the SMs (persistent CTAs of a wave's       */
                           /*   cluster kernel, at least); 0 = the SM count / max_inflight      */
-    int32_t reserved[7];
+    int32_t block;        /* as tinv_opts.block (compact WY in blocks of members; 0 = off)     */
+    int32_t reserved[6];
 } tinv_server_cfg;
 
 /* Request states (tinv_poll). */

@@ -484,7 +484,7 @@ class ServerCfg(ctypes.Structure):
                 ("hbm_fraction", ctypes.c_double), ("method", ctypes.c_int32),
                 ("max_team", ctypes.c_int32), ("max_pending", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("wave_ctas", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("block", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class Stats(ctypes.Structure):

@@ -499,6 +499,108 @@ __device__ bool chunk_solve(int64_t n, const Fac& f, double* x, double* ysave, d
 }
 
 // ------------------------------------------------------------------------------------------
+// Repair of a CTA's chunked back substitution (all rows of the system in x, the forward results
+// in y) whose consistency check failed.  The rows at and below `top` passed; the chunk [top - L,
+// top) that failed is redone sequentially from x[top], x[top + 1]; the rows above it are redone
+// by a fresh chunked pass (128 chunks, one thread folding the chunk maps as values) from those
+// values, and its chunk boundaries are checked again.  Returns 0 once every row passed, else,
+// after kRepairRounds rounds, the row from which the sequential fallback must restart.  Called
+// by every thread of the CTA; `sh` holds >= 1024 doubles.
+// ------------------------------------------------------------------------------------------
+constexpr int kRepairRounds = 4;
+__device__ __noinline__ int64_t cta_back_repair(int64_t n, const Fac& f, const double* y, double* x,
+                                                double* sh, int64_t top, int64_t L, double tol)
+{
+    constexpr int P = 128;
+    const int t = threadIdx.x;
+    __shared__ unsigned long long s_rtop;
+    for (int round = 0; round < kRepairRounds; ++round) {
+        const int64_t lo_f = max((int64_t)0, top - L);
+        if (t == 0) {  // the failing chunk, sequentially
+            double cur = top < n ? x[top] : 0.0, nxt = top + 1 < n ? x[top + 1] : 0.0;
+            for (int64_t k = top - 1; k >= lo_f; --k) {
+                const double v = back_row(f.a[k], f.b[k], f.r[k], y[k], cur, nxt);
+                x[k] = v;
+                nxt = cur;
+                cur = v;
+            }
+        }
+        __syncthreads();
+        const int64_t R = lo_f;  // rows [0, R) remain, entering values x[R], x[R + 1]
+        if (R <= 0) return 0;
+        const int Pn = (int)min((int64_t)P, max((int64_t)1, R / 2));
+        const int64_t Lc = (R + Pn - 1) / Pn;
+        const int64_t clo = (int64_t)t * Lc;
+        const int64_t chi = (t < Pn) ? min(R, clo + Lc) : clo;
+        const bool act = (t < Pn) && (clo < chi);
+        double p0 = 0.0, p1 = 0.0, h10 = 1.0, h11 = 0.0, h20 = 0.0, h21 = 1.0;
+        if (act) {
+            for (int64_t k = chi - 1; k >= clo; --k) {
+                const double a = f.a[k], b = f.b[k];
+                const double vp = back_row(a, b, f.r[k], y[k], p0, p1);
+                const double v1 = fma(a, h10, b * h11);
+                const double v2 = fma(a, h20, b * h21);
+                p1 = p0;
+                p0 = vp;
+                h11 = h10;
+                h10 = v1;
+                h21 = h20;
+                h20 = v2;
+            }
+        }
+        if (t < Pn) {
+            sh[t] = h10;
+            sh[P + t] = h20;
+            sh[2 * P + t] = h11;
+            sh[3 * P + t] = h21;
+            sh[4 * P + t] = p0;
+            sh[5 * P + t] = p1;
+        }
+        __syncthreads();
+        double* ent = sh + 6 * P;  // [2P] values entering each chunk
+        if (t == 0) {
+            double s0 = x[R], s1 = (R + 1 < n) ? x[R + 1] : 0.0;
+            for (int q = Pn - 1; q >= 0; --q) {
+                ent[2 * q] = s0;
+                ent[2 * q + 1] = s1;
+                const double n0 = fma(sh[q], s0, fma(sh[P + q], s1, sh[4 * P + q]));
+                const double n1 = fma(sh[2 * P + q], s0, fma(sh[3 * P + q], s1, sh[5 * P + q]));
+                s0 = n0;
+                s1 = n1;
+            }
+        }
+        __syncthreads();
+        if (act) {
+            double cur = ent[2 * t], nxt = ent[2 * t + 1];
+            for (int64_t k = chi - 1; k >= clo; --k) {
+                const double v = back_row(f.a[k], f.b[k], f.r[k], y[k], cur, nxt);
+                x[k] = v;
+                nxt = cur;
+                cur = v;
+            }
+        }
+        if (t == 0) s_rtop = 0ull;
+        __syncthreads();
+        // the boundaries between the new chunks (the top chunk started from exact values)
+        bool bad = false;
+        if (act && chi < R) {
+            const double x1 = x[chi], x2 = x[chi + 1];
+            bad = !row_consistent(f.a[chi - 1], f.b[chi - 1], f.r[chi - 1], y[chi - 1], x1, x2, x[chi - 1], tol);
+            if (chi - 2 >= clo)
+                bad = bad || !row_consistent(f.a[chi - 2], f.b[chi - 2], f.r[chi - 2], y[chi - 2], x[chi - 1], x1,
+                                             x[chi - 2], tol);
+        }
+        if (bad) atomicMax(&s_rtop, (unsigned long long)chi);
+        __syncthreads();
+        top = (int64_t)s_rtop;
+        __syncthreads();
+        if (top == 0) return 0;
+        L = Lc;
+    }
+    return top;
+}
+
+// ------------------------------------------------------------------------------------------
 // Team-distributed solve of (T - s I) x = fac * b.
 //
 // The team's G CTAs each own rows [r0, r1) (>= 2 rows each).  Inside a CTA the first 128
@@ -831,6 +933,20 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
         const unsigned long long v = ld_volatile_u64(tr.flag);
         fallback = (v >> 32) == tr.stamp;
         top = (int64_t)(v & 0xffffffffull);
+    }
+    if (fallback && tr.G == 1) {
+        // one CTA: repair from the failing chunk upwards; the sequential back substitution only
+        // for what the repair rounds leave
+        const int64_t rest = cta_back_repair(n, f, ysave, vsm, sh, top, L, tr.tol);
+        if (rest > 0) {
+            staged_seq_back(n, f, ysave, vsm, sh, rest);
+            if (t == 0 && tr.nfall) atomicAdd(tr.nfall, 1ull);
+        }
+        __syncthreads();
+        if (vout)
+            for (int64_t k = r0 + t; k < r1; k += B) vout[k] = vsm[k];
+        __syncthreads();
+        return true;
     }
     if (fallback) {
         // the back substitution again, sequentially, by the first CTA of the team, for the rows

@@ -234,6 +234,7 @@ Wave* tinv_server::launch(std::vector<ReqP>&& reqs, int slot, int ctas)
         o.device_ptrs = 1;
         o.stream = st;
         o.max_team = cfg.max_team;
+        o.block = cfg.block;
         // each wave's persistent kernel holds one CTA on each of its SMs (a CTA fills an SM's
         // registers), and the worker keeps the grids of the waves in flight within the SM count,
         // so every wave's CTAs are co-resident

@@ -86,6 +86,9 @@ def workload(name: str):
     elif name == "toeplitz4200":
         d, e = toeplitz(4200, 2.0, 1.0)
         return d, e, toeplitz_eigenpairs(4200, 2.0, 1.0)[0]
+    elif name == "toeplitz6000":
+        d, e = toeplitz(6000, 2.0, 1.0)
+        return d, e, toeplitz_eigenpairs(6000, 2.0, 1.0)[0]
     elif name == "uniform10000":
         d, e = uniform(10000, seed=1)
     elif name == "zero10000":
