@@ -75,9 +75,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="glued4200")
     ap.add_argument("--method", choices=["cwy", "mgs"], default="cwy")
-    ap.add_argument("--block", type=int, default=8,
+    ap.add_argument("--block", type=int, default=None,
                     help="compact WY: cluster members orthogonalized in blocks of up to this many "
-                         "(Sec. 3.2's block form; 0 = one member at a time, Alg. 4)")
+                         "(Sec. 3.2's block form; 0 = one member at a time, Alg. 4); default 8 "
+                         "for single problems, 0 for the batch and the served stream (what "
+                         "tinv_tune_batch picks there)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
@@ -1191,6 +1193,8 @@ def phases_arm(args):
 
 def main():
     args = parse()
+    if args.block is None:
+        args.block = 0 if args.workload in ("batch512", "serve") else 8
     if args.phases_child:
         return _phases_child(args)
     if args.phases:

@@ -245,11 +245,13 @@ __device__ __forceinline__ int block_members(const Ws& w, int64_t mc, int G)
     // staged vectors in shared memory: 2 NB (mc) doubles for the T products, NB (mc + NB) for
     // pass C (NB = kBlockMax, the staging stride)
     if ((int64_t)2 * kBlockMax * mc > w.xcap || (int64_t)kBlockMax * (mc + kBlockMax) > w.xcap) return 1;
+    // the CTA-local solves use the staging area as their scratch
+    if (w.xcap < SolveScratch<16>::size(1) || w.xcap < 6 * kStageRows) return 1;
     return nb;
 }
 
 // ---- one cluster by the blocked compact-WY path (Sec. 3.2; Alg. 4's sweeps per block) -----
-__device__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int nb)
+__device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int nb)
 {
     const Problem& p = cx.p;
     const Ws& w = cx.w;
@@ -383,8 +385,9 @@ __device__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int nb)
                     TeamRef tr{nullptr, &tgt, 1, 0, cx.err, nullptr, 0ull,
                                (unsigned long long*)&w.ctr[kCtrFallback],
                                may_end ? kSolveTol : kSolveTolLoose, 0u};
-                    if (!team_solve(n, f, qb + cc * ns, s_fac[cc], cx.vsm, vb + cc * ns, pG, 0, n,
-                                    nullptr, nullptr, tr, red))
+                    // all 16 warps of the CTA take chunks; the staging area is the scratch
+                    if (!team_solve_nw<16>(n, f, qb + cc * ns, s_fac[cc], cx.vsm, vb + cc * ns, pG, 0, n,
+                                           nullptr, nullptr, tr, xs))
                         return false;
                 }
                 PROF_MARK(cx.prof, kPhSolve);

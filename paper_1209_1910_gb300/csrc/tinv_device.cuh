@@ -649,12 +649,25 @@ __device__ __forceinline__ void compose2(double& m00, double& m01, double& m10, 
     f1 = b1;
 }
 
-__device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* bsrc, double fac,
-                                        double* vsm, double* vout, double* ysave, int64_t r0,
-                                        int64_t r1, double* pubf, double* pubb, TeamRef tr,
-                                        double* sh)
+// Scratch layout of the team solve with NW chunk warps (doubles of sh): forward warp maps,
+// warp carries, back warp maps, warp entering values, the team's published maps (6 per rank),
+// then the chunk maps (6 per chunk).
+template <int NW>
+struct SolveScratch {
+    static constexpr int kFwd = 0, kCarry = 2 * NW, kWarp = 3 * NW, kEnter = 9 * NW;
+    static constexpr int kPub = (11 * NW + 15) / 16 * 16;
+    __device__ static constexpr int chunk_maps(int G) { return kPub + 6 * G; }
+    __device__ static constexpr int size(int G) { return kPub + 6 * G + 6 * 32 * NW; }
+};
+
+template <int NW>
+__device__ __noinline__ bool team_solve_nw(int64_t n, const Fac& f, const double* bsrc, double fac,
+                                           double* vsm, double* vout, double* ysave, int64_t r0,
+                                           int64_t r1, double* pubf, double* pubb, TeamRef tr,
+                                           double* sh)
 {
-    constexpr int NW = 4, PT = 32 * NW;
+    constexpr int PT = 32 * NW;
+    using SS = SolveScratch<NW>;
     const int t = threadIdx.x, B = blockDim.x, lane = t & 31, wid = t >> 5;
     if (!TINV_IN(dbg_range(r0, r1, n) && r1 > r0 && tr.rank < tr.G && tr.G <= kTeamMax, tr.err))
         return false;
@@ -706,22 +719,22 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
             eb = 0.0;
         }
         if (lane == 31) {
-            sh[2 * wid] = A;
-            sh[2 * wid + 1] = Bf;
+            sh[SS::kFwd + 2 * wid] = A;
+            sh[SS::kFwd + 2 * wid + 1] = Bf;
         }
     }
     __syncthreads();
     if (t == 0 && tr.G > 1) {
         double CA = 1.0, CB = 0.0;
         for (int w2 = 0; w2 < NW; ++w2) {
-            CB = fma(sh[2 * w2], CB, sh[2 * w2 + 1]);
-            CA = sh[2 * w2] * CA;
+            CB = fma(sh[SS::kFwd + 2 * w2], CB, sh[SS::kFwd + 2 * w2 + 1]);
+            CA = sh[SS::kFwd + 2 * w2] * CA;
         }
         pubf[2 * tr.rank] = CA;
         pubf[2 * tr.rank + 1] = CB;
     }
     if (!team_sync(tr.bar, *tr.target, tr.G, tr.err, tr.limit)) return false;
-    double* pf = sh + 128;  // the published forward maps of the CTAs before this one
+    double* pf = sh + SS::kPub;  // the published forward maps of the CTAs before this one
     for (int q = t; q < tr.rank; q += B) {
         pf[2 * q] = __ldcg(&pubf[2 * q]);
         pf[2 * q + 1] = __ldcg(&pubf[2 * q + 1]);
@@ -736,13 +749,13 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
             for (int q = 0; q < tr.rank; ++q) c = fma(pf[2 * q], c, pf[2 * q + 1]);
         }
         for (int w2 = 0; w2 < NW; ++w2) {
-            sh[16 + w2] = c;
-            c = fma(sh[2 * w2], c, sh[2 * w2 + 1]);
+            sh[SS::kCarry + w2] = c;
+            c = fma(sh[SS::kFwd + 2 * w2], c, sh[SS::kFwd + 2 * w2 + 1]);
         }
     }
     __syncthreads();
     if (act) {
-        double c = fma(ea, sh[16 + wid], eb);
+        double c = fma(ea, sh[SS::kCarry + wid], eb);
         for (int64_t k = lo; k < hi; ++k) {
             if (k + 1 < n) {
                 const double b1 = (k + 1 < hi) ? vsm[k + 1] : bnext;
@@ -788,7 +801,7 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
     // The chunks' own maps, kept for the value fold below that gives every chunk its boundary
     // values (applying composed maps to values loses accuracy when they span several small
     // pivots; the compositions are used only between warps and between CTAs).
-    double* cm = sh + 128 + 6 * tr.G;  // [6 * PT]; sh holds 2048 doubles, so G <= kTeamMax
+    double* cm = sh + SS::chunk_maps(tr.G);  // [6 * PT]
     if (part) {
         double* o = cm + 6 * t;
         o[0] = m00;
@@ -811,7 +824,7 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
             if (lane + d < 32) compose2(m00, m01, m10, m11, f0, f1, n00, n01, n10, n11, q0, q1);
         }
         if (lane == 0) {
-            double* o = sh + 32 + 6 * wid;
+            double* o = sh + SS::kWarp + 6 * wid;
             o[0] = m00;
             o[1] = m01;
             o[2] = m10;
@@ -824,7 +837,7 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
     if (t == 0 && tr.G > 1) {
         double c00 = 1.0, c01 = 0.0, c10 = 0.0, c11 = 1.0, c0 = 0.0, c1 = 0.0;
         for (int w2 = NW - 1; w2 >= 0; --w2) {  // CTA map = W_0 o W_1 o W_2 o W_3
-            const double* o = sh + 32 + 6 * w2;
+            const double* o = sh + SS::kWarp + 6 * w2;
             double t00 = o[0], t01 = o[1], t10 = o[2], t11 = o[3], t0 = o[4], t1 = o[5];
             compose2(t00, t01, t10, t11, t0, t1, c00, c01, c10, c11, c0, c1);
             c00 = t00;
@@ -843,7 +856,7 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
         o[5] = c1;
     }
     if (!team_sync(tr.bar, *tr.target, tr.G, tr.err, tr.limit)) return false;
-    double* pb = sh + 128;  // the published back maps of the CTAs after this one
+    double* pb = sh + SS::kPub;  // the published back maps of the CTAs after this one
     for (int q = tr.rank + 1 + t; q < tr.G; q += B)
         for (int u = 0; u < 6; ++u) pb[6 * q + u] = __ldcg(&pubb[6 * q + u]);
     __syncthreads();
@@ -857,9 +870,9 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
             s1 = n1;
         }
         for (int w2 = NW - 1; w2 >= 0; --w2) {
-            sh[64 + 2 * w2] = s0;
-            sh[64 + 2 * w2 + 1] = s1;
-            const double* o = sh + 32 + 6 * w2;
+            sh[SS::kEnter + 2 * w2] = s0;
+            sh[SS::kEnter + 2 * w2 + 1] = s1;
+            const double* o = sh + SS::kWarp + 6 * w2;
             const double n0 = fma(o[0], s0, fma(o[1], s1, o[4]));
             const double n1 = fma(o[2], s0, fma(o[3], s1, o[5]));
             s0 = n0;
@@ -870,7 +883,7 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
     // each warp's first lane folds the warp's chunk maps as values, from the warp's boundary
     // values upwards; chunk p receives (x_hi, x_hi+1) in its slots 0 and 1
     if (part && lane == 0) {
-        double s0 = sh[64 + 2 * wid], s1 = sh[64 + 2 * wid + 1];
+        double s0 = sh[SS::kEnter + 2 * wid], s1 = sh[SS::kEnter + 2 * wid + 1];
         for (int l = 31; l >= 0; --l) {
             double* o = cm + 6 * (32 * wid + l);
             const double q00 = o[0], q01 = o[1], q10 = o[2], q11 = o[3], q0 = o[4], q1 = o[5];
@@ -969,6 +982,15 @@ __device__ __noinline__ bool team_solve(int64_t n, const Fac& f, const double* b
         __syncthreads();
     }
     return true;
+}
+
+// The team solve with 4 chunk warps (the team path; sh holds 2048 doubles, so G <= kTeamMax).
+__device__ __forceinline__ bool team_solve(int64_t n, const Fac& f, const double* bsrc, double fac,
+                                           double* vsm, double* vout, double* ysave, int64_t r0,
+                                           int64_t r1, double* pubf, double* pubb, TeamRef tr,
+                                           double* sh)
+{
+    return team_solve_nw<4>(n, f, bsrc, fac, vsm, vout, ysave, r0, r1, pubf, pubb, tr, sh);
 }
 
 enum ColKind { kLower = 0, kUpper = 1 };
