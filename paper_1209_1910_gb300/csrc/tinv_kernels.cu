@@ -406,23 +406,26 @@ __global__ void k_orth_plan(Problem p, Ws w, int32_t method)
 // ==========================================================================================
 
 // Interchange decision of the scaled pivoting rule: true iff fl(|c|/s2) > fl(|a|/s1) (the rule
-// written with correctly rounded quotients; a zero numerator counts as 0).  Most steps are
-// decided from the cross products |c| s1 and |a| s2: when they differ by more than a relative
-// 2^-49 the rounded quotients are ordered the same way (each quotient and product carries at
-// most 2^-53 relative rounding error), so the divisions are only evaluated inside that band or
-// when a product is not a normal number.
+// written with correctly rounded quotients; a zero numerator counts as 0).  All four arguments
+// are non-negative, and non-negative doubles are ordered as their bit patterns, so the tests
+// below are integer compares (they stay off the FP64 pipe, whose latency bounds this
+// one-thread-per-shift recurrence).  Most steps are decided from the cross products P = |c| s1
+// and Q = |a| s2: when both are normal and their bit patterns differ by more than 16, the larger
+// exceeds the smaller by at least 17 units in the last place of the smaller, more than a
+// relative 2^-49, and then the rounded quotients are ordered the same way (each quotient and
+// product carries at most 2^-53 relative rounding error).  Only inside that band, or when a
+// product is not normal, are the two divisions evaluated.
 __device__ __forceinline__ bool lu_interchange(double aa, double s1, double cc, double s2)
 {
-    if (cc == 0.0) return false;
-    if (aa == 0.0) return true;
-    const double P = __dmul_rn(cc, s1);  // |c| s1
-    const double Q = __dmul_rn(aa, s2);  // |a| s2
-    const double kMarg = 1.0 + 1.7763568394002505e-15;  // 1 + 2^-49
-    const bool normal = (P >= 2.2250738585072014e-308) && (Q >= 2.2250738585072014e-308) &&
-                        (P <= 1.0e300) && (Q <= 1.0e300);
-    if (normal) {
-        if (P > __dmul_rn(Q, kMarg)) return true;
-        if (Q > __dmul_rn(P, kMarg)) return false;
+    if (__double_as_longlong(cc) == 0) return false;
+    if (__double_as_longlong(aa) == 0) return true;
+    const long long P = __double_as_longlong(__dmul_rn(cc, s1));  // |c| s1
+    const long long Q = __double_as_longlong(__dmul_rn(aa, s2));  // |a| s2
+    constexpr long long kMinNormal = 0x0010000000000000ll;         // DBL_MIN
+    constexpr long long kLarge = 0x7e37e43c8800759cll;             // 1e300
+    if (P >= kMinNormal && Q >= kMinNormal && P <= kLarge && Q <= kLarge) {
+        if (P > Q + 16) return true;
+        if (Q > P + 16) return false;
     }
     return __ddiv_rn(cc, s2) > __ddiv_rn(aa, s1);
 }
@@ -503,9 +506,10 @@ __global__ void k_lu(int64_t n, const double* __restrict__ d, const double* __re
 }
 
 // Problem table: global eigenvalue j of problem s, shift w'_j, rows at the problem's offsets.
-__global__ void k_lu_seg(Problem p, Ws w)
+__global__ void k_lu_seg(Problem p, Ws w, int lanes)
 {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int)threadIdx.x >= lanes) return;
+    const int64_t j = (int64_t)blockIdx.x * lanes + threadIdx.x;
     if (j >= p.M) return;
     const Seg* g = w.segs + w.segj[j];
     const int64_t n = g->n;
@@ -1452,8 +1456,8 @@ size_t chain_smem_bytes(int64_t n, bool use_smem, int32_t xcap)
 int32_t block_xcap(int64_t n)
 {
     if (!chain_use_smem(n)) return 0;
-    // 220 KB of dynamic shared memory, 4 KB of it left for the kernel's static arrays
-    const int64_t avail = (int64_t)(220 * 1024) / 8 - 2048 - 2 * n - 64 - 512;
+    // 227 KB of shared memory per CTA, 8 KB of it left for the kernel's static arrays
+    const int64_t avail = (int64_t)(227 * 1024 - 8 * 1024) / 8 - 2048 - 2 * n - 64 - 512;
     return (int32_t)max((int64_t)0, min((int64_t)16384, avail));
 }
 
@@ -1518,11 +1522,15 @@ static int device_sms()
 cudaError_t launch_lu_seg(const Problem& p, const Ws& w, cudaStream_t st)
 {
     if (p.M <= 0) return cudaSuccess;
-    const int th = 32;  // one warp per block spreads the sequential factorizations over SMs
-    k_lu_seg<<<(unsigned)((p.M + th - 1) / th), th, 0, st>>>(p, w);
+    // one warp per block spreads the sequential factorizations over the SMs; with fewer than
+    // 32 shifts per SM each warp takes ceil(M / SMs) shifts, so that every SM gets one
+    const int sms = device_sms();
+    const int64_t per = (p.M + sms - 1) / sms;
+    const int lanes = (int)(per < 32 ? per : 32);
+    k_lu_seg<<<(unsigned)((p.M + lanes - 1) / lanes), 32, 0, st>>>(p, w, lanes);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    const unsigned rb = (unsigned)min(p.M, (int64_t)device_sms() * 8);
+    const unsigned rb = (unsigned)min(p.M, (int64_t)sms * 8);
     k_recip_seg<<<rb, 256, 0, st>>>(p, w);
     return cudaGetLastError();
 }

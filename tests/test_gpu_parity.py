@@ -63,10 +63,26 @@ def test_plan_bit_exact(gpu, orc):
 # ---------------------------------------------------------------------------------------------
 # a3: LU
 # ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("case", ["uniform1000", "glued4200", "hand3"])
+def _near_tie(scale):
+    """First pivot step near the tie |c| (|a| + |b|) = |a| (|c| + |a1| + |b1|) of the scaled
+    pivoting rule (a = d0 - s = 1, b = c = e0 = 2, a1 + b1 = 4): shifts a few units in the last
+    place either side of s = 0 put the cross products inside, at and outside the band that
+    integer compares of their bit patterns cannot decide; `scale` (a power of two) moves the
+    products below the normal range or above 1e300."""
+    d = np.array([1.0, 3.0, 2.0, 5.0]) * scale
+    e = np.array([2.0, 1.0, 0.5]) * scale
+    shifts = np.arange(-24, 25) * 2.0 ** -52 * scale
+    return d, e, shifts
+
+
+@pytest.mark.parametrize("case", ["uniform1000", "glued4200", "hand3", "near_tie",
+                                  "near_tie_tiny", "near_tie_huge"])
 def test_lu_bit_exact(gpu, orc, case):
     if case == "hand3":
         d, e, shifts = np.array([1.0, 4.0, 1.0]), np.array([2.0, 1.0]), np.array([0.0, 0.5, 5.0])
+    elif case.startswith("near_tie"):
+        d, e, shifts = _near_tie({"near_tie": 1.0, "near_tie_tiny": 2.0 ** -520,
+                                  "near_tie_huge": 2.0 ** 500}[case])
     else:
         d, e, w = inputs.workload(case)
         rng = np.random.default_rng(0)
