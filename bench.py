@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--method", choices=["cwy", "mgs"], default="cwy")
     ap.add_argument("--block", type=int, default=None,
                     help="compact WY: cluster members orthogonalized in blocks of up to this many "
-                         "(Sec. 3.2's block form; 0 = one member at a time, Alg. 4); default 8 "
+                         "(Sec. 3.2's block form; 0 = one member at a time, Alg. 4); default 16 "
                          "for single problems, 0 for the batch and the served stream (what "
                          "tinv_tune_batch picks there)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -1061,8 +1061,8 @@ def ours_arm(args):
                                           "of the persistent grid (compact WY spreads each "
                                           "cluster over a CTA team)" % (ncl, min(ncl, P), P)}}
         # the other form of compact WY on the same workload: one member at a time (Alg. 4 as
-        # printed) when the line measures blocks, blocks of 8 otherwise
-        other = 0 if blk >= 2 else 8
+        # printed) when the line measures blocks, blocks of 16 otherwise
+        other = 0 if blk >= 2 else 16
         step("cwy", False, block=other)
         torch.cuda.synchronize()
         ms = []
@@ -1075,7 +1075,7 @@ def ours_arm(args):
             b.record(st)
             b.synchronize()
             ms.append(a.elapsed_time(b))
-        out["compare"]["cwy_one_member" if other == 0 else "cwy_block8"] = {
+        out["compare"]["cwy_one_member" if other == 0 else "cwy_block16"] = {
             "value": m / (statistics.mean(ms) * 1e-3), "ms_per_step": statistics.mean(ms),
             "block": other}
 
@@ -1131,7 +1131,7 @@ def extras():
 # cycles per phase and prints them when the CTA ends)
 # ------------------------------------------------------------------------------------------
 PHASES = ["total", "solve", "A", "b1", "T1red", "T1", "b2", "Bload", "Brow", "Bsum", "B", "b3",
-          "T2refl", "T2row", "T2", "b4", "Cload", "Crow", "C", "b5", "load", "end"]
+          "T2refl", "T2red", "T2row", "T2", "b4", "Cload", "Crow", "C", "b5", "load", "end"]
 
 
 def _phases_child(args):
@@ -1194,7 +1194,7 @@ def phases_arm(args):
 def main():
     args = parse()
     if args.block is None:
-        args.block = 0 if args.workload in ("batch512", "serve") else 8
+        args.block = 0 if args.workload in ("batch512", "serve") else 16
     if args.phases_child:
         return _phases_child(args)
     if args.phases:

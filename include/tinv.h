@@ -84,7 +84,7 @@ typedef struct tinv_opts {
                          /*   a small value makes a launch end with TINV_ETIMEDOUT, which tests  */
                          /*   the bounded-wait failure path without hanging the GPU              */
     int32_t block;       /* compact WY only: 0 or 1 = each cluster member orthogonalized on its  */
-                         /*   own (Alg. 4); b = 2..8 = a cluster's members after its head in    */
+                         /*   own (Alg. 4); b = 2..16 = a cluster's members after its head in   */
                          /*   blocks of up to b that sweep together and are orthogonalized by   */
                          /*   the compact-WY block form of Sec. 3.2 (Eqs. cwy1/cwy2).  Applies  */
                          /*   to clusters on CTA teams whose block staging fits the shared      */
@@ -176,7 +176,7 @@ typedef struct tinv_tuning {
 /*
  * tinv_tune_auto -- tinv_tune over both launch parameters of the cluster kernel: the switch
  * between one member at a time (Sec. 3.3.2, GEMV passes) and the blocked compact-WY form of
- * Sec. 3.2 (tinv_opts.block 4 or 8, passes over Y for several members at once), then the team
+ * Sec. 3.2 (tinv_opts.block 4, 8 or 16, passes over Y for several members at once), then the team
  * cap with the chosen block.  Each stage keeps the current choice unless a candidate is at least
  * 1% faster; MGS and problems without multi-member clusters take (0, 0).  Arguments as
  * tinv_tune (o->block and o->max_team are not used); *out receives the choice.  Cached like
@@ -220,7 +220,7 @@ int tinv_tune_save(const char* path);
  * (path NULL), -2 (the file cannot be read or lacks a tag line) or -3 (a malformed entry -- a
  * missing or non-numeric field, trailing text, a line longer than 1023 bytes, or a value out of
  * range: unknown kind, SM count <= 0, m > n or largest cluster > m (kinds 0 and 1), cap outside
- * [0, 192], block outside [0, 8], time negative or not finite, unknown method; the entries before
+ * [0, 192], block outside [0, 16], time negative or not finite, unknown method; the entries before
  * it are kept, the rest of the file is not read).  No device is needed.
  */
 int tinv_tune_load(const char* path);

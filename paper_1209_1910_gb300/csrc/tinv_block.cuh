@@ -242,9 +242,10 @@ __device__ __forceinline__ int block_members(const Ws& w, int64_t mc, int G)
     // up to 2 members per CTA (each CTA solves its members one after the other); the panel
     // buffer holds bb (n/G + 1) <= 2 n + 64 doubles
     int nb = min(w.block, 2 * G);
-    // staged vectors in shared memory: 2 NB (mc) doubles for the T products, NB (mc + NB) for
-    // pass C (NB = kBlockMax, the staging stride)
-    if ((int64_t)2 * kBlockMax * mc > w.xcap || (int64_t)kBlockMax * (mc + kBlockMax) > w.xcap) return 1;
+    // staged vectors in shared memory, nb doubles per row: 2 nb mc for the T products, nb (mc + nb)
+    // for pass C; the block is halved until they fit
+    while (nb >= 2 && ((int64_t)2 * nb * mc > w.xcap || (int64_t)nb * (mc + nb) > w.xcap)) nb >>= 1;
+    if (nb < 2) return 1;
     // the CTA-local solves use the staging area as their scratch
     if (w.xcap < SolveScratch<16>::size(1) || w.xcap < 6 * kStageRows) return 1;
     return nb;
@@ -285,7 +286,8 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
     double* xT = tb + 2 * (size_t)NB * ns;     // X_T, then T_k R1 before it  [i NB + c]
     double* ybr = tb + 3 * (size_t)NB * ns;    // rows k0.. of Y_b  [r NB + c] (rank 1's slot; G >= 2)
     double* W = cx.vsm;                        // this CTA's panel rows, column c at + c Rb
-    double* xs = cx.xs;
+    double* xs = cx.xs;                        // staged vectors, nbs doubles per row
+    const int nbs = nb;
     double* red = cx.red;
     double* scal_t = w.partScal + (size_t)leader * kScalTeam;
     __shared__ double s_cv[NB], s_tv[NB], s_yh[NB], s_fac[NB], s_coef[NB];
@@ -297,7 +299,8 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
     if (!TINV_IN(s0 >= 0 && mc >= 1 && s0 + mc <= w.nM && n <= p.n && rank < G && leader + G <= w.P &&
                      dbg_range((int64_t)jr.off, (int64_t)jr.off + mc * n, w.nF) &&
                      dbg_range(w.cltoff[c], w.cltoff[c] + mc * mc, w.nTT) &&
-                     nb >= 2 && nb <= NB && nb <= 2 * G && (int64_t)2 * NB * mc <= w.xcap &&
+                     nb >= 2 && nb <= NB && nb <= 2 * G && (int64_t)2 * nb * mc <= w.xcap &&
+                     (int64_t)nb * (mc + nb) <= w.xcap &&
                      (p.zlen == 0 || dbg_range(sg.z + jr.jl * ldz, sg.z + (jr.jl + mc - 1) * ldz + n, p.zlen)),
                  cx.err))
         return false;
@@ -418,10 +421,11 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
                 for (int64_t q = t; q < c1 * bb; q += B) {
                     const int64_t l = q / bb;
                     const int cc = (int)(q % bb);
-                    xs[l * NB + cc] = sum_partials(teamP + l * NB + cc, pstride, G);
+                    xs[l * nbs + cc] = sum_partials(teamP + l * NB + cc, pstride, G);
                 }
                 __syncthreads();
-                mv_coldots_fit<kUpper, NB>(Tc, ldt, c0, c1, 0, k0, XRow{xs, NB}, bb, red,
+                PROF_MARK(cx.prof, kPhT1a);
+                mv_coldots_fit<kUpper, NB>(Tc, ldt, c0, c1, 0, k0, XRow{xs, nbs}, bb, red,
                                        [&](int64_t i, int cc, double v) { sP[i * NB + cc] = v; });
             }
             PROF_MARK(cx.prof, kPhT1);
@@ -432,7 +436,7 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
                 for (int64_t q = t; q < k0 * bb; q += B) {
                     const int64_t l = q / bb;
                     const int cc = (int)(q % bb);
-                    xs[l * NB + cc] = __ldcg(&sP[l * NB + cc]);
+                    xs[l * nbs + cc] = __ldcg(&sP[l * NB + cc]);
                 }
             for (int64_t q = t; q < (int64_t)bb * Rb; q += B) {
                 const int cc = (int)(q / Rb);
@@ -441,7 +445,7 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
             }
             __syncthreads();
             if (k0 > 0)
-                mv_rowdots<kAllCols, NB>(Yc, n, rb0, rb1, k0, XRow{xs, NB}, bb, red,
+                mv_rowdots<kAllCols, NB>(Yc, n, rb0, rb1, k0, XRow{xs, nbs}, bb, red,
                                          [&](int64_t r, int cc, double v) { W[cc * Rb + (r - rb0)] -= v; });
             PROF_MARK(cx.prof, kPhBb);
             // ---- (QR) Householder QR of the panel, one column (and team barrier) at a time ----
@@ -534,60 +538,59 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
                     s_yb[ca * NB + cb] = __ldcg(&ybr[ca * NB + cb]);  // y_cb at row k0 + ca
                 }
             }
-            // staged [G12 | R1] for the rows [i0, k0) of T_k (vector v < bb: G12[l, v] =
-            // (Y_k^T Y_b)[l, v]; v = bb + c: R1[l, c] = Y[k0 + c, l], row k0 + c of Y_k)
+            // staged [G12 | R1] for the rows [i0, k0) of T_k, 2 nbs doubles per row (vector
+            // v < bb: G12[l, v] = (Y_k^T Y_b)[l, v]; v = bb + c: R1[l, c] = Y[k0 + c, l], row
+            // k0 + c of Y_k)
             for (int64_t q = t; q < (k0 - i0) * bb; q += B) {
                 const int64_t l = i0 + q / bb;
                 const int cc = (int)(q % bb);
-                xs[(l - i0) * 2 * NB + cc] = sum_partials(teamP + NB * ns + l * NB + cc, pstride, G);
-                xs[(l - i0) * 2 * NB + bb + cc] = __ldcg(&Yc[(k0 + cc) + l * n]);
+                xs[(l - i0) * 2 * nbs + cc] = sum_partials(teamP + NB * ns + l * NB + cc, pstride, G);
+                xs[(l - i0) * 2 * nbs + bb + cc] = __ldcg(&Yc[(k0 + cc) + l * n]);
             }
             __syncthreads();
-            if (t == 0) {  // T_22 by the recurrence of Eq. cwy1 inside the block
-                for (int cb = 0; cb < bb; ++cb) {
-                    s_t22[cb * NB + cb] = s_tv[cb];
-                    for (int ca = cb - 1; ca >= 0; --ca) {
-                        double a = 0.0;
-                        for (int l = ca; l < cb; ++l) a = fma(s_t22[ca * NB + l], s_g22[l * NB + cb], a);
-                        s_t22[ca * NB + cb] = -s_tv[cb] * a;
-                    }
-                    for (int ca = cb + 1; ca < NB; ++ca) s_t22[ca * NB + cb] = 0.0;
+            PROF_MARK(cx.prof, kPhT2b);
+            // T_22 by the recurrence of Eq. cwy1 inside the block: T22[ca, cb] = -t_cb
+            // sum_{ca <= l < cb} T22[ca, l] G22[l, cb] needs only row ca's earlier entries, so
+            // lane ca of warp 0 takes row ca
+            if (wid == 0 && lane < bb) {
+                const int ca = lane;
+                for (int cb = 0; cb < ca; ++cb) s_t22[ca * NB + cb] = 0.0;
+                s_t22[ca * NB + ca] = s_tv[ca];
+                for (int cb = ca + 1; cb < bb; ++cb) {
+                    double a = 0.0;
+                    for (int l = ca; l < cb; ++l) a = fma(s_t22[ca * NB + l], s_g22[l * NB + cb], a);
+                    s_t22[ca * NB + cb] = -s_tv[cb] * a;
                 }
             }
-            // rows [i0, i1) of T_k times [G12 | R1]: into tP (first bb) and xT (last bb)
-            if (k0 > 0 && i1 > i0)
-                mv_rowdots<kUpperCol, 2 * NB>(Tc, ldt, i0, i1, k0, XRow{xs - i0 * 2 * NB, 2 * NB}, 2 * bb, red,
-                                              [&](int64_t i, int v, double a) {
-                                                  if (v < bb)
-                                                      tP[i * NB + v] = a;
-                                                  else
-                                                      xT[i * NB + (v - bb)] = a;
-                                              });
+            // rows [i0, i1) of T_k times G12 (into tP) and times R1 (into xT)
+            if (k0 > 0 && i1 > i0) {
+                const double* xg = xs - i0 * 2 * nbs;
+                mv_rowdots<kUpperCol, NB>(Tc, ldt, i0, i1, k0, XRow{xg, 2 * nbs}, bb, red,
+                                          [&](int64_t i, int v, double a) { tP[i * NB + v] = a; });
+                mv_rowdots<kUpperCol, NB>(Tc, ldt, i0, i1, k0, XRow{xg + bb, 2 * nbs}, bb, red,
+                                          [&](int64_t i, int v, double a) { xT[i * NB + v] = a; });
+            }
             __syncthreads();
-            // per row i of T_k: T[i, k0 + c] = -t_c (P[i, c] + sum_{c2 < c} T[i, k0 + c2] G22[c2, c]),
-            // X_T[i, c] = (T_k R1)[i, c] + sum_{c2 <= c} T[i, k0 + c2] y_c2[k0 + c]
-            for (int64_t i = i0 + t; i < i1; i += B) {
-                double t12[NB], pr[NB];
-#pragma unroll
-                for (int cc = 0; cc < NB; ++cc) {
-                    t12[cc] = 0.0;
-                    pr[cc] = (cc < bb) ? xT[i * NB + cc] : 0.0;
-                }
-#pragma unroll
-                for (int cc = 0; cc < NB; ++cc) {
-                    if (cc >= bb) break;
-                    double a = tP[i * NB + cc];
-                    for (int c2 = 0; c2 < cc; ++c2) a = fma(t12[c2], s_g22[c2 * NB + cc], a);
-                    t12[cc] = -s_tv[cc] * a;
-                    Tc[i + (k0 + cc) * ldt] = t12[cc];
-                }
-#pragma unroll
-                for (int cc = 0; cc < NB; ++cc) {
-                    if (cc >= bb) break;
-                    double a = pr[cc];
-                    for (int c2 = 0; c2 <= cc; ++c2) a = fma(t12[c2], s_yb[cc * NB + c2], a);
-                    xT[i * NB + cc] = a;
-                }
+            PROF_MARK(cx.prof, kPhT2c);
+            // T_12 = -(T_k G12) T_22 (Eq. cwy1) for the rows [i0, i1), one entry per thread; the
+            // rows are staged (xs is free again) for X_T[i, c] = (T_k R1)[i, c] +
+            // sum_{c2 <= c} T[i, k0 + c2] y_c2[k0 + c]
+            double* t12s = xs;
+            for (int64_t q = t; q < (i1 - i0) * bb; q += B) {
+                const int64_t i = i0 + q / bb;
+                const int cc = (int)(q % bb);
+                double a = 0.0;
+                for (int l = 0; l <= cc; ++l) a = fma(__ldcg(&tP[i * NB + l]), s_t22[l * NB + cc], a);
+                Tc[i + (k0 + cc) * ldt] = -a;
+                t12s[(i - i0) * nbs + cc] = -a;
+            }
+            __syncthreads();
+            for (int64_t q = t; q < (i1 - i0) * bb; q += B) {
+                const int64_t i = i0 + q / bb;
+                const int cc = (int)(q % bb);
+                double a = __ldcg(&xT[i * NB + cc]);
+                for (int c2 = 0; c2 <= cc; ++c2) a = fma(t12s[(i - i0) * nbs + c2], s_yb[cc * NB + c2], a);
+                xT[i * NB + cc] = a;
             }
             if (rank == 0 && t < bb * bb) {
                 // the block's own rows: T_22 into T, X_T[k0 + ca, cb] = sum_{ca <= l <= cb} T_22[ca, l] y_l[k0 + cb]
@@ -605,10 +608,10 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
             for (int64_t q = t; q < kb * bb; q += B) {
                 const int64_t l = q / bb;
                 const int cc = (int)(q % bb);
-                xs[l * NB + cc] = __ldcg(&xT[l * NB + cc]);
+                xs[l * nbs + cc] = __ldcg(&xT[l * NB + cc]);
             }
             __syncthreads();
-            mv_rowdots<kLowerCol, NB>(Yc, n, rc0, rc1, kb, XRow{xs, NB}, bb, red,
+            mv_rowdots<kLowerCol, NB>(Yc, n, rc0, rc1, kb, XRow{xs, nbs}, bb, red,
                                       [&](int64_t r, int cc, double a) {
                                           qb[cc * ns + r] = (r == k0 + cc) ? a - 1.0 : a;
                                       });

@@ -19,7 +19,7 @@ constexpr int kScalTeam = 16;       // doubles of per-CTA scalar partials
 // chunk maps: (2048 - 128 - 768) / 6 = 192 ranks.
 constexpr int kTeamMax = 192;
 // Largest block of the blocked compact-WY path (tinv_opts.block).
-constexpr int kBlockMax = 8;
+constexpr int kBlockMax = 16;
 
 // Device error word bits.
 constexpr int kErrTimeout = 1;   // a bounded spin wait expired

@@ -267,7 +267,7 @@ int two_stage(Timed timed, bool cwy, bool teams, int32_t P, int64_t nmax, int32_
     int rc = timed(0, 0, &best);
     int32_t bpick = 0, cpick = 0;
     if (!rc && cwy && teams) {
-        for (int32_t b : {4, 8}) {
+        for (int32_t b : {4, 8, 16}) {
             float t = 0.0f;
             rc = timed(0, b, &t);
             if (rc) break;

@@ -238,7 +238,7 @@ def test_tune_cache_file_round_trip(lib, tmp_path):
     lib.tinv_tune_clear()
     bad = tmp_path / "bad.txt"
     for wrong in ("0\tNVIDIA GB300\t152\t0\t0\t0\t10\t20\t1\t2\t0\t0\t1.0\n",   # m > n
-                  "0\tNVIDIA GB300\t152\t0\t0\t0\t10\t10\t1\t2\t0\t9\t1.0\n",   # block > 8
+                  "0\tNVIDIA GB300\t152\t0\t0\t0\t10\t10\t1\t2\t0\t17\t1.0\n",  # block > 16
                   "3\tNVIDIA GB300\t152\t0\t0\t0\t10\t10\t1\t2\t0\t0\t1.0\n",   # unknown kind
                   "0\tNVIDIA GB300\t152\t0\t0\t0\t10\t10\t1\t2\t0\t0\n"):         # a field short
         bad.write_text(tag + rows[0] + wrong + rows[1])

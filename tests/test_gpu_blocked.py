@@ -36,7 +36,7 @@ def _graded(n, m, kappa, seed=0):
     return (U * np.logspace(0, -np.log10(kappa), m)) @ W.T
 
 
-@pytest.mark.parametrize("block", [2, 5, 8])
+@pytest.mark.parametrize("block", [2, 5, 8, 16])
 @pytest.mark.parametrize("n,m,kappa", [(700, 80, 1.0), (1500, 200, 1e8), (97, 97, 1e3)])
 def test_orth_block_matches_oracle(gpu, orc, n, m, kappa, block):
     V = np.random.default_rng(5).standard_normal((n, m)) if kappa == 1.0 else _graded(n, m, kappa)
@@ -67,7 +67,7 @@ def _check_blocked(gpu, orc, d, e, w, block, oracle_clusters=None):
     return Z
 
 
-@pytest.mark.parametrize("block", [2, 4, 8])
+@pytest.mark.parametrize("block", [2, 4, 8, 16])
 def test_blocked_glued2100_every_cluster(gpu, orc, block):
     d, e = inputs.glued_wilkinson(100, 1e-10)
     w = inputs.eigenvalues(d, e)
@@ -77,9 +77,10 @@ def test_blocked_glued2100_every_cluster(gpu, orc, block):
     _check_blocked(gpu, orc, d, e, w, block)
 
 
-def test_blocked_glued4200_full_size(gpu, orc):
+@pytest.mark.parametrize("block", [8, 16])
+def test_blocked_glued4200_full_size(gpu, orc, block):
     d, e, w = inputs.workload("glued4200")
-    Z = _check_blocked(gpu, orc, d, e, w, 8,
+    Z = _check_blocked(gpu, orc, d, e, w, block,
                        oracle_clusters=lambda cl: [c for c in cl if len(c) == 200][:1] +
                                                   [c for c in cl if len(c) == 400][:1])
     # the one-member iteration spans the same invariant subspaces
