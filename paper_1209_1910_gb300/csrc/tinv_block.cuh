@@ -7,8 +7,9 @@
 // block form of Sec. 3.2 (Eqs. cwy1/cwy2): W = (I - Y T^T Y^T) V with one pass over Y for all
 // bb iterates, a Householder QR of the block's panel (one team barrier per column), T extended
 // by Eq. cwy1 with one triangular product over T for all columns, and the bb vectors
-// q = (Y T Y^T - I) e_col with one more pass over Y.  A sweep takes bb + 6 team barriers, where
-// one member at a time takes about 9 per member.  Included by tinv_kernels.cu inside its
+// q = (Y T Y^T - I) e_col with one more pass over Y.  A sweep takes bb + 6 team barriers (bb + 8
+// on teams of kSliceBlock or more CTAs, which sum the partials of S and of the Gram rows once
+// per team by slices), where one member at a time takes about 9 per member.  Included by tinv_kernels.cu inside its
 // namespace (it uses the cluster kernel's context and the helpers defined there).
 #pragma once
 
@@ -234,6 +235,26 @@ __device__ __forceinline__ double team_sum_at(const double* base, size_t stride,
     return warp_sum(a);
 }
 
+// Teams at least this large sum the partials of S and of the Gram rows once per team (rank r
+// a slice of the rows, then a team barrier) instead of on every CTA.
+constexpr int kSliceBlock = 8;
+
+// The team's sums of the partial rows [l0, l1) x nv (NB doubles per row, ranks `stride` apart,
+// in rank order) written over rank 0's partials, rank `rank` summing its slice of the rows;
+// returns after the team barrier that makes them visible (false: the barrier failed).
+__device__ __forceinline__ bool reduce_rows(double* base, size_t stride, int G, int64_t l0, int64_t l1,
+                                            int nv, int rank, Team& tm, int* err, uint32_t limit)
+{
+    const int64_t a = part_lo(l0, l1, rank, G), b = part_lo(l0, l1, rank + 1, G);
+    for (int64_t q = threadIdx.x; q < (b - a) * nv; q += blockDim.x) {
+        const int64_t l = a + q / nv;
+        const int c = (int)(q % nv);
+        const double v = sum_partials(base + l * kBlockMax + c, stride, G);
+        base[l * kBlockMax + c] = v;
+    }
+    return team_sync(tm.bar, tm.target, G, err, limit);
+}
+
 // Members per block the blocked path uses for a cluster of mc members on a team of G CTAs
 // (1: the cluster takes the one-member path).
 __device__ __forceinline__ int block_members(const Ws& w, int64_t mc, int G)
@@ -288,6 +309,7 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
     double* W = cx.vsm;                        // this CTA's panel rows, column c at + c Rb
     double* xs = cx.xs;                        // staged vectors, nbs doubles per row
     const int nbs = nb;
+    const bool sliced = G >= kSliceBlock;      // team sums of S and the Gram rows by slices
     double* red = cx.red;
     double* scal_t = w.partScal + (size_t)leader * kScalTeam;
     __shared__ double s_cv[NB], s_tv[NB], s_yh[NB], s_fac[NB], s_coef[NB];
@@ -418,10 +440,20 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
             PROF_MARK(cx.prof, kPhB1);
             // ---- (T1) S' = T_k^T S for the columns [c0, c1) of this CTA ----
             if (k0 > 0) {
-                for (int64_t q = t; q < c1 * bb; q += B) {
-                    const int64_t l = q / bb;
-                    const int cc = (int)(q % bb);
-                    xs[l * nbs + cc] = sum_partials(teamP + l * NB + cc, pstride, G);
+                if (sliced) {  // S's rows summed once per team, rank r taking a slice of them
+                    if (!reduce_rows(teamP, pstride, G, 0, k0, bb, rank, tm, cx.err, p.spin_limit))
+                        return false;
+                    for (int64_t q = t; q < c1 * bb; q += B) {
+                        const int64_t l = q / bb;
+                        const int cc = (int)(q % bb);
+                        xs[l * nbs + cc] = __ldcg(teamP + l * NB + cc);
+                    }
+                } else {
+                    for (int64_t q = t; q < c1 * bb; q += B) {
+                        const int64_t l = q / bb;
+                        const int cc = (int)(q % bb);
+                        xs[l * nbs + cc] = sum_partials(teamP + l * NB + cc, pstride, G);
+                    }
                 }
                 __syncthreads();
                 PROF_MARK(cx.prof, kPhT1a);
@@ -530,13 +562,17 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
             if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
             PROF_MARK(cx.prof, kPhBa);
             // ---- (T2) T columns k0.. by Eq. cwy1 and X_T = T (rows col of Y) for pass C ----
-            for (int v = wid; v < bb * bb; v += nW) {
+            // Gram rows [0, k0 + bb): summed once per team by slices, or by every CTA
+            double* gsum = teamP + NB * ns;  // rank 0's Gram partials, then the team's sums
+            if (sliced && !reduce_rows(gsum, pstride, G, 0, k0 + bb, bb, rank, tm, cx.err, p.spin_limit))
+                return false;
+            auto gram = [&](int64_t l, int cc) {
+                return sliced ? __ldcg(gsum + l * NB + cc) : sum_partials(gsum + l * NB + cc, pstride, G);
+            };
+            for (int v = t; v < bb * bb; v += B) {
                 const int ca = v / bb, cb = v % bb;
-                const double g = (ca <= cb) ? team_sum_at(teamP, pstride, G, NB * ns + (size_t)(k0 + ca) * NB + cb) : 0.0;
-                if (lane == 0) {
-                    s_g22[ca * NB + cb] = g;
-                    s_yb[ca * NB + cb] = __ldcg(&ybr[ca * NB + cb]);  // y_cb at row k0 + ca
-                }
+                s_g22[ca * NB + cb] = (ca <= cb) ? gram(k0 + ca, cb) : 0.0;
+                s_yb[ca * NB + cb] = __ldcg(&ybr[ca * NB + cb]);  // y_cb at row k0 + ca
             }
             // staged [G12 | R1] for the rows [i0, k0) of T_k, 2 nbs doubles per row (vector
             // v < bb: G12[l, v] = (Y_k^T Y_b)[l, v]; v = bb + c: R1[l, c] = Y[k0 + c, l], row
@@ -544,7 +580,7 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
             for (int64_t q = t; q < (k0 - i0) * bb; q += B) {
                 const int64_t l = i0 + q / bb;
                 const int cc = (int)(q % bb);
-                xs[(l - i0) * 2 * nbs + cc] = sum_partials(teamP + NB * ns + l * NB + cc, pstride, G);
+                xs[(l - i0) * 2 * nbs + cc] = gram(l, cc);
                 xs[(l - i0) * 2 * nbs + bb + cc] = __ldcg(&Yc[(k0 + cc) + l * n]);
             }
             __syncthreads();
