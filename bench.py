@@ -1131,7 +1131,9 @@ def extras():
 # cycles per phase and prints them when the CTA ends)
 # ------------------------------------------------------------------------------------------
 PHASES = ["total", "solve", "A", "b1", "T1red", "T1", "b2", "Bload", "Brow", "Bsum", "B", "b3",
-          "T2refl", "T2red", "T2row", "T2", "b4", "Cload", "Crow", "C", "b5", "load", "end"]
+          "T2refl", "T2red", "T2row", "T2", "b4", "Cload", "Crow", "C", "b5", "load", "end",
+          "sv_stage", "sv_fwd1", "sv_fcarry", "sv_fwd2", "sv_back1", "sv_bfold", "sv_back2",
+          "sv_check"]
 
 
 def _phases_child(args):
@@ -1155,12 +1157,19 @@ def summarize_phases(text: str):
 
     teams = collections.defaultdict(list)
     chain = ""
+    solve = {}
+    for line in text.splitlines():
+        if line.startswith("SPROF "):
+            kv = {k: int(v) for k, v in re.findall(r"(\w+)=(-?\d+)", line)}
+            solve[kv["cta"]] = kv
     for line in text.splitlines():
         if line.startswith("PHASES_MS"):
             chain = line
         if not line.startswith("PROF "):
             continue
         kv = {k: int(v) for k, v in re.findall(r"(\w+)=(-?\d+)", line)}
+        for k, v in solve.get(kv.get("cta"), {}).items():
+            kv.setdefault(k, v)
         if kv.get("team", -1) >= 0:
             teams[(kv["team"], kv["G"])].append(kv)
     by_g = collections.defaultdict(list)

@@ -660,6 +660,24 @@ struct SolveScratch {
     __device__ static constexpr int size(int G) { return kPub + 6 * G + 6 * 32 * NW; }
 };
 
+#ifdef TINV_PHASE_PROFILE
+// Diagnostic build: SM cycles of the 16-warp solve's steps, per CTA (thread 0's timeline).
+constexpr int kSolvePh = 8;
+__device__ unsigned long long g_solve_prof[1024 * kSolvePh];
+#define SOLVE_MARK(i)                                                                    \
+    do {                                                                                 \
+        if (NW == 16 && threadIdx.x == 0) {                                              \
+            const long long _n = clock64();                                              \
+            g_solve_prof[blockIdx.x * kSolvePh + (i)] += (unsigned long long)(_n - _sp); \
+            _sp = _n;                                                                    \
+        }                                                                                \
+    } while (0)
+#else
+#define SOLVE_MARK(i) \
+    do {              \
+    } while (0)
+#endif
+
 template <int NW>
 __device__ __noinline__ bool team_solve_nw(int64_t n, const Fac& f, const double* bsrc, double fac,
                                            double* vsm, double* vout, double* ysave, int64_t r0,
@@ -678,11 +696,15 @@ __device__ __noinline__ bool team_solve_nw(int64_t n, const Fac& f, const double
     const int64_t lo = r0 + (int64_t)t * L;
     const int64_t hi = (t < Pn) ? min(r1, lo + L) : lo;
     const bool act = (t < Pn) && (lo < hi);
+#ifdef TINV_PHASE_PROFILE
+    long long _sp = clock64();
+#endif
 
     // stage b (scaled) for the own rows and the first row of the next CTA
     const int64_t send = min(r1 + 1, n);
     for (int64_t k = r0 + t; k < send; k += B) vsm[k] = bsrc[k] * fac;
     __syncthreads();
+    SOLVE_MARK(0);
 
     // ---------------- forward (P, L) ----------------
     double A = 1.0, Bf = 0.0, bnext = 0.0;
@@ -724,6 +746,7 @@ __device__ __noinline__ bool team_solve_nw(int64_t n, const Fac& f, const double
         }
     }
     __syncthreads();
+    SOLVE_MARK(1);
     if (t == 0 && tr.G > 1) {
         double CA = 1.0, CB = 0.0;
         for (int w2 = 0; w2 < NW; ++w2) {
@@ -754,6 +777,7 @@ __device__ __noinline__ bool team_solve_nw(int64_t n, const Fac& f, const double
         }
     }
     __syncthreads();
+    SOLVE_MARK(2);
     if (act) {
         double c = fma(ea, sh[SS::kCarry + wid], eb);
         for (int64_t k = lo; k < hi; ++k) {
@@ -773,6 +797,7 @@ __device__ __noinline__ bool team_solve_nw(int64_t n, const Fac& f, const double
         }
     }
     __syncthreads();
+    SOLVE_MARK(3);
 
     // ---------------- back substitution (U) ----------------
     // chunk map: (x_lo, x_lo+1) = M (x_hi, x_hi+1) + f
@@ -834,6 +859,7 @@ __device__ __noinline__ bool team_solve_nw(int64_t n, const Fac& f, const double
         }
     }
     __syncthreads();
+    SOLVE_MARK(4);
     if (t == 0 && tr.G > 1) {
         double c00 = 1.0, c01 = 0.0, c10 = 0.0, c11 = 1.0, c0 = 0.0, c1 = 0.0;
         for (int w2 = NW - 1; w2 >= 0; --w2) {  // CTA map = W_0 o W_1 o W_2 o W_3
@@ -860,42 +886,62 @@ __device__ __noinline__ bool team_solve_nw(int64_t n, const Fac& f, const double
     for (int q = tr.rank + 1 + t; q < tr.G; q += B)
         for (int u = 0; u < 6; ++u) pb[6 * q + u] = __ldcg(&pubb[6 * q + u]);
     __syncthreads();
-    if (t == 0) {
+    // Value folds: a map applied to (s0, s1) gives n_h = fma(M[h][0], s0, fma(M[h][1], s1, f_h))
+    // for h = 0, 1.  An FP64 instruction costs the FP64 pipe a whole warp's slot however few of
+    // its lanes are active, so each fold runs on a lane pair (lane 2v + h computes n_h of fold v)
+    // that swaps its two values by a shuffle: half the instructions of one lane computing both.
+    if (t < 2) {  // the boundary values entering each warp, from the CTAs below and the warps
+        const int h = t;
         double s0 = 0.0, s1 = 0.0;  // x_n = x_{n+1} = 0 below the last CTA
         for (int q = tr.G - 1; q > tr.rank; --q) {
             const double* o = pb + 6 * q;
-            const double n0 = fma(o[0], s0, fma(o[1], s1, o[4]));
-            const double n1 = fma(o[2], s0, fma(o[3], s1, o[5]));
-            s0 = n0;
-            s1 = n1;
+            const double nv = fma(o[2 * h], s0, fma(o[2 * h + 1], s1, o[4 + h]));
+            const double ov = __shfl_xor_sync(0x3u, nv, 1);
+            s0 = h ? ov : nv;
+            s1 = h ? nv : ov;
         }
         for (int w2 = NW - 1; w2 >= 0; --w2) {
-            sh[SS::kEnter + 2 * w2] = s0;
-            sh[SS::kEnter + 2 * w2 + 1] = s1;
+            sh[SS::kEnter + 2 * w2 + h] = h ? s1 : s0;
             const double* o = sh + SS::kWarp + 6 * w2;
-            const double n0 = fma(o[0], s0, fma(o[1], s1, o[4]));
-            const double n1 = fma(o[2], s0, fma(o[3], s1, o[5]));
-            s0 = n0;
-            s1 = n1;
+            const double nv = fma(o[2 * h], s0, fma(o[2 * h + 1], s1, o[4 + h]));
+            const double ov = __shfl_xor_sync(0x3u, nv, 1);
+            s0 = h ? ov : nv;
+            s1 = h ? nv : ov;
         }
     }
     __syncthreads();
-    // each warp's first lane folds the warp's chunk maps as values, from the warp's boundary
-    // values upwards; chunk p receives (x_hi, x_hi+1) in its slots 0 and 1
-    if (part && lane == 0) {
-        double s0 = sh[SS::kEnter + 2 * wid], s1 = sh[SS::kEnter + 2 * wid + 1];
-        for (int l = 31; l >= 0; --l) {
-            double* o = cm + 6 * (32 * wid + l);
-            const double q00 = o[0], q01 = o[1], q10 = o[2], q11 = o[3], q0 = o[4], q1 = o[5];
-            o[0] = s0;
-            o[1] = s1;
-            const double n0 = fma(q00, s0, fma(q01, s1, q0));
-            const double n1 = fma(q10, s0, fma(q11, s1, q1));
-            s0 = n0;
-            s1 = n1;
+    // the chunk maps of each warp folded as values, from the warp's boundary values upwards
+    // (chunk p receives (x_hi, x_hi+1) in its slots 0 and 1): warp 0 folds 16 warps at once,
+    // on the lane pair 2v, 2v + 1 for warp v
+    if (wid == 0) {
+        const int h = lane & 1;
+        for (int v0 = 0; v0 < NW; v0 += 16) {
+            const int v = v0 + (lane >> 1);
+            const bool on = v < NW;
+            double s0 = 0.0, s1 = 0.0;
+            if (on) {
+                s0 = sh[SS::kEnter + 2 * v];
+                s1 = sh[SS::kEnter + 2 * v + 1];
+            }
+            for (int l = 31; l >= 0; --l) {
+                double* o = cm + 6 * (32 * v + l);
+                double qa = 0.0, qb = 0.0, qc = 0.0;
+                if (on) {
+                    qa = o[2 * h];
+                    qb = o[2 * h + 1];
+                    qc = o[4 + h];
+                }
+                const double nv = fma(qa, s0, fma(qb, s1, qc));
+                __syncwarp();  // both lanes of the pair have read the map before it is overwritten
+                if (on) o[h] = h ? s1 : s0;
+                const double ov = __shfl_xor_sync(0xffffffffu, nv, 1);
+                s0 = h ? ov : nv;
+                s1 = h ? nv : ov;
+            }
         }
     }
-    __syncwarp();
+    __syncthreads();
+    SOLVE_MARK(5);
     double ysv0 = 0.0, ysv1 = 0.0;  // forward results of rows hi-1, hi-2
     if (act) {
         double cur = cm[6 * t], nxt = cm[6 * t + 1];
@@ -912,6 +958,7 @@ __device__ __noinline__ bool team_solve_nw(int64_t n, const Fac& f, const double
         }
     }
     __syncthreads();
+    SOLVE_MARK(6);
 
     // ---------------- consistency at the chunk boundaries ----------------
     // The rows below a CTA's last chunk belong to the next CTA: read them once all are written.
@@ -931,6 +978,7 @@ __device__ __noinline__ bool team_solve_nw(int64_t n, const Fac& f, const double
     __syncthreads();
     if (bad) atomicMax(&s_top, (unsigned long long)hi);
     bool fallback = __syncthreads_or(bad) != 0;
+    SOLVE_MARK(7);
     int64_t top = (int64_t)s_top;
 #ifdef TINV_PHASE_PROFILE
     if (bad) {

@@ -1419,6 +1419,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t
         if (!ok) return;
     }
 #ifdef TINV_PHASE_PROFILE
+    if (t == 0) {
+        const unsigned long long* sp = g_solve_prof + (size_t)b * kSolvePh;
+        printf("SPROF cta=%d team=%d G=%d sv_stage=%llu sv_fwd1=%llu sv_fcarry=%llu sv_fwd2=%llu sv_back1=%llu "
+               "sv_bfold=%llu sv_back2=%llu sv_check=%llu\n",
+               b, tc, tg, sp[0], sp[1], sp[2], sp[3], sp[4], sp[5], sp[6], sp[7]);
+    }
     if (t == 0)
         printf("PROF cta=%d team=%d G=%d total=%lld load=%llu solve=%llu A=%llu b1=%llu T1red=%llu T1=%llu "
                "b2=%llu Bload=%llu Brow=%llu Bsum=%llu B=%llu b3=%llu T2refl=%llu T2red=%llu T2row=%llu "
