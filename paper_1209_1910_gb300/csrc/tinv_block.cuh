@@ -507,19 +507,23 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
                     if (lane == 0) red[v] = s;
                 }
                 __syncthreads();
-                if (t == 0) {
+                if (wid == 0) {  // every lane forms the scalars (a warp costs what one lane does)
                     const double nrm = sqrt(red[0]);
                     const bool broke = !(nrm > 0.0) || !isfinite(nrm);
                     const double u1 = red[bb - cc];
                     const double cv = broke ? -1.0 : -sgn(u1) * nrm;
                     const double ue = broke ? 1.0 : u1;
                     const double tv = 1.0 / (cv * cv - ue * cv);
-                    s_cv[cc] = cv;
-                    s_tv[cc] = tv;
-                    s_yh[cc] = ue - cv;
-                    s_broke[cc] = broke ? 1 : 0;
-                    // y^T w_{cc+v} = (w_cc - c e_col)^T w_{cc+v}, or 2 w_{cc+v}[col] after a breakdown
-                    for (int v = 1; v < bb - cc; ++v) {
+                    if (lane == 0) {
+                        s_cv[cc] = cv;
+                        s_tv[cc] = tv;
+                        s_yh[cc] = ue - cv;
+                        s_broke[cc] = broke ? 1 : 0;
+                    }
+                    // lane v: y^T w_{cc+v} = (w_cc - c e_col)^T w_{cc+v}, or 2 w_{cc+v}[col] after a
+                    // breakdown
+                    const int v = lane;
+                    if (v >= 1 && v < bb - cc) {
                         const double hv = red[bb - cc + v];
                         s_coef[cc + v] = tv * (broke ? 2.0 * hv : red[v] - cv * hv);
                     }
@@ -694,15 +698,17 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
             }
             __syncthreads();
             // convergence test on x_c = -c_c q_c (||x||_inf = |c_c| max|q_c|), per member
-            if (t == 0) {
-                int all = 1;
-                for (int cc = 0; cc < bb; ++cc) {
+            if (wid == 0) {  // lane cc tests member cc
+                const int cc = lane;
+                bool done = true;
+                if (cc < bb) {
                     if (!s_broke[cc] && fabs(s_cv[cc]) * s_stat[NB + cc] >= dtpcrt) ++s_chk[cc];
-                    if (s_chk[cc] < kExtra + 1) all = 0;
+                    done = s_chk[cc] >= kExtra + 1;
                     const int64_t j = s0 + mem0 + mstride * cc;
                     s_fac[cc] = -sgn(s_cv[cc]) * (((double)n * onenrm) * fmax(kEps, w.u0n[j])) / s_stat[cc];
                 }
-                s_b[3] = all ? 1.0 : 0.0;
+                const bool all = __all_sync(0xffffffffu, done);
+                if (lane == 0) s_b[3] = all ? 1.0 : 0.0;
             }
             __syncthreads();
             if (s_b[3] != 0.0 || its == maxits) {
