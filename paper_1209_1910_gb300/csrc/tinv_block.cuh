@@ -238,6 +238,8 @@ __device__ __forceinline__ double team_sum_at(const double* base, size_t stride,
 // Teams at least this large sum the partials of S and of the Gram rows once per team (rank r
 // a slice of the rows, then a team barrier) instead of on every CTA.
 constexpr int kSliceBlock = 8;
+// Fixed cost of a row of the T products (their lane-group reductions), in columns.
+constexpr double kRowCost = 16.0;
 
 // The team's sums of the partial rows [l0, l1) x nv (NB doubles per row, ranks `stride` apart,
 // in rank order) written over rank 0's partials, rank `rank` summing its slice of the rows;
@@ -377,12 +379,17 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
         if (t == 0) {
             s_rows[0] = part_lo(k0, n, rank, G);       // panel rows
             s_rows[1] = part_lo(k0, n, rank + 1, G);
-            s_rows[2] = trap_row_lo(n, kb, rank, G);   // rows of passes A and C
-            s_rows[3] = trap_row_lo(n, kb, rank + 1, G);
+            // rows of passes A and C: ranges of equal cost (a short row of the triangle costs
+            // its length plus kb / 4, the measured slowdown of short rows) when the largest
+            // range (rank 0's) still lets pass A stage its V rows, equal rows otherwise
+            const double c0 = 0.25 * (double)kb;
+            const bool by_cost = (int64_t)bb * trap_row_lo(n, kb, 1, G, c0) <= 2 * n;
+            s_rows[2] = trap_row_lo(n, kb, rank, G, by_cost ? c0 : -1.0);
+            s_rows[3] = trap_row_lo(n, kb, rank + 1, G, by_cost ? c0 : -1.0);
             s_rows[4] = tri_col_lo(k0, rank, G);       // columns of T^T s
             s_rows[5] = tri_col_lo(k0, rank + 1, G);
-            s_rows[6] = tri_row_lo(k0, rank, G);       // rows of the T products
-            s_rows[7] = tri_row_lo(k0, rank + 1, G);
+            s_rows[6] = tri_row_lo_c(k0, rank, G, kRowCost);      // rows of the T products
+            s_rows[7] = tri_row_lo_c(k0, rank + 1, G, kRowCost);
         }
         if (t < NB) s_chk[t] = 0;
         __syncthreads();

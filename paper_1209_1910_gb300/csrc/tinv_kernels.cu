@@ -789,22 +789,29 @@ __device__ __forceinline__ int64_t part_lo(int64_t a, int64_t b, int r, int G)
 }
 
 // Rows of passes A and C for rank r of G: the n rows of a lower trapezoid with K columns (row
-// rho holds min(rho+1, K) of them).  While the triangle is a small part (4K <= n) equal rows
-// are used (short rows run less efficiently, so their smaller work does not make them cheaper);
-// beyond that, ranges of equal work.
-__device__ __forceinline__ int64_t trap_row_lo(int64_t n, int64_t K, int r, int G)
+// rho holds min(rho+1, K) of them).  For the one-member passes, while the triangle is a small
+// part (4K <= n), equal rows are used (their short rows run less efficiently, so the smaller
+// work does not make them cheaper); beyond that, ranges of equal work.  With c0 >= 0 (the
+// multi-vector passes of the blocked path) always ranges of equal cost, a row costing
+// min(rho+1, K) + c0.
+__device__ __forceinline__ int64_t trap_row_lo(int64_t n, int64_t K, int r, int G, double c0 = -1.0)
 {
     if (r <= 0) return 0;
     if (r >= G) return n;
-    if (4 * K <= n) return (n * r) / G;
-    const double Kd = (double)K, tri = 0.5 * Kd * (Kd + 1.0);
-    const double total = tri + (double)(n - K) * Kd;
+    if (c0 < 0.0) {
+        if (4 * K <= n) return (n * r) / G;
+        c0 = 0.0;
+    }
+    const double Kd = (double)K, head = 0.5 * Kd * (Kd + 1.0) + c0 * Kd;
+    const double total = head + (double)(n - K) * (Kd + c0);
     const double tgt = total * (double)r / (double)G;
     int64_t rho;
-    if (tgt <= tri)
-        rho = (int64_t)llrint(0.5 * (sqrt(8.0 * tgt + 1.0) - 1.0));
-    else
-        rho = K + (int64_t)llrint((tgt - tri) / Kd);
+    if (tgt <= head) {
+        const double b1 = 1.0 + 2.0 * c0;
+        rho = (int64_t)llrint(0.5 * (sqrt(b1 * b1 + 8.0 * tgt) - b1));
+    } else {
+        rho = K + (int64_t)llrint((tgt - head) / (Kd + c0));
+    }
     return min(n, max((int64_t)0, rho));
 }
 
@@ -821,6 +828,17 @@ __device__ __forceinline__ int64_t tri_row_lo(int64_t k, int r, int G)
     if (r <= 0) return 0;
     if (r >= G) return k;
     return max((int64_t)0, k - (int64_t)llrint((double)k * sqrt(1.0 - (double)r / (double)G)));
+}
+// The same with a fixed cost of c0 columns per row (work k - i + c0): the rank with the short
+// bottom rows gets fewer of them.  Cumulative work i (k + c0 + 1/2) - i^2 / 2 = its share.
+__device__ __forceinline__ int64_t tri_row_lo_c(int64_t k, int r, int G, double c0)
+{
+    if (r <= 0) return 0;
+    if (r >= G) return k;
+    const double kd = (double)k, bq = 2.0 * kd + 2.0 * c0 + 1.0;
+    const double tgt = (0.5 * kd * (kd + 1.0) + c0 * kd) * (double)r / (double)G;
+    const double i = 0.5 * (bq - sqrt(fmax(0.0, bq * bq - 8.0 * tgt)));
+    return min(k, max((int64_t)0, (int64_t)llrint(i)));
 }
 
 __device__ __forceinline__ int solve_group_size(int64_t n)
