@@ -64,7 +64,9 @@ DRIVER_EXTRA_LAUNCHES = {"split4200": 3, "bidiag2000": 3}
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (vector and tensor alike), TFLOP/s
 # DRAM bytes (read + write) of one cluster-kernel launch, from one ncu capture of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum); None where no capture exists
-TRAFFIC_BYTES = {("glued4200", "cwy"): 33.09e9}
+# DRAM bytes of one k_chain launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass),
+# by workload, method and block; None for a configuration not captured with the current kernel
+TRAFFIC_BYTES = {("glued4200", "cwy", 16): 18.58e9}
 
 
 def parse():
@@ -995,7 +997,7 @@ def ours_arm(args):
     achieved = flops / (kern_ms * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": TRAFFIC_BYTES.get((args.workload, args.method)), "kernel": "k_chain",
+            "traffic": TRAFFIC_BYTES.get((args.workload, args.method, args.block)), "kernel": "k_chain",
             "kernel_ms": kern_ms, "flops_per_launch": flops,
             "peak_source": "nominal GB300 FP64: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz = 1.26 TFLOP/s",
             "phase_ms": {"plan": float(phase[0]), "lu": float(phase[1]),
