@@ -1041,45 +1041,54 @@ def ours_arm(args):
                       "h2d_bytes_per_step": (n + (n - 1) + m) * 8,
                       "d2h_bytes_per_step": n * m * 8 + m * 4 + 64}
 
-    # the MGS comparison on the same workload (Alg. 1 on the GPU), fewer steps
+    # the MGS comparison on the same workload (Alg. 1 on the GPU), fewer steps.  On the n = 10^4
+    # workloads (one cluster of ~10^4 members) MGS would need about ten minutes on its one CTA,
+    # so both methods run on the first SUB eigenvalues of the same matrix (a cluster of SUB
+    # members)
     if not args.no_compare and args.method == "cwy" and world == 1:
-        step("mgs", False)
-        torch.cuda.synchronize()
-        ms = []
-        for _ in range(2):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(st)
-            step("mgs", False)
-            b.record(st)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
+        SUB = 500
+        msub = m if m <= 5000 else SUB
+        tw_c, Z_c = tw[:msub], Zt[:msub]
+
+        def step_c(method, block):
+            binding.tinv_device(td, te, tw_c, Z_c, method=method, workspace=ws, iters=iters[:msub],
+                                info=info, counters=counters.data_ptr(),
+                                block=block if method == "cwy" else 0)
+
+        def timed_c(method, block):
+            step_c(method, block)
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(2):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                step_c(method, block)
+                b.record(st)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            return statistics.mean(ms)
+
+        t_mgs = timed_c("mgs", 0)
         ncl = int(counters[1].item())  # clusters with >= 2 members (MGS: one CTA each)
         P = torch.cuda.get_device_properties(dev).multi_processor_count
-        out["compare"] = {"mgs": {"value": m / (statistics.mean(ms) * 1e-3),
-                                  "ms_per_step": statistics.mean(ms),
+        out["compare"] = {"mgs": {"value": msub / (t_mgs * 1e-3), "ms_per_step": t_mgs,
                                   "ctas": "one CTA per cluster: %d clusters on %d of the %d CTAs "
                                           "of the persistent grid (compact WY spreads each "
                                           "cluster over a CTA team)" % (ncl, min(ncl, P), P)}}
+        if msub < m:
+            t_cwy = timed_c("cwy", blk)
+            out["compare"]["subset"] = ("the first %d of the %d eigenvalues, both methods (MGS on "
+                                        "the whole matrix would take about ten minutes)" % (msub, m))
+            out["compare"]["cwy"] = {"value": msub / (t_cwy * 1e-3), "ms_per_step": t_cwy,
+                                     "block": blk}
         # the other form of compact WY on the same workload: one member at a time (Alg. 4 as
         # printed) when the line measures blocks, blocks of 16 otherwise
         other = 0 if blk >= 2 else 16
-        step("cwy", False, block=other)
-        torch.cuda.synchronize()
-        ms = []
-        for _ in range(2):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(st)
-            step("cwy", False, block=other)
-            b.record(st)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
+        t_oth = timed_c("cwy", other)
         out["compare"]["cwy_one_member" if other == 0 else "cwy_block16"] = {
-            "value": m / (statistics.mean(ms) * 1e-3), "ms_per_step": statistics.mean(ms),
-            "block": other}
+            "value": msub / (t_oth * 1e-3), "ms_per_step": t_oth, "block": other}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc = cpu_sample(args.workload, args.method, d, e, w)

@@ -25,6 +25,12 @@ struct XCol {
     int64_t ld, off;
     __device__ __forceinline__ double operator()(int64_t idx, int c) const { return p[c * ld + idx - off]; }
 };
+// Row-major vectors in global memory written by other CTAs (read through L2): p[idx * ld + c].
+struct XGRow {
+    const double* p;
+    int64_t ld;
+    __device__ __forceinline__ double operator()(int64_t idx, int c) const { return __ldcg(p + idx * ld + c); }
+};
 // Column vectors in global memory written by other CTAs (read through L2): base + c * ld + idx.
 struct XGlob {
     const double* base;
@@ -114,6 +120,9 @@ __device__ __noinline__ void mv_coldots(const double* __restrict__ A, int64_t ld
 // [r0, r1) and vectors c < nv, C(rho) as cta_rowdots (LOWERCOL: [0, min(ccap, rho + 1)),
 // UPPERCOL: [rho, ccap), ALL: [0, ccap)).  A warp takes RL consecutive rows x 32/RL column
 // phases; column ranges are split into segments when the rows alone do not fill the warps.
+// The lanes of a row group step through the same columns (for UPPERCOL from the group's first
+// row, the entries left of a lane's own row masked), so that each load of A is RL consecutive
+// doubles of one column and each x_c[i] one broadcast value.
 template <int RL, int KIND, int NV, class XF, class Out>
 __device__ __noinline__ void mv_rowdots_rl(const double* __restrict__ A, int64_t lda, int64_t r0, int64_t r1,
                                            int64_t ccap, XF xf, int nv, double* red, Out out)
@@ -140,7 +149,7 @@ __device__ __noinline__ void mv_rowdots_rl(const double* __restrict__ A, int64_t
         int64_t a = 0, b = 0;
         if (act) {
             const int64_t s0 = gb + sg * seglen, s1 = min(ge, s0 + seglen);
-            const int64_t cb = (KIND == kUpperCol) ? rho : 0;
+            const int64_t cb = (KIND == kUpperCol) ? r0 + g * RL : 0;  // the group's first row
             const int64_t ce = (KIND == kLowerCol) ? min(ccap, rho + 1) : ccap;
             a = max(s0, cb);
             b = min(s1, ce);
@@ -150,15 +159,17 @@ __device__ __noinline__ void mv_rowdots_rl(const double* __restrict__ A, int64_t
         for (int c = 0; c < NV; ++c) acc[c] = 0.0;
         if (act && a < b) {
             const double* row = A + rho;
+            // UPPERCOL: columns i < rho of this lane's row are not its terms (masked to 0)
+            auto ld = [&](int64_t i) { return (KIND != kUpperCol || i >= rho) ? row[i * lda] : 0.0; };
             int64_t i = a + (((int64_t)ph - a) % CL + CL) % CL;
             for (; i + CL < b; i += 2 * CL) {
-                const double y0 = row[i * lda], y1 = row[(i + CL) * lda];
+                const double y0 = ld(i), y1 = ld(i + CL);
 #pragma unroll
                 for (int c = 0; c < NV; ++c)
                     if (c < nv) acc[c] = fma(y1, xf(i + CL, c), fma(y0, xf(i, c), acc[c]));
             }
             if (i < b) {
-                const double y0 = row[i * lda];
+                const double y0 = ld(i);
 #pragma unroll
                 for (int c = 0; c < NV; ++c)
                     if (c < nv) acc[c] = fma(y0, xf(i, c), acc[c]);
@@ -191,7 +202,8 @@ template <int KIND, int NV, class XF, class Out>
 __device__ __forceinline__ void mv_rowdots_nv(const double* __restrict__ A, int64_t lda, int64_t r0, int64_t r1,
                                               int64_t ccap, XF xf, int nv, double* red, Out out)
 {
-    if (r1 - r0 > 64)
+    // groups of 8 rows x 4 column phases unless the rows alone give every warp two groups of 32
+    if (r1 - r0 > 1024)
         mv_rowdots_rl<32, KIND, NV>(A, lda, r0, r1, ccap, xf, nv, red, out);
     else
         mv_rowdots_rl<8, KIND, NV>(A, lda, r0, r1, ccap, xf, nv, red, out);
@@ -257,6 +269,12 @@ __device__ __forceinline__ bool reduce_rows(double* base, size_t stride, int G, 
     return team_sync(tm.bar, tm.target, G, err, limit);
 }
 
+// The block's staged vectors fit the shared-memory staging area.
+__device__ __forceinline__ bool staging_fits(const Ws& w, int64_t mc, int nb)
+{
+    return (int64_t)2 * nb * mc <= w.xcap && (int64_t)nb * (mc + nb) <= w.xcap;
+}
+
 // Members per block the blocked path uses for a cluster of mc members on a team of G CTAs
 // (1: the cluster takes the one-member path).
 __device__ __forceinline__ int block_members(const Ws& w, int64_t mc, int G)
@@ -266,9 +284,12 @@ __device__ __forceinline__ int block_members(const Ws& w, int64_t mc, int G)
     // buffer holds bb (n/G + 1) <= 2 n + 64 doubles
     int nb = min(w.block, 2 * G);
     // staged vectors in shared memory, nb doubles per row: 2 nb mc for the T products, nb (mc + nb)
-    // for pass C; the block is halved until they fit
-    while (nb >= 2 && ((int64_t)2 * nb * mc > w.xcap || (int64_t)nb * (mc + nb) > w.xcap)) nb >>= 1;
-    if (nb < 2) return 1;
+    // for pass C.  Teams of kSliceBlock or more CTAs read them from the team's buffers in global
+    // memory (L2) when they do not fit; smaller teams halve the block until they fit.
+    if (G < kSliceBlock) {
+        while (nb >= 2 && !staging_fits(w, mc, nb)) nb >>= 1;
+        if (nb < 2) return 1;
+    }
     // the CTA-local solves use the staging area as their scratch
     if (w.xcap < SolveScratch<16>::size(1) || w.xcap < 6 * kStageRows) return 1;
     return nb;
@@ -311,7 +332,11 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
     double* W = cx.vsm;                        // this CTA's panel rows, column c at + c Rb
     double* xs = cx.xs;                        // staged vectors, nbs doubles per row
     const int nbs = nb;
-    const bool sliced = G >= kSliceBlock;      // team sums of S and the Gram rows by slices
+    // gst: the staged vectors are read from the team's buffers in L2 (the cluster is too large
+    // for the shared-memory staging); the team sums of S and the Gram rows are then always
+    // formed by slices, so that they exist in global memory
+    const bool gst = !staging_fits(w, mc, nb);
+    const bool sliced = G >= kSliceBlock || gst;  // team sums of S and the Gram rows by slices
     double* red = cx.red;
     double* scal_t = w.partScal + (size_t)leader * kScalTeam;
     __shared__ double s_cv[NB], s_tv[NB], s_yh[NB], s_fac[NB], s_coef[NB];
@@ -323,8 +348,7 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
     if (!TINV_IN(s0 >= 0 && mc >= 1 && s0 + mc <= w.nM && n <= p.n && rank < G && leader + G <= w.P &&
                      dbg_range((int64_t)jr.off, (int64_t)jr.off + mc * n, w.nF) &&
                      dbg_range(w.cltoff[c], w.cltoff[c] + mc * mc, w.nTT) &&
-                     nb >= 2 && nb <= NB && nb <= 2 * G && (int64_t)2 * nb * mc <= w.xcap &&
-                     (int64_t)nb * (mc + nb) <= w.xcap &&
+                     nb >= 2 && nb <= NB && nb <= 2 * G && (staging_fits(w, mc, nb) || G >= kSliceBlock) &&
                      (p.zlen == 0 || dbg_range(sg.z + jr.jl * ldz, sg.z + (jr.jl + mc - 1) * ldz + n, p.zlen)),
                  cx.err))
         return false;
@@ -380,9 +404,9 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
             s_rows[0] = part_lo(k0, n, rank, G);       // panel rows
             s_rows[1] = part_lo(k0, n, rank + 1, G);
             // rows of passes A and C: ranges of equal cost (a short row of the triangle costs
-            // its length plus kb / 4, the measured slowdown of short rows) when the largest
+            // its length plus min(kb / 4, 128), the measured slowdown of short rows) when the largest
             // range (rank 0's) still lets pass A stage its V rows, equal rows otherwise
-            const double c0 = 0.25 * (double)kb;
+            const double c0 = fmin(0.25 * (double)kb, 128.0);
             const bool by_cost = (int64_t)bb * trap_row_lo(n, kb, 1, G, c0) <= 2 * n;
             s_rows[2] = trap_row_lo(n, kb, rank, G, by_cost ? c0 : -1.0);
             s_rows[3] = trap_row_lo(n, kb, rank + 1, G, by_cost ? c0 : -1.0);
@@ -450,11 +474,12 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
                 if (sliced) {  // S's rows summed once per team, rank r taking a slice of them
                     if (!reduce_rows(teamP, pstride, G, 0, k0, bb, rank, tm, cx.err, p.spin_limit))
                         return false;
-                    for (int64_t q = t; q < c1 * bb; q += B) {
-                        const int64_t l = q / bb;
-                        const int cc = (int)(q % bb);
-                        xs[l * nbs + cc] = __ldcg(teamP + l * NB + cc);
-                    }
+                    if (!gst)
+                        for (int64_t q = t; q < c1 * bb; q += B) {
+                            const int64_t l = q / bb;
+                            const int cc = (int)(q % bb);
+                            xs[l * nbs + cc] = __ldcg(teamP + l * NB + cc);
+                        }
                 } else {
                     for (int64_t q = t; q < c1 * bb; q += B) {
                         const int64_t l = q / bb;
@@ -464,14 +489,17 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
                 }
                 __syncthreads();
                 PROF_MARK(cx.prof, kPhT1a);
-                mv_coldots_fit<kUpper, NB>(Tc, ldt, c0, c1, 0, k0, XRow{xs, nbs}, bb, red,
-                                       [&](int64_t i, int cc, double v) { sP[i * NB + cc] = v; });
+                auto outT1 = [&](int64_t i, int cc, double v) { sP[i * NB + cc] = v; };
+                if (gst)
+                    mv_coldots_fit<kUpper, NB>(Tc, ldt, c0, c1, 0, k0, XGRow{teamP, NB}, bb, red, outT1);
+                else
+                    mv_coldots_fit<kUpper, NB>(Tc, ldt, c0, c1, 0, k0, XRow{xs, nbs}, bb, red, outT1);
             }
             PROF_MARK(cx.prof, kPhT1);
             if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
             PROF_MARK(cx.prof, kPhB2);
             // ---- (B) panel rows of W = V - Y_k S' (this CTA's rows [rb0, rb1) of [k0, n)) ----
-            if (k0 > 0)
+            if (k0 > 0 && !gst)
                 for (int64_t q = t; q < k0 * bb; q += B) {
                     const int64_t l = q / bb;
                     const int cc = (int)(q % bb);
@@ -483,9 +511,13 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
                 W[cc * Rb + (r - rb0)] = vsrc(r, cc);
             }
             __syncthreads();
-            if (k0 > 0)
-                mv_rowdots<kAllCols, NB>(Yc, n, rb0, rb1, k0, XRow{xs, nbs}, bb, red,
-                                         [&](int64_t r, int cc, double v) { W[cc * Rb + (r - rb0)] -= v; });
+            if (k0 > 0) {
+                auto outB = [&](int64_t r, int cc, double v) { W[cc * Rb + (r - rb0)] -= v; };
+                if (gst)
+                    mv_rowdots<kAllCols, NB>(Yc, n, rb0, rb1, k0, XGRow{sP, NB}, bb, red, outB);
+                else
+                    mv_rowdots<kAllCols, NB>(Yc, n, rb0, rb1, k0, XRow{xs, nbs}, bb, red, outB);
+            }
             PROF_MARK(cx.prof, kPhBb);
             // ---- (QR) Householder QR of the panel, one column (and team barrier) at a time ----
             for (int cc = 0; cc < bb; ++cc) {
@@ -588,12 +620,13 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
             // staged [G12 | R1] for the rows [i0, k0) of T_k, 2 nbs doubles per row (vector
             // v < bb: G12[l, v] = (Y_k^T Y_b)[l, v]; v = bb + c: R1[l, c] = Y[k0 + c, l], row
             // k0 + c of Y_k)
-            for (int64_t q = t; q < (k0 - i0) * bb; q += B) {
-                const int64_t l = i0 + q / bb;
-                const int cc = (int)(q % bb);
-                xs[(l - i0) * 2 * nbs + cc] = gram(l, cc);
-                xs[(l - i0) * 2 * nbs + bb + cc] = __ldcg(&Yc[(k0 + cc) + l * n]);
-            }
+            if (!gst)
+                for (int64_t q = t; q < (k0 - i0) * bb; q += B) {
+                    const int64_t l = i0 + q / bb;
+                    const int cc = (int)(q % bb);
+                    xs[(l - i0) * 2 * nbs + cc] = gram(l, cc);
+                    xs[(l - i0) * 2 * nbs + bb + cc] = __ldcg(&Yc[(k0 + cc) + l * n]);
+                }
             __syncthreads();
             PROF_MARK(cx.prof, kPhT2b);
             // T_22 by the recurrence of Eq. cwy1 inside the block: T22[ca, cb] = -t_cb
@@ -611,11 +644,16 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
             }
             // rows [i0, i1) of T_k times G12 (into tP) and times R1 (into xT)
             if (k0 > 0 && i1 > i0) {
-                const double* xg = xs - i0 * 2 * nbs;
-                mv_rowdots<kUpperCol, NB>(Tc, ldt, i0, i1, k0, XRow{xg, 2 * nbs}, bb, red,
-                                          [&](int64_t i, int v, double a) { tP[i * NB + v] = a; });
-                mv_rowdots<kUpperCol, NB>(Tc, ldt, i0, i1, k0, XRow{xg + bb, 2 * nbs}, bb, red,
-                                          [&](int64_t i, int v, double a) { xT[i * NB + v] = a; });
+                auto outP = [&](int64_t i, int v, double a) { tP[i * NB + v] = a; };
+                auto outX = [&](int64_t i, int v, double a) { xT[i * NB + v] = a; };
+                if (gst) {  // G12 from the team's sums, R1[l, c] = Y[k0 + c, l]
+                    mv_rowdots<kUpperCol, NB>(Tc, ldt, i0, i1, k0, XGRow{gsum, NB}, bb, red, outP);
+                    mv_rowdots<kUpperCol, NB>(Tc, ldt, i0, i1, k0, XGRow{Yc + k0, n}, bb, red, outX);
+                } else {
+                    const double* xg = xs - i0 * 2 * nbs;
+                    mv_rowdots<kUpperCol, NB>(Tc, ldt, i0, i1, k0, XRow{xg, 2 * nbs}, bb, red, outP);
+                    mv_rowdots<kUpperCol, NB>(Tc, ldt, i0, i1, k0, XRow{xg + bb, 2 * nbs}, bb, red, outX);
+                }
             }
             __syncthreads();
             PROF_MARK(cx.prof, kPhT2c);
@@ -629,14 +667,17 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
                 double a = 0.0;
                 for (int l = 0; l <= cc; ++l) a = fma(__ldcg(&tP[i * NB + l]), s_t22[l * NB + cc], a);
                 Tc[i + (k0 + cc) * ldt] = -a;
-                t12s[(i - i0) * nbs + cc] = -a;
+                if (!gst) t12s[(i - i0) * nbs + cc] = -a;
             }
             __syncthreads();
             for (int64_t q = t; q < (i1 - i0) * bb; q += B) {
                 const int64_t i = i0 + q / bb;
                 const int cc = (int)(q % bb);
                 double a = __ldcg(&xT[i * NB + cc]);
-                for (int c2 = 0; c2 <= cc; ++c2) a = fma(t12s[(i - i0) * nbs + c2], s_yb[cc * NB + c2], a);
+                for (int c2 = 0; c2 <= cc; ++c2) {
+                    const double t12 = gst ? __ldcg(&Tc[i + (k0 + c2) * ldt]) : t12s[(i - i0) * nbs + c2];
+                    a = fma(t12, s_yb[cc * NB + c2], a);
+                }
                 xT[i * NB + cc] = a;
             }
             if (rank == 0 && t < bb * bb) {
@@ -652,16 +693,20 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
             if (!team_sync(tm.bar, tm.target, G, cx.err, p.spin_limit)) return false;
             PROF_MARK(cx.prof, kPhB4);
             // ---- (C) q_c = (Y T Y^T - I) e_{k0+c} = Y_{kb} X_T[:, c] - e_{k0+c}, rows [rc0, rc1) ----
-            for (int64_t q = t; q < kb * bb; q += B) {
-                const int64_t l = q / bb;
-                const int cc = (int)(q % bb);
-                xs[l * nbs + cc] = __ldcg(&xT[l * NB + cc]);
-            }
+            if (!gst)
+                for (int64_t q = t; q < kb * bb; q += B) {
+                    const int64_t l = q / bb;
+                    const int cc = (int)(q % bb);
+                    xs[l * nbs + cc] = __ldcg(&xT[l * NB + cc]);
+                }
             __syncthreads();
-            mv_rowdots<kLowerCol, NB>(Yc, n, rc0, rc1, kb, XRow{xs, nbs}, bb, red,
-                                      [&](int64_t r, int cc, double a) {
-                                          qb[cc * ns + r] = (r == k0 + cc) ? a - 1.0 : a;
-                                      });
+            {
+                auto outC = [&](int64_t r, int cc, double a) { qb[cc * ns + r] = (r == k0 + cc) ? a - 1.0 : a; };
+                if (gst)
+                    mv_rowdots<kLowerCol, NB>(Yc, n, rc0, rc1, kb, XGRow{xT, NB}, bb, red, outC);
+                else
+                    mv_rowdots<kLowerCol, NB>(Yc, n, rc0, rc1, kb, XRow{xs, nbs}, bb, red, outC);
+            }
             // statistics of this CTA's rows: sum |q_c| (next scaling) and max |q_c| (the test)
             for (int cc = wid; cc < bb; cc += nW) {
                 double as = 0.0;

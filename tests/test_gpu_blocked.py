@@ -37,7 +37,7 @@ def _graded(n, m, kappa, seed=0):
 
 
 @pytest.mark.parametrize("block", [2, 5, 8, 16])
-@pytest.mark.parametrize("n,m,kappa", [(700, 80, 1.0), (1500, 200, 1e8), (97, 97, 1e3)])
+@pytest.mark.parametrize("n,m,kappa", [(700, 80, 1.0), (1500, 200, 1e8), (97, 97, 1e3), (1500, 600, 1e4)])
 def test_orth_block_matches_oracle(gpu, orc, n, m, kappa, block):
     V = np.random.default_rng(5).standard_normal((n, m)) if kappa == 1.0 else _graded(n, m, kappa)
     kap = np.linalg.cond(V)
@@ -101,13 +101,17 @@ def test_blocked_other_workloads(gpu, orc, case):
     _check_blocked(gpu, orc, d, e, w, 8, oracle_clusters=pick)
 
 
-def test_blocked_toeplitz4200_closed_form(gpu):
-    # one cluster of 4200 members: too large for the block staging, so it takes the one-member
-    # path inside the blocked kernel; the closed form still holds
+@pytest.mark.parametrize("block", [8, 16])
+def test_blocked_toeplitz4200_closed_form(gpu, block):
+    # one cluster of 4200 members on a team of the whole grid: too large for the shared-memory
+    # block staging, so the team reads its staged vectors from its buffers in L2; the closed
+    # form holds
     n = 4200
     d, e = inputs.toeplitz(n, 2.0, 1.0)
     lam, V = inputs.toeplitz_eigenpairs(n, 2.0, 1.0)
-    Z, info, *_ = gpu.tinv(d, e, lam, block=8, return_info=True)
+    cnt = np.zeros(4, dtype=np.int64)
+    Z, info, *_ = gpu.tinv(d, e, lam, block=block, return_info=True, counters=cnt.ctypes.data)
+    assert cnt[2] > 0  # the cluster ran on a CTA team
     assert info == 0 and residual_ratio(d, e, lam, Z) <= 10 and orth_ratio(Z) <= 10
     from helpers import tri_matvec
 
