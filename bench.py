@@ -80,8 +80,8 @@ def parse():
     ap.add_argument("--block", type=int, default=None,
                     help="compact WY: cluster members orthogonalized in blocks of up to this many "
                          "(Sec. 3.2's block form; 0 = one member at a time, Alg. 4); default 16 "
-                         "for the glued workloads, 0 elsewhere (what tinv_tune_auto and "
-                         "tinv_tune_batch pick there)")
+                         "for single problems, 0 for the batch and the served stream (what "
+                         "tinv_tune_batch picks there)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
@@ -1214,10 +1214,10 @@ def phases_arm(args):
 def main():
     args = parse()
     if args.block is None:
-        # blocks of 16 where the clusters fit the block staging (glued W21+: clusters of 200
-        # and 400); elsewhere one member at a time, whose passes run faster with the L1 that
-        # the blocked kernel's shared-memory staging would take
-        args.block = 16 if args.workload.startswith("glued") else 0
+        # blocks of 16 for single problems; one member at a time for the batch and the served
+        # stream, whose many clusters on single CTAs run faster with the L1 that the blocked
+        # kernel's shared-memory staging would take
+        args.block = 0 if args.workload in ("batch512", "serve") else 16
     if args.phases_child:
         return _phases_child(args)
     if args.phases:

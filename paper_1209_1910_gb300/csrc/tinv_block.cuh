@@ -202,8 +202,8 @@ template <int KIND, int NV, class XF, class Out>
 __device__ __forceinline__ void mv_rowdots_nv(const double* __restrict__ A, int64_t lda, int64_t r0, int64_t r1,
                                               int64_t ccap, XF xf, int nv, double* red, Out out)
 {
-    // groups of 8 rows x 4 column phases unless the rows alone give every warp two groups of 32
-    if (r1 - r0 > 1024)
+    // groups of 8 rows x 4 column phases unless groups of 32 rows alone fill the 16 warps
+    if (r1 - r0 >= 512)
         mv_rowdots_rl<32, KIND, NV>(A, lda, r0, r1, ccap, xf, nv, red, out);
     else
         mv_rowdots_rl<8, KIND, NV>(A, lda, r0, r1, ccap, xf, nv, red, out);
