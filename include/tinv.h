@@ -87,9 +87,8 @@ typedef struct tinv_opts {
                          /*   own (Alg. 4); b = 2..16 = a cluster's members after its head in   */
                          /*   blocks of up to b that sweep together and are orthogonalized by   */
                          /*   the compact-WY block form of Sec. 3.2 (Eqs. cwy1/cwy2).  Applies  */
-                         /*   to clusters on CTA teams whose block staging fits the shared      */
-                         /*   memory (the block shrinks to fit: b <= team size, 2 b m_c <= a    */
-                         /*   per-order capacity); other clusters take b = 1                    */
+                         /*   to clusters of >= 3 members on CTA teams (the block is at most    */
+                         /*   twice the team size); clusters on single CTAs take b = 1          */
     int32_t reserved[3];
 } tinv_opts;
 

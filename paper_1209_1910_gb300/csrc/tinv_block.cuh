@@ -2,15 +2,17 @@
 // (tinv_opts.block >= 2): the members after the cluster's head are split into blocks of at most
 // nb that sweep together, block b holding the members 1 + b + nblk c (nblk blocks): the members
 // of a block are spread evenly over the cluster, and near neighbours in the spectrum, in
-// different blocks, are orthogonalized against finished vectors.  Per block sweep, each member's iterate is solved on its own CTA of the team
-// (no team barrier inside a solve), then the whole block is orthogonalized by the compact-WY
-// block form of Sec. 3.2 (Eqs. cwy1/cwy2): W = (I - Y T^T Y^T) V with one pass over Y for all
-// bb iterates, a Householder QR of the block's panel (one team barrier per column), T extended
-// by Eq. cwy1 with one triangular product over T for all columns, and the bb vectors
-// q = (Y T Y^T - I) e_col with one more pass over Y.  A sweep takes bb + 6 team barriers (bb + 8
-// on teams of kSliceBlock or more CTAs, which sum the partials of S and of the Gram rows once
-// per team by slices), where one member at a time takes about 9 per member.  Included by tinv_kernels.cu inside its
-// namespace (it uses the cluster kernel's context and the helpers defined there).
+// different blocks, are orthogonalized against finished vectors.  Per block sweep, each member's
+// iterate is solved on its own CTA of the team (no team barrier inside a solve), then the whole
+// block is orthogonalized by the compact-WY block form of Sec. 3.2 (Eqs. cwy1/cwy2):
+// W = (I - Y T^T Y^T) V with one pass over Y for all bb iterates, a Householder QR of the
+// block's panel (one team barrier per column), T extended by Eq. cwy1 with triangular products
+// over T for all columns, and the bb vectors q = (Y T Y^T - I) e_col with one more pass over Y.
+// The vectors the passes and products share (the team's sums of S, S', the Gram rows, X_T) are
+// staged in shared memory for small blocks and read from the team's buffers in L2 otherwise.
+// A sweep takes bb + 6 team barriers (bb + 8 where the team sums S and the Gram rows once by
+// slices), where one member at a time takes about 9 per member.  Included by tinv_kernels.cu
+// inside its namespace (it uses the cluster kernel's context and the helpers defined there).
 #pragma once
 
 // Row-major staged vectors in shared memory: x_c[idx] = p[idx * ld + c].
@@ -282,14 +284,9 @@ __device__ __forceinline__ int block_members(const Ws& w, int64_t mc, int G)
     if (w.block < 2 || G < 2 || mc < 3 || !w.vblk) return 1;
     // up to 2 members per CTA (each CTA solves its members one after the other); the panel
     // buffer holds bb (n/G + 1) <= 2 n + 64 doubles
-    int nb = min(w.block, 2 * G);
-    // staged vectors in shared memory, nb doubles per row: 2 nb mc for the T products, nb (mc + nb)
-    // for pass C.  Teams of kSliceBlock or more CTAs read them from the team's buffers in global
-    // memory (L2) when they do not fit; smaller teams halve the block until they fit.
-    if (G < kSliceBlock) {
-        while (nb >= 2 && !staging_fits(w, mc, nb)) nb >>= 1;
-        if (nb < 2) return 1;
-    }
+    // staged vectors in shared memory when they fit (nb doubles per row: 2 nb mc for the T
+    // products, nb (mc + nb) for pass C), else read from the team's buffers in L2
+    const int nb = min(w.block, 2 * G);
     // the CTA-local solves use the staging area as their scratch
     if (w.xcap < SolveScratch<16>::size(1) || w.xcap < 6 * kStageRows) return 1;
     return nb;
@@ -332,9 +329,9 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
     double* W = cx.vsm;                        // this CTA's panel rows, column c at + c Rb
     double* xs = cx.xs;                        // staged vectors, nbs doubles per row
     const int nbs = nb;
-    // gst: the staged vectors are read from the team's buffers in L2 (the cluster is too large
-    // for the shared-memory staging); the team sums of S and the Gram rows are then always
-    // formed by slices, so that they exist in global memory
+    // gst: the staged vectors are read from the team's buffers in L2 (they do not fit the
+    // shared-memory staging area, which holds only small blocks); the team sums of S and the
+    // Gram rows are then always formed by slices, so that they exist in global memory
     const bool gst = !staging_fits(w, mc, nb);
     const bool sliced = G >= kSliceBlock || gst;  // team sums of S and the Gram rows by slices
     double* red = cx.red;
@@ -348,7 +345,7 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
     if (!TINV_IN(s0 >= 0 && mc >= 1 && s0 + mc <= w.nM && n <= p.n && rank < G && leader + G <= w.P &&
                      dbg_range((int64_t)jr.off, (int64_t)jr.off + mc * n, w.nF) &&
                      dbg_range(w.cltoff[c], w.cltoff[c] + mc * mc, w.nTT) &&
-                     nb >= 2 && nb <= NB && nb <= 2 * G && (staging_fits(w, mc, nb) || G >= kSliceBlock) &&
+                     nb >= 2 && nb <= NB && nb <= 2 * G &&
                      (p.zlen == 0 || dbg_range(sg.z + jr.jl * ldz, sg.z + (jr.jl + mc - 1) * ldz + n, p.zlen)),
                  cx.err))
         return false;

@@ -1480,9 +1480,13 @@ size_t chain_smem_bytes(int64_t n, bool use_smem, int32_t xcap)
 int32_t block_xcap(int64_t n)
 {
     if (!chain_use_smem(n)) return 0;
-    // 227 KB of shared memory per CTA, 8 KB of it left for the kernel's static arrays
+    // 227 KB of shared memory per CTA, 8 KB of it left for the kernel's static arrays.  The area
+    // holds the CTA-local solves' scratch and the staged vectors of small blocks only: larger
+    // blocks read theirs from the team's buffers in L2, which measured faster than a larger area
+    // (every KB of it is taken from the L1 that the passes' reads of Y go through; glued
+    // n = 4200: 89.8 ms with 4 K doubles, 92.4 ms with 16 K)
     const int64_t avail = (int64_t)(227 * 1024 - 8 * 1024) / 8 - 2048 - 2 * n - 64 - 512;
-    return (int32_t)max((int64_t)0, min((int64_t)16384, avail));
+    return (int32_t)max((int64_t)0, min((int64_t)4096, avail));
 }
 
 int32_t chain_grid(int32_t cap, int64_t)
