@@ -1041,13 +1041,14 @@ def ours_arm(args):
                       "h2d_bytes_per_step": (n + (n - 1) + m) * 8,
                       "d2h_bytes_per_step": n * m * 8 + m * 4 + 64}
 
-    # the MGS comparison on the same workload (Alg. 1 on the GPU), fewer steps.  On the n = 10^4
-    # workloads (one cluster of ~10^4 members) MGS would need about ten minutes on its one CTA,
-    # so both methods run on the first SUB eigenvalues of the same matrix (a cluster of SUB
-    # members)
+    # the MGS comparison on the same workload (Alg. 1 on the GPU), fewer steps.  Where MGS would
+    # take minutes (one cluster of thousands of members on one CTA: Toeplitz, n = 10^4), both
+    # methods run on the first SUB eigenvalues of the same matrix
     if not args.no_compare and args.method == "cwy" and world == 1:
         SUB = 500
-        msub = m if m <= 5000 else SUB
+        sizes = np.diff(np.r_[np.flatnonzero(np.r_[True, head[1:] != head[:-1]]), len(head)])
+        mgs_cost = float(np.sum(sizes.astype(np.float64) ** 2)) * n  # ~ MGS flops / 6 per sweep
+        msub = m if mgs_cost <= 2e10 else min(m, SUB)
         tw_c, Z_c = tw[:msub], Zt[:msub]
 
         def step_c(method, block):
@@ -1079,8 +1080,9 @@ def ours_arm(args):
                                           "cluster over a CTA team)" % (ncl, min(ncl, P), P)}}
         if msub < m:
             t_cwy = timed_c("cwy", blk)
-            out["compare"]["subset"] = ("the first %d of the %d eigenvalues, both methods (MGS on "
-                                        "the whole matrix would take about ten minutes)" % (msub, m))
+            out["compare"]["subset"] = ("the first %d of the %d eigenvalues, both methods (MGS, one "
+                                        "CTA per cluster, would take minutes on the whole matrix)"
+                                        % (msub, m))
             out["compare"]["cwy"] = {"value": msub / (t_cwy * 1e-3), "ms_per_step": t_cwy,
                                      "block": blk}
         # the other form of compact WY on the same workload: one member at a time (Alg. 4 as
@@ -1214,10 +1216,9 @@ def phases_arm(args):
 def main():
     args = parse()
     if args.block is None:
-        # blocks of 16 for single problems; one member at a time for the batch and the served
-        # stream, whose many clusters on single CTAs run faster with the L1 that the blocked
-        # kernel's shared-memory staging would take
-        args.block = 0 if args.workload in ("batch512", "serve") else 16
+        # blocks of 16 for single problems; one member at a time for the batch, the served stream
+        # and the split driver (many small clusters on single CTAs, where blocks gain nothing)
+        args.block = 0 if args.workload in ("batch512", "serve", "split4200") else 16
     if args.phases_child:
         return _phases_child(args)
     if args.phases:
