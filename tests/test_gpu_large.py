@@ -1,6 +1,8 @@
 """Full-size single problems of order 10^4 (one Peters-Wilkinson cluster of nearly all vectors):
 the residual and orthogonality bounds on the whole result (products formed on the GPU), the closed form per
-sampled vector for d=0, e=1, and the singletons of the uniform matrix against the oracle."""
+sampled vector for d=0, e=1, and the singletons of the uniform matrix against the oracle; one
+member at a time and in blocks of 16 (the cluster on the whole grid, its staged vectors read from
+the team's buffers in L2)."""
 import math
 
 import numpy as np
@@ -24,7 +26,7 @@ def gpu():
     return binding
 
 
-def _solve_on_device(gpu, d, e, w):
+def _solve_on_device(gpu, d, e, w, block=0):
     import torch
 
     dev = torch.device("cuda:0")
@@ -32,7 +34,7 @@ def _solve_on_device(gpu, d, e, w):
     td, te, tw = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (d, e, w))
     Zt = torch.zeros((n, n), dtype=torch.float64, device=dev)  # row j = eigenvector j
     info = torch.zeros(1, dtype=torch.int64, device=dev)
-    gpu.tinv_device(td, te, tw, Zt, info=info)
+    gpu.tinv_device(td, te, tw, Zt, info=info, block=block)
     torch.cuda.synchronize()
     assert int(info.item()) == 0
     Z = Zt.T
@@ -50,11 +52,12 @@ def _solve_on_device(gpu, d, e, w):
     return Zt, res, orth
 
 
-def test_toeplitz_zero_diagonal_10000_closed_form(gpu):
+@pytest.mark.parametrize("block", [0, 16])
+def test_toeplitz_zero_diagonal_10000_closed_form(gpu, block):
     n = 10000
     d, e = inputs.toeplitz(n, 0.0, 1.0)
     lam = np.sort(2.0 * np.cos(np.arange(1, n + 1) * math.pi / (n + 1)))
-    Zt, res, orth = _solve_on_device(gpu, d, e, lam)
+    Zt, res, orth = _solve_on_device(gpu, d, e, lam, block)
     assert res <= 10 and orth <= 10
     # sampled vectors against sin(i k pi / (n+1)), within the Davis-Kahan bound 4 |r| / gap
     i = np.arange(1, n + 1)
@@ -71,12 +74,13 @@ def test_toeplitz_zero_diagonal_10000_closed_form(gpu):
         assert ang <= 4 * np.linalg.norm(r) / gap + 1e-13, j
 
 
-def test_uniform_10000_invariants_and_singletons(gpu, orc):
+@pytest.mark.parametrize("block", [0, 16])
+def test_uniform_10000_invariants_and_singletons(gpu, orc, block):
     from scipy.linalg import eigvalsh_tridiagonal
 
     d, e = inputs.uniform(10000, seed=1)
     w = eigvalsh_tridiagonal(d, e)  # LAPACK's MRRR eigenvalues: any accurate w will do here
-    Zt, res, orth = _solve_on_device(gpu, d, e, w)
+    Zt, res, orth = _solve_on_device(gpu, d, e, w, block)
     assert res <= 10 and orth <= 10
     head = orc.plan(d, e, w)[1]
     cl = clusters_from_heads(head)
