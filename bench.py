@@ -759,6 +759,7 @@ def driver_arm(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     phase = np.zeros(4, dtype=np.float32)
     iters = torch.zeros(n, dtype=torch.int32, device=dev)
+    blk = args.block if args.method == "cwy" else 0
     if args.workload == "split4200":
         tw = torch.zeros(n, dtype=torch.float64, device=dev)
         tZ = torch.zeros((n, n), dtype=torch.float64, device=dev)
@@ -767,7 +768,7 @@ def driver_arm(args):
         def step(with_phase):
             kw = {"phase_ms": phase.ctypes.data} if with_phase else {}
             return binding.eig_device(ta, tb, tw, tZ, tib, method=args.method, iters=iters,
-                                      **kw)[0]
+                                      block=blk, **kw)[0]
     else:
         ts = torch.zeros(n, dtype=torch.float64, device=dev)
         tU = torch.zeros((n, n), dtype=torch.float64, device=dev)
@@ -776,7 +777,7 @@ def driver_arm(args):
         def step(with_phase):
             kw = {"phase_ms": phase.ctypes.data} if with_phase else {}
             return binding.bdsvd_device(ta, tb, ts, tU, tV, method=args.method,
-                                        iters=iters.data_ptr(), **kw)
+                                        iters=iters.data_ptr(), block=blk, **kw)
 
     for _ in range(args.warmup):
         if step(False) != 0:
@@ -851,7 +852,7 @@ def driver_arm(args):
         "metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "method": args.method,
+        "config": {"workload": WORKLOADS[args.workload], "method": args.method, "block": blk,
                    "parallelism": "single", "inputs": "resident in HBM",
                    "l2": "flushed by a 512 MiB write between steps"},
         "check": check,
