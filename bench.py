@@ -868,8 +868,8 @@ def driver_arm(args):
     if not args.no_e2e:
         pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
         ha, hb2 = pin(a), pin(b)
-        call = (lambda: binding.eig(ha, hb2, method=args.method)) if args.workload == "split4200" \
-            else (lambda: binding.bdsvd(ha, hb2, method=args.method))
+        call = (lambda: binding.eig(ha, hb2, method=args.method, block=blk)) \
+            if args.workload == "split4200" else (lambda: binding.bdsvd(ha, hb2, method=args.method, block=blk))
         call()
         el = 0.0
         for _ in range(args.steps):

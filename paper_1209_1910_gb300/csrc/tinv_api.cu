@@ -14,10 +14,84 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/tinv.h"
 #include "tinv_internal.h"
 
 namespace tinvx {
+
+// One pool per (device, context): a pool belongs to the context it was created in (a driver
+// context the caller made current, or a primary context re-created after cudaDeviceReset, has
+// its own), so the cache is keyed by the unique id of the current context.
+using PoolCtxGetCurrentFn = CUresult (*)(CUcontext*);
+using PoolCtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+struct PoolEntry {
+    unsigned long long ctx_id;
+    cudaMemPool_t pool;
+};
+static std::mutex g_pool_mu;
+static PoolEntry g_pools[64];
+static int g_pool_used = 0;
+static bool g_pool_fn_init = false;
+static PoolCtxGetCurrentFn g_pool_ctx_cur = nullptr;
+static PoolCtxGetIdFn g_pool_ctx_id = nullptr;
+
+cudaMemPool_t lib_pool(cudaStream_t st)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    // a stream being captured into a graph takes a pool that exists; none is created then
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool_fn_init) {
+        g_pool_fn_init = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_pool_ctx_cur = (PoolCtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_pool_ctx_id = (PoolCtxGetIdFn)f;
+    }
+    if (!g_pool_ctx_cur || !g_pool_ctx_id) return nullptr;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_pool_ctx_cur(&ctx) != CUDA_SUCCESS || !ctx || g_pool_ctx_id(ctx, &id) != CUDA_SUCCESS)
+        return nullptr;
+    for (int i = 0; i < g_pool_used; ++i)
+        if (g_pools[i].ctx_id == id) return g_pools[i].pool;
+    if (g_pool_used == 64 || cap != cudaStreamCaptureStatusNone) return nullptr;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+        cudaMemPoolDestroy(pool);
+        return nullptr;
+    }
+    g_pools[g_pool_used++] = {id, pool};
+    return pool;
+}
+
+size_t lib_pool_idle()
+{
+    cudaMemPool_t pool = lib_pool(nullptr);
+    if (!pool) return 0;
+    uint64_t reserved = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess)
+        return 0;
+    return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -237,8 +237,18 @@ inline bool ascending(const double* a, int64_t k)
     return true;
 }
 
-// A device allocation owned by a scope: stream-ordered on `st` (cudaMallocAsync/cudaFreeAsync)
-// when `use_async`, else cudaMalloc/cudaFree.  Zero bytes allocate a small block.
+// The library's stream-ordered memory pool on the current device and context (created on first
+// use outside graph capture; it keeps freed memory instead of returning it at each
+// synchronization, so the workspaces of repeated calls are not mapped again); null when there
+// is none (no current context, or `st` is being captured before the pool exists).
+cudaMemPool_t lib_pool(cudaStream_t st);
+// Bytes the library's pool on the current device holds unused (free for its next allocations,
+// though cudaMemGetInfo counts them as taken).
+size_t lib_pool_idle();
+
+// A device allocation owned by a scope: stream-ordered on `st` (from the library's pool, else
+// the device's default pool, and cudaFreeAsync) when `use_async`, else cudaMalloc/cudaFree.
+// Zero bytes allocate a small block.
 struct DevBuf {
     void* p = nullptr;
     cudaStream_t st = nullptr;
@@ -248,7 +258,9 @@ struct DevBuf {
         st = s;
         async = use_async;
         if (bytes == 0) bytes = 256;
-        return async ? cudaMallocAsync(&p, bytes, st) : cudaMalloc(&p, bytes);
+        if (!async) return cudaMalloc(&p, bytes);
+        cudaMemPool_t pool = lib_pool(st);
+        return pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMallocAsync(&p, bytes, st);
     }
     ~DevBuf()
     {

@@ -330,12 +330,13 @@ bool tinv_server::admit()
                                         : std::max(1, sms / (int)streams.size());
     const int free_sms = sms - sms_used;
     if (free_sms < share && !inflight.empty()) return false;
-    // memory budget now: hbm_fraction of the free device memory plus what the waves hold
+    // memory budget now: hbm_fraction of the free device memory (with what the library's pool
+    // keeps unused from earlier waves) plus what the waves hold
     size_t budget_now = budget;
     {
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
-            budget_now = (size_t)(cfg.hbm_fraction * (double)(free_b + inflight_bytes));
+            budget_now = (size_t)(cfg.hbm_fraction * (double)(free_b + lib_pool_idle() + inflight_bytes));
     }
     double pend_work = 0.0;
     for (const ReqP& r : pending) pend_work += request_work(r->n);
