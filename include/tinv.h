@@ -59,7 +59,9 @@ typedef struct tinv_opts {
     uint64_t seed;       /* start vectors: counter-based SplitMix64 keyed by (seed, j0 + j)  */
     int64_t j0;          /* index offset of w[0] inside a larger problem (for start keys)    */
     void* workspace;     /* optional device workspace (device_ptrs = 1); NULL = the library  */
-    size_t workspace_bytes; /*   allocates stream-ordered memory itself                       */
+    size_t workspace_bytes; /*   allocates stream-ordered memory itself, from a memory pool   */
+                            /*   of its own per device and context that keeps freed memory  */
+                            /*   for later calls (no pool is created during graph capture)  */
     int32_t* iters;      /* optional [m]: sweeps taken by vector j, negated if not converged;  */
                          /*   host or device memory following device_ptrs                     */
     int64_t* info;       /* optional (device_ptrs = 1): device scalar that receives the count */
