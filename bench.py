@@ -79,9 +79,8 @@ def parse():
     ap.add_argument("--method", choices=["cwy", "mgs"], default="cwy")
     ap.add_argument("--block", type=int, default=None,
                     help="compact WY: cluster members orthogonalized in blocks of up to this many "
-                         "(Sec. 3.2's block form; 0 = one member at a time, Alg. 4); default 16 "
-                         "for single problems, 0 for the batch and the served stream (what "
-                         "tinv_tune_batch picks there)")
+                         "(Sec. 3.2's block form; 0 = one member at a time, Alg. 4); default 16, "
+                         "0 for the served stream and the split driver")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
@@ -1217,9 +1216,9 @@ def phases_arm(args):
 def main():
     args = parse()
     if args.block is None:
-        # blocks of 16 for single problems; one member at a time for the batch, the served stream
-        # and the split driver (many small clusters on single CTAs, where blocks gain nothing)
-        args.block = 0 if args.workload in ("batch512", "serve", "split4200") else 16
+        # blocks of 16; one member at a time for the served stream and the split driver (the
+        # latter's clusters lie inside blocks of order 21, where blocks gain nothing)
+        args.block = 0 if args.workload in ("serve", "split4200") else 16
     if args.phases_child:
         return _phases_child(args)
     if args.phases:

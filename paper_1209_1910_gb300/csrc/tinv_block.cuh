@@ -281,14 +281,19 @@ __device__ __forceinline__ bool staging_fits(const Ws& w, int64_t mc, int nb)
 
 // Members per block the blocked path uses for a cluster of mc members on a team of G CTAs
 // (1: the cluster takes the one-member path).
-__device__ __forceinline__ int block_members(const Ws& w, int64_t mc, int G)
+__device__ __forceinline__ int block_members(const Ws& w, int64_t mc, int G, int64_t n)
 {
-    if (w.block < 2 || G < 2 || mc < 3 || !w.vblk) return 1;
+    if (w.block < 2 || mc < 3 || !w.vblk) return 1;
+    // a CTA alone keeps the block's head rows in its own partial slot (16 n doubles), which
+    // needs n >= 24; small problems stay with one member at a time
+    if (G == 1 && n < 64) return 1;
     // up to 2 members per CTA (each CTA solves its members one after the other); the panel
     // buffer holds bb (n/G + 1) <= 2 n + 64 doubles
     // staged vectors in shared memory when they fit (nb doubles per row: 2 nb mc for the T
-    // products, nb (mc + nb) for pass C), else read from the team's buffers in L2
-    const int nb = min(w.block, 2 * G);
+    // products, nb (mc + nb) for pass C), else read from the team's buffers in L2.  On a team a
+    // CTA solves at most two members per sweep and holds its panel rows in shared memory; a CTA
+    // alone solves them all and holds its panel in its q-vector buffer.
+    const int nb = (G >= 2) ? min(w.block, 2 * G) : w.block;
     // the CTA-local solves use the staging area as their scratch
     if (w.xcap < SolveScratch<16>::size(1) || w.xcap < 6 * kStageRows) return 1;
     return nb;
@@ -327,8 +332,12 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
     double* sP = tb;                           // S' = T^T Y^T V  [i NB + c]
     double* tP = tb + (size_t)NB * ns;         // T_k (Y_k^T Y_b)  [i NB + c]
     double* xT = tb + 2 * (size_t)NB * ns;     // X_T, then T_k R1 before it  [i NB + c]
-    double* ybr = tb + 3 * (size_t)NB * ns;    // rows k0.. of Y_b  [r NB + c] (rank 1's slot; G >= 2)
-    double* W = cx.vsm;                        // this CTA's panel rows, column c at + c Rb
+    // rows k0.. of Y_b [r NB + c]: in rank 1's slot of the team vectors, or, for a CTA alone,
+    // after the panel and statistics partials of its own slot
+    double* ybr = (G >= 2) ? tb + 3 * (size_t)NB * ns : pQ + 128;
+    // this CTA's panel rows, column c at + c Rb: in shared memory on a team; a CTA alone holds
+    // all rows k0.. of the panel in its q-vector buffer (free from the solves to pass C)
+    double* W = (G >= 2) ? cx.vsm : qb;
     double* xs = cx.xs;                        // staged vectors, nbs doubles per row
     const int nbs = nb;
     // gst: the staged vectors are read from the team's buffers in L2 (they do not fit the
@@ -347,7 +356,7 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
     if (!TINV_IN(s0 >= 0 && mc >= 1 && s0 + mc <= w.nM && n <= p.n && rank < G && leader + G <= w.P &&
                      dbg_range((int64_t)jr.off, (int64_t)jr.off + mc * n, w.nF) &&
                      dbg_range(w.cltoff[c], w.cltoff[c] + mc * mc, w.nTT) &&
-                     nb >= 2 && nb <= NB && nb <= 2 * G &&
+                     nb >= 2 && nb <= NB && (G == 1 || nb <= 2 * G) && (G >= 2 || (int64_t)NB * ns >= 384) &&
                      (p.zlen == 0 || dbg_range(sg.z + jr.jl * ldz, sg.z + (jr.jl + mc - 1) * ldz + n, p.zlen)),
                  cx.err))
         return false;
@@ -420,7 +429,7 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
         const int64_t rc0 = s_rows[2], rc1 = s_rows[3];
         const int64_t c0 = s_rows[4], c1 = s_rows[5], i0 = s_rows[6], i1 = s_rows[7];
         if (!TINV_IN(dbg_range(rb0, rb1, n) && rb0 >= k0 && dbg_range(rc0, rc1, n) && dbg_range(c0, c1, k0) &&
-                         dbg_range(i0, i1, k0) && (int64_t)bb * Rb <= 2 * n + 64 && kb <= mc,
+                         dbg_range(i0, i1, k0) && (G == 1 || (int64_t)bb * Rb <= 2 * n + 64) && kb <= mc,
                      cx.err))
             return false;
         const int maxits = orth ? 1 : kMaxIts;
@@ -454,7 +463,7 @@ __device__ __noinline__ bool bcwy_cluster(ChainCtx& cx, int32_t c, Team& tm, int
             if (k0 > 0) {
                 const int64_t Ra = rc1 - rc0;
                 auto outA = [&](int64_t i, int cc, double v) { pA[i * NB + cc] = v; };
-                if ((int64_t)bb * Ra <= 2 * n) {
+                if (G >= 2 && (int64_t)bb * Ra <= 2 * n) {
                     for (int64_t q = t; q < (int64_t)bb * Ra; q += B) {
                         const int cc = (int)(q / Ra);
                         W[q] = vsrc(rc0 + q % Ra, cc);

@@ -1411,7 +1411,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t
         Team tm{tf, tg, tr, w.bar + tf, 0u};
         bool ok;
         if (METHOD == 2) {  // compact WY with blocks of members where the team's cluster allows
-            const int nbk = cx.xs ? block_members(w, w.clsize[tc], tg) : 1;
+            const int nbk = cx.xs ? block_members(w, w.clsize[tc], tg, w.segs[w.segj[w.clstart[tc]]].n) : 1;
             ok = (nbk >= 2) ? bcwy_cluster(cx, tc, tm, nbk) : cwy_cluster(cx, tc, tm);
         } else if (METHOD == 0) {
             ok = cwy_cluster(cx, tc, tm);
@@ -1433,7 +1433,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_chain(Problem p, Ws w, int32_t
         if (c < 0) break;
         if (!TINV_IN(c < (int32_t)w.nM, cx.err)) return;
         Team tm{b, 1, 0, w.bar + b, 0u};
-        const bool ok = (METHOD != 1) ? cwy_cluster(cx, c, tm) : mgs_cluster(cx, c);
+        bool ok;
+        if (METHOD == 2) {  // the blocked form also on a CTA alone where the cluster allows
+            const int nbk = cx.xs ? block_members(w, w.clsize[c], 1, w.segs[w.segj[w.clstart[c]]].n) : 1;
+            ok = (nbk >= 2) ? bcwy_cluster(cx, c, tm, nbk) : cwy_cluster(cx, c, tm);
+        } else {
+            ok = (METHOD != 1) ? cwy_cluster(cx, c, tm) : mgs_cluster(cx, c);
+        }
         if (!ok) return;
     }
 #ifdef TINV_PHASE_PROFILE

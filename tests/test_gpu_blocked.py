@@ -130,6 +130,29 @@ def test_blocked_deterministic_and_block_one_is_the_member_path(gpu):
     assert np.array_equal(gpu.tinv(d, e, w, block=0), Z0)
 
 
+@pytest.mark.parametrize("block", [8, 16])
+def test_blocked_single_cta(gpu, orc, block):
+    # every cluster on one CTA (max_team = 1): the blocked form there holds the block's panel in
+    # the CTA's q-vector buffer; every cluster against the oracle's blocked iteration
+    d, e = inputs.glued_wilkinson(100, 1e-10)
+    w = inputs.eigenvalues(d, e)
+    Z, info, ifail, iters = gpu.tinv(d, e, w, block=block, max_team=1, return_info=True)
+    assert info == 0 and np.all(iters == 3)
+    assert residual_ratio(d, e, w, Z) <= 10 and orth_ratio(Z) <= 10
+    for idx in clusters_from_heads(orc.plan(d, e, w)[1]):
+        if len(idx) > 1:
+            s, t = int(idx[0]), int(idx[-1]) + 1
+            Zo, oinfo, *_ = orc.tinv(d, e, w[s:t], "cwy", j0=s, block=block)
+            assert oinfo == 0
+            assert sin_angle(Zo, Z[:, s:t]) <= 1e-10, (s, t)
+    assert check_sign_convention(Z) > 0
+    # a uniform matrix's clusters of all sizes, and repeats bit for bit
+    d, e, w = inputs.workload("uniform1000")
+    Z = gpu.tinv(d, e, w, block=block, max_team=1)
+    assert residual_ratio(d, e, w, Z) <= 10 and orth_ratio(Z) <= 10
+    assert np.array_equal(Z, gpu.tinv(d, e, w, block=block, max_team=1))
+
+
 def test_blocked_batch(gpu, orc):
     probs = []
     for q, n in enumerate([64, 2100, 97, 420, 1000]):
