@@ -66,7 +66,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (vector and tensor alike), TFLOP/s
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum); None where no capture exists
 # DRAM bytes of one k_chain launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass),
 # by workload, method and block; None for a configuration not captured with the current kernel
-TRAFFIC_BYTES = {("glued4200", "cwy", 16): 17.93e9}
+TRAFFIC_BYTES = {("glued4200", "cwy", 16): 16.56e9}
 
 
 def parse():
